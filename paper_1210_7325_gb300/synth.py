@@ -1,0 +1,128 @@
+"""Seeded synthetic inputs shaped like the paper's GWAS workloads.
+
+This module only draws inputs (M, X_L, y, X_R); it holds none of the GLS
+arithmetic, so both the GPU path's tests/benchmarks and the CPU oracle can be
+fed from it.
+
+Recipe (the paper fixes only shapes and SPD-ness of M; the rest is the stated
+synthetic workload):
+  * kinship: G is n x n_markers with column j ~ Binomial(2, f_j),
+    f_j ~ U(0.05, 0.5); columns standardized by their empirical mean and
+    (population) standard deviation, zero-variance columns redrawn;
+    K = G G^T / n_markers; Phi_ij = K_ij / sqrt(K_ii K_jj) (unit diagonal);
+    M = h Phi + (1 - h) I, SPD for 0 <= h < 1.
+  * covariates: X_L = [1, N(0,1), ..., N(0,1)], n x (p - 1).
+  * phenotype: y ~ N(0, 1), n.
+  * genotypes: X_R is n x m int8, SNP i ~ Binomial(2, f_i), f_i ~ U(0.05, 0.5),
+    stored column-major (each SNP's n genotypes contiguous).
+Every draw comes from a counter-based Philox stream keyed by (seed, stream id).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+BASE_SEED = 20121030
+
+_STREAM_KINSHIP = 1
+_STREAM_COVARIATES = 2
+_STREAM_PHENOTYPE = 3
+_STREAM_GENOTYPES = 4
+
+
+def rng(seed: int, stream: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(np.random.SeedSequence([int(seed), int(stream)])))
+
+
+def kinship_markers(n: int, seed: int, n_markers: int = 5000) -> np.ndarray:
+    """Standardized marker matrix G (n x n_markers, float64, C order)."""
+    g = rng(seed, _STREAM_KINSHIP)
+    G = np.empty((n, n_markers), dtype=np.float64)
+    f = g.uniform(0.05, 0.5, size=n_markers)
+    for j in range(n_markers):
+        while True:
+            col = g.binomial(2, f[j], size=n).astype(np.float64)
+            sd = col.std()
+            if sd > 0.0:
+                break
+            f[j] = g.uniform(0.05, 0.5)
+        G[:, j] = (col - col.mean()) / sd
+    return G
+
+
+def kinship_M(n: int, h: float, seed: int, n_markers: int = 5000, device: str = "cpu"):
+    """M = h Phi + (1 - h) I as an n x n float64 array (symmetric, so C order
+    equals column-major).  ``device`` selects where G G^T is multiplied
+    (a torch device string); the result is always returned on the host."""
+    G = kinship_markers(n, seed, n_markers)
+    if device == "cpu":
+        K = (G @ G.T) / n_markers
+    else:
+        import torch
+        Gt = torch.from_numpy(G).to(device)
+        K = (Gt @ Gt.T).div_(n_markers).cpu().numpy()
+    d = np.sqrt(np.diag(K).copy())
+    Phi = K / d[:, None] / d[None, :]
+    Phi = 0.5 * (Phi + Phi.T)
+    np.fill_diagonal(Phi, 1.0)
+    M = h * Phi
+    M[np.diag_indices(n)] += (1.0 - h)
+    return np.ascontiguousarray(M)
+
+
+def covariates(n: int, p: int, seed: int) -> np.ndarray:
+    """X_L (n x (p-1)) column-major: a column of ones then N(0,1) columns."""
+    if p < 1:
+        raise ValueError("p >= 1")
+    g = rng(seed, _STREAM_COVARIATES)
+    XL = np.empty((n, max(p - 1, 0)), dtype=np.float64, order="F")
+    if p >= 2:
+        XL[:, 0] = 1.0
+        for c in range(1, p - 1):
+            XL[:, c] = g.standard_normal(n)
+    return XL
+
+
+def phenotype(n: int, seed: int) -> np.ndarray:
+    return rng(seed, _STREAM_PHENOTYPE).standard_normal(n)
+
+
+def genotypes_np(n: int, m: int, seed: int) -> np.ndarray:
+    """X_R (n x m int8, column-major) on the host with numpy; for small m."""
+    g = rng(seed, _STREAM_GENOTYPES)
+    f = g.uniform(0.05, 0.5, size=m)
+    X = np.empty((n, m), dtype=np.int8, order="F")
+    for i in range(m):
+        X[:, i] = g.binomial(2, f[i], size=n)
+    return X
+
+
+def genotypes_torch(n: int, m: int, seed: int, device="cpu", chunk: int = 8192, out=None):
+    """X_R as a torch int8 tensor of shape (m, n) (row i = SNP i, i.e. the
+    column-major n x m matrix), drawn on ``device`` in chunks of SNPs.
+    Binomial(2, f) is drawn as the sum of two Bernoulli(f) draws."""
+    import torch
+    dev = torch.device(device)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed) * 1000003 + _STREAM_GENOTYPES)
+    if out is None:
+        out = torch.empty((m, n), dtype=torch.int8, device=dev)
+    for s in range(0, m, chunk):
+        c = min(chunk, m - s)
+        f = torch.rand((c, 1), generator=gen, device=dev, dtype=torch.float32) * 0.45 + 0.05
+        u0 = torch.rand((c, n), generator=gen, device=dev, dtype=torch.float32)
+        x = (u0 < f).to(torch.int8)
+        u0 = torch.rand((c, n), generator=gen, device=dev, dtype=torch.float32, out=u0)
+        x += (u0 < f).to(torch.int8)
+        out[s:s + c].copy_(x)
+    return out
+
+
+def problem(n: int, p: int, m: int, h: float, seed: int, n_markers: int = 5000,
+            kin_device: str = "cpu"):
+    """A small complete problem on the host: dict(M, XL, y, XR) with XR n x m int8."""
+    return dict(
+        M=kinship_M(n, h, seed, n_markers, device=kin_device),
+        XL=covariates(n, p, seed),
+        y=phenotype(n, seed),
+        XR=genotypes_np(n, m, seed),
+    )
