@@ -1,0 +1,164 @@
+/*
+ * gls_gb300.h -- C ABI of the GB300 (sm_103a) GWAS GLS library.
+ *
+ * The library computes the sequence of generalized least-squares problems of
+ * Eq. 1 of Fabregat-Traver, Aulchenko and Bientinesi, "Solving Sequences of
+ * Generalized Least-Squares Problems on Multi-threaded Architectures":
+ *
+ *     b_i := (X_i^T M^{-1} X_i)^{-1} X_i^T M^{-1} y,   1 <= i <= m,
+ *
+ * with X_i = (X_L | x_Ri) (Section 1), M an n x n SPD matrix, X_L the n x (p-1)
+ * covariates shared by every problem, x_Ri one n x 1 SNP column and y the
+ * phenotype.  The calls follow the two phases of Alg. 5 (hp-gwas) and Alg. 8
+ * (ooc-hp-gwas): a setup that factors M and whitens X_L and y once
+ * (Alg. 5 lines 1, 2, 4, 5, 6), then a loop over blocks of SNP columns
+ * (Alg. 5 lines 3, 7-11; Alg. 8 lines 6-16).
+ *
+ * Conventions for every entry point
+ *   - Matrices are column-major with an explicit leading dimension (the
+ *     LAPACK convention of Table 1).
+ *   - Pointers may be host memory (pageable or pinned) or device memory of the
+ *     plan's device; the library finds out which with cudaPointerGetAttributes.
+ *     The caller owns every input and output buffer.
+ *   - No call throws, aborts or traps: each returns a gls_status_t, and
+ *     gls_last_error() gives a one-line description of the last failure on
+ *     the calling thread.
+ *   - A plan is used by one host thread at a time.
+ */
+#ifndef GLS_GB300_H
+#define GLS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gls_plan* gls_plan_t;
+
+typedef enum {
+  GLS_OK = 0,
+  GLS_ERR_INVALID_ARG = 1,      /* a size, pointer or leading dimension is invalid          */
+  GLS_ERR_NOT_SPD = 2,          /* M is not SPD; *info = 1-based failing pivot (potrf)      */
+  GLS_ERR_OOM = 3,              /* device or pinned host allocation failed                  */
+  GLS_ERR_CUDA = 4,             /* a CUDA runtime call failed (see gls_last_error)          */
+  GLS_ERR_TIMEOUT = 5,          /* a bounded device wait gave up; the result is not valid   */
+  GLS_ERR_STATE = 6,            /* call out of order (e.g. solve before factor)             */
+  GLS_ERR_UNSUPPORTED = 7,      /* precision or device not supported by this build          */
+  GLS_ERR_COVARIATES_SINGULAR = 8 /* X~_L^T X~_L not SPD; *info = 1-based failing pivot     */
+} gls_status_t;
+
+typedef enum {
+  /* Every step in binary64 (Section 2.3 precision of the paper's MKL runs). */
+  GLS_PREC_FP64 = 0,
+  /* The off-diagonal blocks of the blocked triangular solve run on tcgen05
+   * tensor cores with operands split into BF16 (resp. FP16) slices and FP32
+   * accumulation; the Cholesky of M, the diagonal blocks, the Gram epilogue
+   * reduction and the p x p solves stay FP64. */
+  GLS_PREC_MIXED_BF16 = 1,
+  GLS_PREC_MIXED_FP16 = 2
+} gls_precision_t;
+
+/* Plan flags (gls_plan_desc_t.flags). */
+/* Mixed paths only: split every entry of L^{-1} on its own in floating point
+ * (hi/lo terms, no per-row fixed-point hi part).  FP32 accumulation of the hi
+ * products is then inexact; kept to measure what the fixed-point hi part buys. */
+#define GLS_FLAG_NAIVE_SPLIT 1u
+
+/* Plan description.  Zero-initialise and fill the fields that matter. */
+typedef struct {
+  int64_t n;               /* number of observations (rows of M, X_L, y, x_Ri), n >= 1       */
+  int32_t p;               /* unknowns per problem: cols(X_L) + 1, 1 <= p <= 32              */
+  int32_t precision;       /* gls_precision_t                                                */
+  int64_t max_block_snps;  /* largest k passed to gls_solve_block; sizes the workspaces      */
+  int32_t device;          /* CUDA device ordinal                                            */
+  int32_t split_terms;     /* mixed paths: operand slices of L^{-1}, 2 or 3 (0 = default 3)  */
+  void* stream;            /* cudaStream_t for compute; NULL = the plan creates its own      */
+  uint32_t flags;          /* GLS_FLAG_* bits; 0 for the defaults                            */
+  int32_t reserved[7];     /* must be 0                                                      */
+} gls_plan_desc_t;
+
+/*
+ * Creates a plan and allocates its device workspaces (L, L^{-1}, whitened
+ * covariates and phenotype, the two double-buffered X_R and b blocks, the
+ * Gram partials).  *out receives the plan.  Errors: INVALID_ARG (bad
+ * description), UNSUPPORTED (device is not sm_103), OOM, CUDA.
+ */
+gls_status_t gls_plan_create(const gls_plan_desc_t* desc, gls_plan_t* out);
+
+/*
+ * Setup phase of Alg. 5 (lines 1, 2, 4, 5, 6):
+ *   L L^T = M (potrf); X~_L = L^{-1} X_L; y~ = L^{-1} y;
+ *   S_TL = X~_L^T X~_L; b_T = X~_L^T y~ (Fig. 1), all in binary64.
+ * M   n x n (ldm >= n), only the lower triangle is read.  M == NULL keeps the
+ *     factor of the previous call (a new phenotype for the same M).
+ * XL  n x (p-1) (ldxl >= n); NULL when p == 1.  With M == NULL, XL == NULL
+ *     also keeps the previous X~_L.
+ * y   n.
+ * info (may be NULL) receives 0, or the 1-based failing pivot when the
+ *     status is NOT_SPD or COVARIATES_SINGULAR.
+ * Synchronous: returns when the setup has finished on the device.
+ */
+gls_status_t gls_factor(gls_plan_t plan, const double* M, int64_t ldm, const double* XL,
+                        int64_t ldxl, const double* y, int64_t* info);
+
+/*
+ * One block of the SNP loop (Alg. 5 lines 3 and 7-11): for the k SNP columns
+ * of XR, x~_i = L^{-1} x_Ri (blocked triangular solve), the Gram entries
+ * S_BL_i = X~_L^T x~_i, S_BR_i = x~_i^T x~_i, b_B_i = y~^T x~_i, and
+ * b_i = S_i^{-1} (b_T; b_B_i) by a Cholesky solve of the p x p system.
+ * XR  n x k int8 genotype codes (ldxr >= n); every int8 value is accepted.
+ * B   p x k binary64 output (ldb >= p): X_L coefficients first, SNP last.
+ * snp_status (may be NULL) k int32: 0, or 1 when S_i is not numerically SPD
+ *     (its last pivot d <= tau * S_BR_i with tau = 2^-30 for FP64 and 2^-16
+ *     for the mixed paths); that b_i is NaN and the call still returns OK.
+ * 0 <= k <= max_block_snps.  With every pointer in device memory the call is
+ * asynchronous on the plan's stream; with any host pointer it copies and
+ * returns after the block is complete.  Errors: STATE (no successful
+ * gls_factor yet), INVALID_ARG, CUDA, TIMEOUT.
+ */
+gls_status_t gls_solve_block(gls_plan_t plan, const int8_t* XR, int64_t ldxr, int64_t k,
+                             double* B, int64_t ldb, int32_t* snp_status);
+
+/*
+ * The whole SNP stream of Alg. 8 (ooc-hp-gwas): XR holds m SNP columns in host
+ * memory (pinned for full overlap; pageable is staged through pinned
+ * buffers).  Blocks of up to max_block_snps columns are double-buffered: the
+ * copy of block j+1 to the device runs on a side stream while block j is
+ * solved, and b of block j is copied back while block j+1 is solved
+ * (Section 4.2).  The first block is smaller so that its unoverlapped load is
+ * short (Section 4.3).  B (p x m, ldb >= p) and snp_status (m, may be NULL)
+ * are host memory.  Synchronous.  Device-resident XR is also accepted, in
+ * which case only B and snp_status are copied.
+ */
+gls_status_t gls_solve_stream(gls_plan_t plan, const int8_t* XR, int64_t ldxr, int64_t m,
+                              double* B, int64_t ldb, int32_t* snp_status);
+
+/* Waits for all work of the plan (all its streams).  */
+gls_status_t gls_synchronize(gls_plan_t plan);
+
+/* The plan's compute stream (a cudaStream_t), for callers that order their
+ * own work after an asynchronous gls_solve_block. */
+void* gls_plan_stream(gls_plan_t plan);
+
+/* Frees every resource of the plan (after waiting for its work).  NULL is OK. */
+gls_status_t gls_destroy(gls_plan_t plan);
+
+/* Device bytes a plan with this description allocates (0 for an invalid one). */
+size_t gls_plan_footprint_bytes(const gls_plan_desc_t* desc);
+
+/* Static, NUL-terminated name of a status code. */
+const char* gls_status_string(gls_status_t status);
+
+/* One-line description of the last failure on the calling thread ("" if none). */
+const char* gls_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t gls_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GLS_GB300_H */

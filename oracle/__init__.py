@@ -26,9 +26,12 @@ _lock = threading.Lock()
 _lib = None
 
 # Pivot thresholds for the p x p solve (pivot d_j <= TAU * S_jj marks S_i as
-# not SPD).  FP64: 64 machine epsilons.  Mixed precision: 2^-16, the level at
-# which the reduced-precision Gram entries can no longer decide the sign.
-TAU_FP64 = 64.0 * np.finfo(np.float64).eps
+# not SPD).  d_j / S_jj is the fraction of column j's weight left after the
+# earlier columns are projected out: about 1/3 or more for a real SNP against
+# an intercept, and at rounding level (1e-14 in FP64, 1e-8 in the mixed paths)
+# for an exactly collinear one.  The thresholds sit between, with margin on
+# both sides.
+TAU_FP64 = 2.0 ** -30
 TAU_MIXED = 2.0 ** -16
 
 

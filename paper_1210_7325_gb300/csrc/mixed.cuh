@@ -1,0 +1,37 @@
+// mixed.cuh -- interface of the mixed-precision blocked triangular solve (tcgen05).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gls_gb300.h"
+
+namespace gls {
+
+struct MixedState;
+
+// Device bytes the mixed path adds to a plan.
+size_t mixed_footprint(int64_t n, int64_t npad, int p, int64_t kmax, int split_terms);
+
+// Allocates the operand slices and encodes the TMA descriptors.
+gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int64_t kmax,
+                          int precision, int split_terms, uint32_t flags, cudaStream_t st);
+void mixed_free(MixedState* ms);
+const char* mixed_last_error();
+
+// After the FP64 setup: splits the off-diagonal part of Z = L^{-1} into
+// tensor-core slices (only when new_factor), keeps the FP64 diagonal blocks,
+// and stages [X~_L | y~] in FP32 for the Gram epilogue.
+gls_status_t mixed_prepare(MixedState* ms, const double* Z, int64_t ldz, const double* Wt,
+                           int64_t ldw, bool new_factor, cudaStream_t st);
+
+// One block: converts the int8 genotypes to the operand type and runs the
+// persistent tcgen05 solve + Gram epilogue, writing FP32 partials
+// P[I][q][j] (I < npad/128, q <= p, j < k; leading dimension ldp).
+cudaError_t mixed_trsm_gram(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,
+                            float* partials, int64_t ldp, int* flags, cudaStream_t st);
+
+// Size of the FP64 diagonal blocks kept out of the tensor-core slices.
+int mixed_diag_block(const MixedState* ms);
+
+}  // namespace gls

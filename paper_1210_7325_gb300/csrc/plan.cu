@@ -1,0 +1,667 @@
+// plan.cu -- the C ABI of include/gls_gb300.h: plan objects, the setup phase,
+// one block of the SNP loop, and the double-buffered stream of Alg. 8.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "gls_gb300.h"
+#include "mixed.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+#define GLS_CUDA(expr)                                                          \
+  do {                                                                          \
+    cudaError_t e_ = (expr);                                                    \
+    if (e_ != cudaSuccess) {                                                    \
+      set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                __LINE__);                                                      \
+      return GLS_ERR_CUDA;                                                      \
+    }                                                                           \
+  } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+enum class Mem { Device, Pinned, Pageable };
+
+Mem classify(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return Mem::Pageable;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return Mem::Device;
+  if (a.type == cudaMemoryTypeHost) return Mem::Pinned;
+  return Mem::Pageable;
+}
+
+}  // namespace
+
+struct gls_plan {
+  gls_plan_desc_t desc{};
+  int device = 0;
+  int64_t n = 0, npad = 0, kmax = 0;
+  int p = 1;
+  int precision = GLS_PREC_FP64;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t ev_loaded[2]{}, ev_computed[2]{}, ev_stored[2]{}, ev_staged[2]{};
+
+  double* A = nullptr;      // L, npad x npad
+  double* Z = nullptr;      // L^{-1}, npad x npad
+  double* Wrhs = nullptr;   // [X_L | y], npad x p
+  double* Wt = nullptr;     // [X~_L | y~], npad x p
+  double* gram = nullptr;   // p x p
+  double* RTL = nullptr;    // (p-1) x (p-1)
+  double* zT = nullptr;     // p-1
+  int* flags = nullptr;     // kFlagCount
+  int8_t* xr[2]{};          // device staging of X_R blocks (ld = n)
+  double* bdev[2]{};        // p x kmax
+  int32_t* sdev[2]{};       // kmax
+  double* partials = nullptr;
+  int64_t ldp = 0;
+  int nI = 0;               // row blocks of the active path
+  int8_t* h_xr[2]{};        // pinned staging for pageable inputs
+  double* h_b[2]{};
+  int32_t* h_s[2]{};
+  gls::MixedState* mixed = nullptr;
+  bool has_factor = false;  // L and Z valid
+  bool has_xl = false;      // X_L staged
+  bool factored = false;    // ready for solves
+};
+
+namespace {
+
+size_t footprint(const gls_plan_desc_t& d, int64_t* npad_out = nullptr) {
+  const int64_t npad = gls::round_up(d.n, 128);
+  if (npad_out) *npad_out = npad;
+  const int p = d.p;
+  const int64_t kmax = d.max_block_snps;
+  size_t bytes = 0;
+  bytes += 2 * (size_t)npad * npad * sizeof(double);              // L, Z
+  bytes += 2 * (size_t)npad * p * sizeof(double);                 // Wrhs, Wt
+  bytes += (size_t)p * p * sizeof(double) + 2 * 32 * 32 * sizeof(double);
+  bytes += 64;                                                    // flags
+  bytes += 2 * (size_t)d.n * kmax;                                // X_R staging
+  bytes += 2 * (size_t)kmax * (p * sizeof(double) + sizeof(int32_t));
+  const int64_t nI = (d.precision == GLS_PREC_FP64) ? npad / gls::kT : npad / 128;
+  bytes += (size_t)nI * (p + 1) * kmax * sizeof(double);           // Gram partials
+  if (d.precision != GLS_PREC_FP64) bytes += gls::mixed_footprint(d.n, npad, p, kmax, d.split_terms);
+  return bytes;
+}
+
+gls_status_t validate_desc(const gls_plan_desc_t* d) {
+  if (!d) {
+    set_error("desc is NULL");
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (d->n < 1 || d->n > (int64_t)1 << 20) {
+    set_error("n = %lld out of range", (long long)d->n);
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (d->p < 1 || d->p > gls::kMaxP) {
+    set_error("p = %d out of range [1, %d]", d->p, gls::kMaxP);
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (d->max_block_snps < 1) {
+    set_error("max_block_snps must be >= 1");
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (d->precision != GLS_PREC_FP64 && d->precision != GLS_PREC_MIXED_BF16 &&
+      d->precision != GLS_PREC_MIXED_FP16) {
+    set_error("unknown precision %d", d->precision);
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (!(d->split_terms == 0 || d->split_terms == 2 || d->split_terms == 3)) {
+    set_error("split_terms must be 0, 2 or 3");
+    return GLS_ERR_INVALID_ARG;
+  }
+  if ((d->flags & ~GLS_FLAG_NAIVE_SPLIT) != 0) {
+    set_error("unknown flag bits 0x%x", d->flags);
+    return GLS_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < 7; ++i)
+    if (d->reserved[i] != 0) {
+      set_error("reserved fields must be 0");
+      return GLS_ERR_INVALID_ARG;
+    }
+  return GLS_OK;
+}
+
+void free_plan(gls_plan* pl) {
+  if (!pl) return;
+  if (pl->stream) cudaStreamSynchronize(pl->stream);
+  if (pl->h2d) cudaStreamSynchronize(pl->h2d);
+  if (pl->d2h) cudaStreamSynchronize(pl->d2h);
+  if (pl->mixed) gls::mixed_free(pl->mixed);
+  cudaFree(pl->A);
+  cudaFree(pl->Z);
+  cudaFree(pl->Wrhs);
+  cudaFree(pl->Wt);
+  cudaFree(pl->gram);
+  cudaFree(pl->RTL);
+  cudaFree(pl->zT);
+  cudaFree(pl->flags);
+  cudaFree(pl->partials);
+  for (int s = 0; s < 2; ++s) {
+    cudaFree(pl->xr[s]);
+    cudaFree(pl->bdev[s]);
+    cudaFree(pl->sdev[s]);
+    cudaFreeHost(pl->h_xr[s]);
+    cudaFreeHost(pl->h_b[s]);
+    cudaFreeHost(pl->h_s[s]);
+    if (pl->ev_loaded[s]) cudaEventDestroy(pl->ev_loaded[s]);
+    if (pl->ev_computed[s]) cudaEventDestroy(pl->ev_computed[s]);
+    if (pl->ev_stored[s]) cudaEventDestroy(pl->ev_stored[s]);
+    if (pl->ev_staged[s]) cudaEventDestroy(pl->ev_staged[s]);
+  }
+  if (pl->h2d) cudaStreamDestroy(pl->h2d);
+  if (pl->d2h) cudaStreamDestroy(pl->d2h);
+  if (pl->own_stream && pl->stream) cudaStreamDestroy(pl->stream);
+  cudaGetLastError();
+  delete pl;
+}
+
+template <class T>
+gls_status_t dev_alloc(T** p, size_t count) {
+  if (cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_error("cudaMalloc of %zu bytes failed", count * sizeof(T));
+    return GLS_ERR_OOM;
+  }
+  return GLS_OK;
+}
+
+template <class T>
+gls_status_t host_alloc(T** p, size_t count) {
+  if (cudaMallocHost((void**)p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_error("cudaMallocHost of %zu bytes failed", count * sizeof(T));
+    return GLS_ERR_OOM;
+  }
+  return GLS_OK;
+}
+
+#define GLS_TRY(expr)              \
+  do {                             \
+    gls_status_t s_ = (expr);      \
+    if (s_ != GLS_OK) return s_;   \
+  } while (0)
+
+gls_status_t check_flags(gls_plan* pl, int host_flags[gls::kFlagCount]) {
+  GLS_CUDA(cudaMemcpyAsync(host_flags, pl->flags, sizeof(int) * gls::kFlagCount,
+                           cudaMemcpyDeviceToHost, pl->stream));
+  GLS_CUDA(cudaStreamSynchronize(pl->stream));
+  if (host_flags[gls::kFlagKernel] & gls::kErrTimeout) {
+    set_error("a bounded device wait gave up (site %d)", host_flags[gls::kFlagWhere]);
+    return GLS_ERR_TIMEOUT;
+  }
+  if (host_flags[gls::kFlagKernel] != 0) {
+    set_error("kernel error bits 0x%x", host_flags[gls::kFlagKernel]);
+    return GLS_ERR_CUDA;
+  }
+  return GLS_OK;
+}
+
+// Solves one block whose inputs/outputs are all device resident, on pl->stream.
+gls_status_t run_block(gls_plan* pl, const int8_t* xr, int64_t ldxr, int64_t k, double* B,
+                       int64_t ldb, int32_t* status) {
+  if (k == 0) return GLS_OK;
+  if (pl->precision == GLS_PREC_FP64) {
+    GLS_CUDA(gls::launch_trsm_gram_fp64(pl->Z, pl->npad, pl->n, pl->npad, xr, ldxr, k, pl->Wt,
+                                        pl->npad, pl->p, pl->partials, pl->ldp, pl->stream));
+    gls::launch_assemble_solve(pl->partials, pl->ldp, pl->nI, pl->p, k, pl->RTL, pl->zT,
+                               gls::kTauFP64, B, ldb, status, pl->stream);
+  } else {
+    float* pf = reinterpret_cast<float*>(pl->partials);
+    GLS_CUDA(gls::mixed_trsm_gram(pl->mixed, xr, ldxr, k, pf, pl->ldp, pl->flags, pl->stream));
+    gls::launch_assemble_solve_f32(pf, pl->ldp, pl->nI, pl->p, k, pl->RTL, pl->zT,
+                                   gls::kTauMixed, B, ldb, status, pl->stream);
+  }
+  GLS_CUDA(cudaGetLastError());
+  return GLS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t gls_version(void) { return 100; }
+
+const char* gls_last_error(void) { return g_last_error.c_str(); }
+
+const char* gls_status_string(gls_status_t s) {
+  switch (s) {
+    case GLS_OK: return "GLS_OK";
+    case GLS_ERR_INVALID_ARG: return "GLS_ERR_INVALID_ARG";
+    case GLS_ERR_NOT_SPD: return "GLS_ERR_NOT_SPD";
+    case GLS_ERR_OOM: return "GLS_ERR_OOM";
+    case GLS_ERR_CUDA: return "GLS_ERR_CUDA";
+    case GLS_ERR_TIMEOUT: return "GLS_ERR_TIMEOUT";
+    case GLS_ERR_STATE: return "GLS_ERR_STATE";
+    case GLS_ERR_UNSUPPORTED: return "GLS_ERR_UNSUPPORTED";
+    case GLS_ERR_COVARIATES_SINGULAR: return "GLS_ERR_COVARIATES_SINGULAR";
+  }
+  return "GLS_ERR_UNKNOWN";
+}
+
+size_t gls_plan_footprint_bytes(const gls_plan_desc_t* desc) {
+  if (validate_desc(desc) != GLS_OK) return 0;
+  return footprint(*desc);
+}
+
+gls_status_t gls_plan_create(const gls_plan_desc_t* desc, gls_plan_t* out) {
+  g_last_error.clear();
+  if (!out) {
+    set_error("out is NULL");
+    return GLS_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  GLS_TRY(validate_desc(desc));
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    set_error("no CUDA device");
+    return GLS_ERR_UNSUPPORTED;
+  }
+  if (desc->device < 0 || desc->device >= ndev) {
+    set_error("device %d out of range", desc->device);
+    return GLS_ERR_INVALID_ARG;
+  }
+  DeviceGuard guard(desc->device);
+  if (!guard.ok) {
+    set_error("cudaSetDevice(%d) failed", desc->device);
+    return GLS_ERR_CUDA;
+  }
+  cudaDeviceProp prop;
+  GLS_CUDA(cudaGetDeviceProperties(&prop, desc->device));
+  if (!(prop.major == 10 && prop.minor == 3)) {
+    set_error("device %d is sm_%d%d; this build targets sm_103a", desc->device, prop.major,
+              prop.minor);
+    return GLS_ERR_UNSUPPORTED;
+  }
+  gls_plan* pl = new gls_plan();
+  pl->desc = *desc;
+  pl->device = desc->device;
+  pl->n = desc->n;
+  pl->p = desc->p;
+  pl->kmax = desc->max_block_snps;
+  pl->precision = desc->precision;
+  footprint(*desc, &pl->npad);
+  const int64_t npad = pl->npad, n = pl->n, kmax = pl->kmax;
+  const int p = pl->p;
+  pl->nI = (int)((pl->precision == GLS_PREC_FP64) ? npad / gls::kT : npad / 128);
+  pl->ldp = kmax;
+
+  auto fail = [&](gls_status_t s) {
+    free_plan(pl);
+    return s;
+  };
+  if (desc->stream) {
+    pl->stream = (cudaStream_t)desc->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&pl->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      set_error("cudaStreamCreate failed");
+      return fail(GLS_ERR_CUDA);
+    }
+    pl->own_stream = true;
+  }
+  if (cudaStreamCreateWithFlags(&pl->h2d, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&pl->d2h, cudaStreamNonBlocking) != cudaSuccess) {
+    set_error("cudaStreamCreate failed");
+    return fail(GLS_ERR_CUDA);
+  }
+  for (int s = 0; s < 2; ++s) {
+    if (cudaEventCreateWithFlags(&pl->ev_loaded[s], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pl->ev_computed[s], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pl->ev_stored[s], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pl->ev_staged[s], cudaEventDisableTiming) != cudaSuccess) {
+      set_error("cudaEventCreate failed");
+      return fail(GLS_ERR_CUDA);
+    }
+  }
+  gls_status_t st;
+  if ((st = dev_alloc(&pl->A, (size_t)npad * npad)) != GLS_OK) return fail(st);
+  if ((st = dev_alloc(&pl->Z, (size_t)npad * npad)) != GLS_OK) return fail(st);
+  if ((st = dev_alloc(&pl->Wrhs, (size_t)npad * p)) != GLS_OK) return fail(st);
+  if ((st = dev_alloc(&pl->Wt, (size_t)npad * p)) != GLS_OK) return fail(st);
+  if ((st = dev_alloc(&pl->gram, (size_t)p * p)) != GLS_OK) return fail(st);
+  if ((st = dev_alloc(&pl->RTL, (size_t)32 * 32)) != GLS_OK) return fail(st);
+  if ((st = dev_alloc(&pl->zT, (size_t)32)) != GLS_OK) return fail(st);
+  if ((st = dev_alloc(&pl->flags, (size_t)gls::kFlagCount)) != GLS_OK) return fail(st);
+  if ((st = dev_alloc(&pl->partials, (size_t)pl->nI * (p + 1) * kmax)) != GLS_OK) return fail(st);
+  for (int s = 0; s < 2; ++s) {
+    if ((st = dev_alloc(&pl->xr[s], (size_t)n * kmax)) != GLS_OK) return fail(st);
+    if ((st = dev_alloc(&pl->bdev[s], (size_t)p * kmax)) != GLS_OK) return fail(st);
+    if ((st = dev_alloc(&pl->sdev[s], (size_t)kmax)) != GLS_OK) return fail(st);
+  }
+  if (cudaMemsetAsync(pl->Wrhs, 0, sizeof(double) * npad * p, pl->stream) != cudaSuccess ||
+      cudaMemsetAsync(pl->flags, 0, sizeof(int) * gls::kFlagCount, pl->stream) != cudaSuccess) {
+    set_error("cudaMemset failed");
+    return fail(GLS_ERR_CUDA);
+  }
+  if (pl->precision != GLS_PREC_FP64) {
+    if ((st = gls::mixed_create(&pl->mixed, n, npad, p, kmax, pl->precision, desc->split_terms,
+                                desc->flags, pl->stream)) != GLS_OK) {
+      set_error("%s", gls::mixed_last_error());
+      return fail(st);
+    }
+  }
+  if (cudaStreamSynchronize(pl->stream) != cudaSuccess) {
+    set_error("plan setup failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return fail(GLS_ERR_CUDA);
+  }
+  *out = pl;
+  return GLS_OK;
+}
+
+gls_status_t gls_factor(gls_plan_t pl, const double* M, int64_t ldm, const double* XL,
+                        int64_t ldxl, const double* y, int64_t* info) {
+  g_last_error.clear();
+  if (info) *info = 0;
+  if (!pl) {
+    set_error("plan is NULL");
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (!y) {
+    set_error("y is NULL");
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (M && ldm < pl->n) {
+    set_error("ldm < n");
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (!M && !pl->has_factor) {
+    set_error("M == NULL but no earlier factor to keep");
+    return GLS_ERR_STATE;
+  }
+  if (pl->p > 1) {
+    if (XL && ldxl < pl->n) {
+      set_error("ldxl < n");
+      return GLS_ERR_INVALID_ARG;
+    }
+    if (!XL && !pl->has_xl) {
+      set_error("XL is NULL but p > 1 and no earlier X_L to keep");
+      return GLS_ERR_INVALID_ARG;
+    }
+  }
+  DeviceGuard guard(pl->device);
+  pl->factored = false;
+  const int64_t n = pl->n, npad = pl->npad;
+  const int p = pl->p;
+  cudaStream_t st = pl->stream;
+  GLS_CUDA(cudaMemsetAsync(pl->flags, 0, sizeof(int) * gls::kFlagCount, st));
+  if (M) {
+    pl->has_factor = false;
+    GLS_CUDA(cudaMemcpy2DAsync(pl->A, npad * sizeof(double), M, ldm * sizeof(double),
+                               n * sizeof(double), n, cudaMemcpyDefault, st));
+    gls::launch_pad_lower(pl->A, npad, n, npad, st);
+    gls::launch_identity(pl->Z, npad, npad, st);
+    GLS_CUDA(gls::potrf_trtri_fp64(pl->A, pl->Z, npad, npad, pl->flags, st));
+  }
+  if (p > 1 && XL) {
+    GLS_CUDA(cudaMemcpy2DAsync(pl->Wrhs, npad * sizeof(double), XL, ldxl * sizeof(double),
+                               n * sizeof(double), p - 1, cudaMemcpyDefault, st));
+    pl->has_xl = true;
+  }
+  GLS_CUDA(cudaMemcpyAsync(pl->Wrhs + (int64_t)(p - 1) * npad, y, n * sizeof(double),
+                           cudaMemcpyDefault, st));
+  gls::launch_whiten(pl->Z, npad, n, npad, pl->Wrhs, npad, p, pl->Wt, npad, pl->flags, st);
+  gls::launch_fixed_gram(pl->Wt, npad, n, p, pl->gram, st);
+  if (p > 1) gls::launch_small_chol(pl->gram, p, pl->RTL, pl->zT, pl->flags, st);
+  GLS_CUDA(cudaGetLastError());
+  int hf[gls::kFlagCount];
+  GLS_TRY(check_flags(pl, hf));
+  if (hf[gls::kFlagPotrf] != 0) {
+    if (info) *info = hf[gls::kFlagPotrf];
+    set_error("M is not positive definite (pivot %d)", hf[gls::kFlagPotrf]);
+    return GLS_ERR_NOT_SPD;
+  }
+  pl->has_factor = true;
+  if (hf[gls::kFlagSTL] != 0) {
+    if (info) *info = hf[gls::kFlagSTL];
+    set_error("X~_L^T X~_L is not positive definite (pivot %d)", hf[gls::kFlagSTL]);
+    return GLS_ERR_COVARIATES_SINGULAR;
+  }
+  if (pl->precision != GLS_PREC_FP64) {
+    GLS_TRY(gls::mixed_prepare(pl->mixed, pl->Z, npad, pl->Wt, npad, M != nullptr, st));
+    GLS_TRY(check_flags(pl, hf));
+  }
+  pl->factored = true;
+  return GLS_OK;
+}
+
+gls_status_t gls_solve_block(gls_plan_t pl, const int8_t* XR, int64_t ldxr, int64_t k,
+                             double* B, int64_t ldb, int32_t* snp_status) {
+  g_last_error.clear();
+  if (!pl) {
+    set_error("plan is NULL");
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (!pl->factored) {
+    set_error("gls_solve_block before a successful gls_factor");
+    return GLS_ERR_STATE;
+  }
+  if (k < 0 || k > pl->kmax) {
+    set_error("k = %lld outside [0, max_block_snps = %lld]", (long long)k, (long long)pl->kmax);
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (k == 0) return GLS_OK;
+  if (!XR || !B || ldxr < pl->n || ldb < pl->p) {
+    set_error("bad XR/B pointer or leading dimension");
+    return GLS_ERR_INVALID_ARG;
+  }
+  DeviceGuard guard(pl->device);
+  const Mem mx = classify(XR), mb = classify(B);
+  const Mem ms = snp_status ? classify(snp_status) : Mem::Device;
+  cudaStream_t st = pl->stream;
+  const int8_t* xin = XR;
+  int64_t ldin = ldxr;
+  if (mx != Mem::Device) {
+    GLS_CUDA(cudaMemcpy2DAsync(pl->xr[0], pl->n, XR, ldxr, pl->n, k, cudaMemcpyHostToDevice, st));
+    xin = pl->xr[0];
+    ldin = pl->n;
+  }
+  double* bout = (mb == Mem::Device) ? B : pl->bdev[0];
+  const int64_t ldout = (mb == Mem::Device) ? ldb : pl->p;
+  int32_t* sout = snp_status ? ((ms == Mem::Device) ? snp_status : pl->sdev[0]) : nullptr;
+  GLS_TRY(run_block(pl, xin, ldin, k, bout, ldout, sout));
+  const bool sync = (mx != Mem::Device) || (mb != Mem::Device) || (ms != Mem::Device);
+  if (mb != Mem::Device)
+    GLS_CUDA(cudaMemcpy2DAsync(B, ldb * sizeof(double), bout, pl->p * sizeof(double),
+                               pl->p * sizeof(double), k, cudaMemcpyDeviceToHost, st));
+  if (snp_status && ms != Mem::Device)
+    GLS_CUDA(cudaMemcpyAsync(snp_status, sout, k * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  if (sync) {
+    int hf[gls::kFlagCount];
+    GLS_TRY(check_flags(pl, hf));
+  }
+  return GLS_OK;
+}
+
+gls_status_t gls_solve_stream(gls_plan_t pl, const int8_t* XR, int64_t ldxr, int64_t m,
+                              double* B, int64_t ldb, int32_t* snp_status) {
+  g_last_error.clear();
+  if (!pl) {
+    set_error("plan is NULL");
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (!pl->factored) {
+    set_error("gls_solve_stream before a successful gls_factor");
+    return GLS_ERR_STATE;
+  }
+  if (m < 0) {
+    set_error("m < 0");
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (m == 0) return GLS_OK;
+  if (!XR || !B || ldxr < pl->n || ldb < pl->p) {
+    set_error("bad XR/B pointer or leading dimension");
+    return GLS_ERR_INVALID_ARG;
+  }
+  DeviceGuard guard(pl->device);
+  const int64_t n = pl->n, kmax = pl->kmax;
+  const int p = pl->p;
+  const Mem mx = classify(XR), mb = classify(B);
+  const Mem ms = snp_status ? classify(snp_status) : Mem::Device;
+
+  // Block schedule: a short first block (its load is not overlapped), then
+  // doubling up to max_block_snps (Section 4.3).
+  std::vector<std::pair<int64_t, int64_t>> blocks;
+  {
+    int64_t kb = std::min<int64_t>(kmax, std::max<int64_t>(256, kmax / 8));
+    for (int64_t s0 = 0; s0 < m;) {
+      const int64_t kk = std::min<int64_t>(kb, m - s0);
+      blocks.emplace_back(s0, kk);
+      s0 += kk;
+      kb = std::min<int64_t>(kmax, kb * 2);
+    }
+  }
+  const bool pageable_in = (mx == Mem::Pageable);
+  const bool out_b_host = (mb != Mem::Device);
+  const bool out_s_host = snp_status && (ms != Mem::Device);
+  const bool pageable_out = (mb == Mem::Pageable) || (snp_status && ms == Mem::Pageable);
+  for (int s = 0; s < 2; ++s) {
+    if (pageable_in && !pl->h_xr[s]) GLS_TRY(host_alloc(&pl->h_xr[s], (size_t)n * kmax));
+    if (pageable_out && !pl->h_b[s]) {
+      GLS_TRY(host_alloc(&pl->h_b[s], (size_t)p * kmax));
+      GLS_TRY(host_alloc(&pl->h_s[s], (size_t)kmax));
+    }
+  }
+  cudaStream_t cs = pl->stream;
+  // Order the side streams after any earlier work on the compute stream.
+  cudaEvent_t ev0 = pl->ev_computed[1];
+  GLS_CUDA(cudaEventRecord(ev0, cs));
+  GLS_CUDA(cudaStreamWaitEvent(pl->h2d, ev0, 0));
+  GLS_CUDA(cudaStreamWaitEvent(pl->d2h, ev0, 0));
+  GLS_CUDA(cudaEventRecord(pl->ev_computed[0], cs));
+  GLS_CUDA(cudaEventRecord(pl->ev_stored[0], pl->d2h));
+  GLS_CUDA(cudaEventRecord(pl->ev_stored[1], pl->d2h));
+  GLS_CUDA(cudaEventRecord(pl->ev_staged[0], pl->h2d));
+  GLS_CUDA(cudaEventRecord(pl->ev_staged[1], pl->h2d));
+
+  auto issue_load = [&](size_t jb) -> gls_status_t {
+    const int s = (int)(jb % 2);
+    const int64_t s0 = blocks[jb].first, kb = blocks[jb].second;
+    // device buffer s is free once the compute of block jb-2 is done
+    GLS_CUDA(cudaStreamWaitEvent(pl->h2d, pl->ev_computed[s], 0));
+    if (!pageable_in) {
+      GLS_CUDA(cudaMemcpy2DAsync(pl->xr[s], n, XR + s0 * ldxr, ldxr, n, kb,
+                                 cudaMemcpyHostToDevice, pl->h2d));
+    } else {
+      GLS_CUDA(cudaEventSynchronize(pl->ev_staged[s]));  // pinned staging s is free
+      for (int64_t c = 0; c < kb; ++c)
+        memcpy(pl->h_xr[s] + c * n, XR + (s0 + c) * ldxr, (size_t)n);
+      GLS_CUDA(cudaMemcpyAsync(pl->xr[s], pl->h_xr[s], (size_t)n * kb, cudaMemcpyHostToDevice,
+                               pl->h2d));
+      GLS_CUDA(cudaEventRecord(pl->ev_staged[s], pl->h2d));
+    }
+    GLS_CUDA(cudaEventRecord(pl->ev_loaded[s], pl->h2d));
+    return GLS_OK;
+  };
+  auto finish_host = [&](size_t jb) -> gls_status_t {
+    if (!pageable_out) return GLS_OK;
+    const int s = (int)(jb % 2);
+    const int64_t s0 = blocks[jb].first, kb = blocks[jb].second;
+    GLS_CUDA(cudaEventSynchronize(pl->ev_stored[s]));
+    if (mb == Mem::Pageable)
+      for (int64_t c = 0; c < kb; ++c)
+        memcpy(B + (s0 + c) * ldb, pl->h_b[s] + c * p, sizeof(double) * p);
+    if (snp_status && ms == Mem::Pageable)
+      memcpy(snp_status + s0, pl->h_s[s], sizeof(int32_t) * kb);
+    return GLS_OK;
+  };
+
+  if (mx != Mem::Device) GLS_TRY(issue_load(0));
+  for (size_t jb = 0; jb < blocks.size(); ++jb) {
+    const int s = (int)(jb % 2);
+    const int64_t s0 = blocks[jb].first, kb = blocks[jb].second;
+    if (mx != Mem::Device && jb + 1 < blocks.size()) GLS_TRY(issue_load(jb + 1));
+    const int8_t* xin = (mx == Mem::Device) ? XR + s0 * ldxr : pl->xr[s];
+    const int64_t ldin = (mx == Mem::Device) ? ldxr : n;
+    if (mx != Mem::Device) GLS_CUDA(cudaStreamWaitEvent(cs, pl->ev_loaded[s], 0));
+    GLS_CUDA(cudaStreamWaitEvent(cs, pl->ev_stored[s], 0));  // output slot s copied out
+    double* bout = out_b_host ? pl->bdev[s] : B + s0 * ldb;
+    const int64_t ldout = out_b_host ? p : ldb;
+    int32_t* sout = snp_status ? (out_s_host ? pl->sdev[s] : snp_status + s0) : nullptr;
+    GLS_TRY(run_block(pl, xin, ldin, kb, bout, ldout, sout));
+    GLS_CUDA(cudaEventRecord(pl->ev_computed[s], cs));
+    if (out_b_host || out_s_host) {
+      GLS_CUDA(cudaStreamWaitEvent(pl->d2h, pl->ev_computed[s], 0));
+      if (out_b_host) {
+        if (mb == Mem::Pinned)
+          GLS_CUDA(cudaMemcpy2DAsync(B + s0 * ldb, ldb * sizeof(double), bout, p * sizeof(double),
+                                     p * sizeof(double), kb, cudaMemcpyDeviceToHost, pl->d2h));
+        else
+          GLS_CUDA(cudaMemcpyAsync(pl->h_b[s], bout, sizeof(double) * p * kb,
+                                   cudaMemcpyDeviceToHost, pl->d2h));
+      }
+      if (out_s_host) {
+        int32_t* dst = (ms == Mem::Pinned) ? snp_status + s0 : pl->h_s[s];
+        GLS_CUDA(cudaMemcpyAsync(dst, sout, sizeof(int32_t) * kb, cudaMemcpyDeviceToHost,
+                                 pl->d2h));
+      }
+      GLS_CUDA(cudaEventRecord(pl->ev_stored[s], pl->d2h));
+    }
+    if (jb >= 1) GLS_TRY(finish_host(jb - 1));
+  }
+  GLS_TRY(finish_host(blocks.size() - 1));
+  GLS_CUDA(cudaStreamSynchronize(pl->h2d));
+  GLS_CUDA(cudaStreamSynchronize(pl->d2h));
+  int hf[gls::kFlagCount];
+  GLS_TRY(check_flags(pl, hf));
+  return GLS_OK;
+}
+
+gls_status_t gls_synchronize(gls_plan_t pl) {
+  g_last_error.clear();
+  if (!pl) {
+    set_error("plan is NULL");
+    return GLS_ERR_INVALID_ARG;
+  }
+  DeviceGuard guard(pl->device);
+  GLS_CUDA(cudaStreamSynchronize(pl->h2d));
+  GLS_CUDA(cudaStreamSynchronize(pl->d2h));
+  int hf[gls::kFlagCount];
+  return check_flags(pl, hf);
+}
+
+void* gls_plan_stream(gls_plan_t pl) { return pl ? (void*)pl->stream : nullptr; }
+
+gls_status_t gls_destroy(gls_plan_t pl) {
+  g_last_error.clear();
+  if (!pl) return GLS_OK;
+  DeviceGuard guard(pl->device);
+  free_plan(pl);
+  return GLS_OK;
+}
+
+}  // extern "C"

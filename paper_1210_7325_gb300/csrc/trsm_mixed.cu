@@ -1,0 +1,629 @@
+// trsm_mixed.cu -- mixed-precision blocked triangular solve of a block of SNP
+// columns on tcgen05 tensor cores, with the Gram epilogue fused in
+// (Alg. 5 lines 3 and 8-10; the grouped TRSM of Section 2).
+//
+// Blocked form.  With Z = L^{-1} (binary64, from the setup),
+//     x~_I = Z_II x_I + sum_{K<I} Z_IK x_K,
+// i.e. L_KK^{-1} applied to the diagonal block plus the off-diagonal updates.
+// The genotype codes x are small integers, exact in BF16/FP16, so only Z is
+// split.  For every row r of Z the entries left of its nd x nd diagonal block
+// are written as
+//     Z_rc = u_r (H_rc + R1_rc + R2_rc),   u_r = 2^(E_r - B),
+// where 2^E_r bounds the row's largest such |Z_rc|, H_rc = rint(Z_rc / u_r) is an
+// integer of at most B bits (B = 7 for BF16, 10 for FP16) and R1, R2 are the
+// first two 16-bit float terms of the remainder (|R| <= 1/2).  Products of H
+// with genotype codes are integers, so their FP32 tensor-core sum is exact
+// while it stays below 2^24 in magnitude (any n <= 65536 for |x| <= 2 with
+// BF16); the remainder terms are 2^-B smaller, so FP32 rounding in their sum
+// is negligible.  Slice H accumulates in one TMEM accumulator, R1 + R2 in a
+// second one.  The epilogue forms
+//     x~_r = u_r (acc_H + acc_R) + sum_{c in diag block} Z_rc x_c    (that sum in FP64)
+// and reduces the Gram partials of Fig. 1 over the tile's 128 rows:
+//     P[I][q][j] = sum_r W(r, q) x~(r, j) (q < p),  P[I][p][j] = sum_r x~(r, j)^2.
+//
+// Kernel shape (one persistent CTA per SM, 192 threads):
+//   warp 0      TMA producer: A slices of Z (128 x 64 each) and the 128-SNP x 64
+//               genotype tile per stage, 128-byte swizzled, one mbarrier per stage
+//   warp 1      TMEM allocator and the single thread issuing tcgen05.mma
+//               (M = 128, N = 128, K = 16) into two double-buffered accumulator pairs
+//   warps 2-5   epilogue: tcgen05.ld of the accumulators, FP64 diagonal block,
+//               Gram reduction, FP32 partial write-out
+// Work items (row block I, SNP tile J) are visited heaviest row block first;
+// consecutive CTAs share I, so the Z slices of a row block are read from HBM
+// once and served to the other CTAs from L2.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <string>
+
+#include "common.cuh"
+#include "mixed.cuh"
+#include "sm100.cuh"
+
+namespace gls {
+
+using namespace sm100;
+
+namespace {
+
+constexpr int BM = 128;                 // rows of x~ per tile (TMEM lanes)
+constexpr int BN = 128;                 // SNPs per tile (accumulator columns)
+constexpr int BK = 64;                  // K per stage: 64 x 16-bit = one 128-byte swizzle row
+constexpr int kTileBytes = BM * BK * 2;  // one A slice or the B tile per stage
+constexpr int kThreads = 192;
+constexpr uint32_t kTmemCols = 512;     // 2 buffers x (acc_H + acc_R) x 128 columns
+constexpr int kMaxDynSmem = 232448;     // 227 KB
+constexpr int kDiag = 4;                // nd: FP64 diagonal block edge
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // bounded waits give up after 1 s
+constexpr uint64_t kDrainLimitNs = 100000000ull;
+
+thread_local std::string g_err;
+
+struct KParams {
+  const int8_t* x8;
+  int64_t ldx8;
+  int64_t n, k;
+  int nI, nJ, p, S, stages;
+  uint32_t idesc;
+  const float* rowscale;  // u_r
+  const double* diagZ;    // npad x kDiag
+  const float* W32;       // npad x p, row-major
+  float* P;
+  int64_t ldp;
+  int* flags;
+  uint32_t off_T, off_W, off_tab, off_bar, stage_bytes;
+};
+
+__device__ void raise_error(int* flags, int site) {
+  atomicOr(&flags[kFlagKernel], kErrTimeout);
+  atomicExch(&flags[kFlagWhere], site);
+}
+
+// True when every one of the 128 epilogue threads passes ok = true (named barrier 1).
+__device__ __forceinline__ bool epilogue_all(bool ok) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, 1, 128, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)ok)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ bool wait_drain(uint64_t* bar, uint32_t parity) {
+  volatile int never = 0;
+  return mbar_wait_bounded(bar, parity, &never, kDrainLimitNs);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    trsm_gram_mixed_kernel(const __grid_constant__ CUtensorMap tmA,
+                           const __grid_constant__ CUtensorMap tmB, const KParams kp) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + kp.off_bar);
+  uint64_t* empty = full + kp.stages;
+  uint64_t* tfull = empty + kp.stages;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* T = reinterpret_cast<float*>(base + kp.off_T);
+  float* Ws = reinterpret_cast<float*>(base + kp.off_W);
+  double* dtab = reinterpret_cast<double*>(base + kp.off_tab);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int S = kp.S, stages = kp.stages;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp >= 2)
+    for (int i = threadIdx.x - 64; i < 256; i += 128) dtab[i] = (double)(int8_t)(uint8_t)i;
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, kTmemCols);
+    tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int total = kp.nI * kp.nJ;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        const int I = kp.nI - 1 - t / kp.nJ, J = t % kp.nJ;
+        const int kblocks = 2 * (I + 1);
+        for (int kb = 0; kb < kblocks; ++kb, ++g) {
+          const int st = (int)(g % stages);
+          const uint32_t w = g / stages;
+          if (!mbar_wait_bounded(&empty[st], (w & 1) ^ 1, abort_flag, kWaitLimitNs)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&full[st], (uint32_t)(S + 1) * kTileBytes);
+          uint8_t* sb = base + (size_t)st * kp.stage_bytes;
+          for (int s = 0; s < S; ++s)
+            tma_load_3d(sb + s * kTileBytes, &tmA, &full[st], kb * BK, I * BM, s);
+          tma_load_2d(sb + S * kTileBytes, &tmB, &full[st], kb * BK, J * BN);
+        }
+      }
+      if (!ok) {
+        raise_error(kp.flags, 1);
+        // let the loads already issued land before the CTA's shared memory goes away
+        const uint32_t first = g > (uint32_t)stages ? g - stages : 0;
+        for (uint32_t g2 = first; g2 < g; ++g2)
+          wait_drain(&full[g2 % stages], (g2 / stages) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      int it = 0;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
+        const int I = kp.nI - 1 - t / kp.nJ;
+        const int kblocks = 2 * (I + 1);
+        const int buf = it & 1;
+        const uint32_t u = (uint32_t)it >> 1;
+        if (!mbar_wait_bounded(&tempty[buf], (u & 1) ^ 1, abort_flag, kWaitLimitNs)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dH = tmem + (uint32_t)buf * 256u;
+        const uint32_t dR = dH + 128u;
+        for (int kb = 0; kb < kblocks; ++kb, ++g) {
+          const int st = (int)(g % stages);
+          const uint32_t w = g / stages;
+          if (!mbar_wait_bounded(&full[st], w & 1, abort_flag, kWaitLimitNs)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(base + (size_t)st * kp.stage_bytes);
+          const uint32_t sbB = sa + (uint32_t)S * kTileBytes;
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t bdesc = umma_desc_sw128(sbB + kk * 32);
+            const uint32_t first = (kb | kk) != 0;
+            umma_f16(dH, umma_desc_sw128(sa + kk * 32), bdesc, kp.idesc, first);
+            for (int s = 1; s < S; ++s)
+              umma_f16(dR, umma_desc_sw128(sa + s * kTileBytes + kk * 32), bdesc, kp.idesc,
+                       first | (s > 1));
+          }
+          umma_commit(&empty[st]);
+        }
+        if (ok) umma_commit(&tfull[buf]);
+      }
+      if (!ok) raise_error(kp.flags, 2);
+      // every issued MMA completes before the accumulators are released
+      umma_commit(drain);
+      wait_drain(drain, 0);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int quarter = warp & 3;            // TMEM lanes this warp may read
+    const int row = quarter * 32 + lane;     // row of the tile owned by this thread
+    const int et = threadIdx.x - 64;         // 0..127
+    const int gj = et >> 2, gg = et & 3;     // Gram mapping: SNP column, row group
+    const int p = kp.p;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    int it = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
+      const int I = kp.nI - 1 - t / kp.nJ, J = t % kp.nJ;
+      const int buf = it & 1;
+      const uint32_t u = (uint32_t)it >> 1;
+      const int64_t r = (int64_t)I * BM + row;
+      const float ur = kp.rowscale[r];
+      double dz[kDiag];
+#pragma unroll
+      for (int q = 0; q < kDiag; ++q) dz[q] = kp.diagZ[r * kDiag + q];
+      const int64_t r0 = r - (r % kDiag);
+      for (int q = 0; q < p; ++q) Ws[row * p + q] = kp.W32[r * p + q];
+      const bool got = mbar_wait_bounded(&tfull[buf], u & 1, abort_flag, kWaitLimitNs);
+      if (!epilogue_all(got)) {  // all 128 threads leave together
+        if (!got && lane == 0) raise_error(kp.flags, 3);
+        break;
+      }
+      tc_fence_after();
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t aH[32], aR[32];
+        tmem_ld32(lane_base + (uint32_t)buf * 256u + (uint32_t)c * 32u, aH);
+        tmem_ld32(lane_base + (uint32_t)buf * 256u + 128u + (uint32_t)c * 32u, aR);
+        tmem_ld_wait(aH);
+        tmem_ld_fence(aR);
+        if (c == BN / 32 - 1) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[buf]);
+        }
+        const int64_t jbase = (int64_t)J * BN + c * 32;
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+          const int64_t j = jbase + jj;
+          double dg = 0.0;
+          if (j < kp.k) {
+            const int8_t* xc = kp.x8 + j * kp.ldx8 + r0;
+#pragma unroll
+            for (int q = 0; q < kDiag; ++q)
+              if (r0 + q < kp.n) dg = fma(dz[q], dtab[(uint8_t)xc[q]], dg);
+          }
+          const float v = (__uint_as_float(aH[jj]) + __uint_as_float(aR[jj])) * ur + (float)dg;
+          T[row * 32 + (jj ^ lane)] = v;
+        }
+        named_barrier_sync(1, 128);
+        float acc[kMaxP + 1];
+#pragma unroll
+        for (int q = 0; q <= kMaxP; ++q) acc[q] = 0.f;
+        for (int i = 0; i < BM / 4; ++i) {
+          const int rr = gg + 4 * i;
+          const float x = T[rr * 32 + (gj ^ (rr & 31))];
+#pragma unroll
+          for (int q = 0; q < kMaxP; ++q)
+            if (q < p) acc[q] = fmaf(Ws[rr * p + q], x, acc[q]);
+          acc[kMaxP] = fmaf(x, x, acc[kMaxP]);
+        }
+#pragma unroll
+        for (int q = 0; q <= kMaxP; ++q) {
+          acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 1);
+          acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 2);
+        }
+        const int64_t j = jbase + gj;
+        if (gg == 0 && j < kp.k) {
+          float* out = kp.P + (int64_t)I * (p + 1) * kp.ldp + j;
+#pragma unroll
+          for (int q = 0; q < kMaxP; ++q)
+            if (q < p) out[(int64_t)q * kp.ldp] = acc[q];
+          out[(int64_t)p * kp.ldp] = acc[kMaxP];
+        }
+        named_barrier_sync(1, 128);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, kTmemCols);
+}
+
+// X_R block (n x k int8, ldx) -> operand layout X16[j][c], c < npad (zero rows >= n).
+template <bool kBF16>
+__global__ void convert_x_kernel(const int8_t* __restrict__ x8, int64_t ldx, int64_t n,
+                                 int64_t k, int64_t npad, uint16_t* __restrict__ x16) {
+  const int64_t per_col = npad / 8;
+  const int64_t total = k * per_col;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = idx / per_col;
+    const int64_t c0 = (idx - j * per_col) * 8;
+    uint16_t v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int64_t c = c0 + e;
+      const float xf = (c < n) ? (float)x8[c + j * ldx] : 0.f;
+      v[e] = kBF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(xf))
+                   : __half_as_ushort(__float2half_rn(xf));
+    }
+    uint4 w;
+    w.x = (uint32_t)v[0] | ((uint32_t)v[1] << 16);
+    w.y = (uint32_t)v[2] | ((uint32_t)v[3] << 16);
+    w.z = (uint32_t)v[4] | ((uint32_t)v[5] << 16);
+    w.w = (uint32_t)v[6] | ((uint32_t)v[7] << 16);
+    *reinterpret_cast<uint4*>(x16 + j * npad + c0) = w;
+  }
+}
+
+template <bool kBF16>
+__device__ __forceinline__ uint16_t to16(double v) {
+  return kBF16 ? __bfloat16_as_ushort(__float2bfloat16_rn((float)v))
+               : __half_as_ushort(__float2half_rn((float)v));
+}
+template <bool kBF16>
+__device__ __forceinline__ double from16(uint16_t b) {
+  return kBF16 ? (double)__bfloat162float(__ushort_as_bfloat16(b))
+               : (double)__half2float(__ushort_as_half(b));
+}
+
+// Splits the part of each row of Z left of its diagonal block into S slices
+// (see the file header); also writes u_r and the FP64 diagonal blocks.
+// One CTA per 32-row stripe; Z is read column-major (coalesced along rows) and
+// the slices are written row-major through a shared-memory transpose.
+template <bool kBF16>
+__global__ void __launch_bounds__(256) split_kernel(const double* __restrict__ Z, int64_t ldz,
+                                                    int64_t npad, int S, int bits, int naive,
+                                                    uint16_t* __restrict__ slices,
+                                                    float* __restrict__ rowscale,
+                                                    double* __restrict__ diagZ) {
+  __shared__ double red[8][33];
+  __shared__ uint16_t sh[3][32][64 + 8];
+  const int l = threadIdx.x % 32, w = threadIdx.x / 32;
+  const int64_t r = (int64_t)blockIdx.x * 32 + l;
+  const int64_t r0 = r - (r % kDiag);
+  double m = 0.0;
+  for (int64_t c = w; c < r0; c += 8) m = fmax(m, fabs(Z[r + c * ldz]));
+  red[w][l] = m;
+  __syncthreads();
+  if (w == 0) {
+    for (int v = 1; v < 8; ++v) m = fmax(m, red[v][l]);
+    double u = 1.0;
+    if (!naive && m > 0.0) {
+      int e;
+      frexp(m, &e);  // m < 2^e
+      u = ldexp(1.0, e - bits);
+    }
+    red[0][l] = u;
+    rowscale[r] = (float)u;
+#pragma unroll
+    for (int q = 0; q < kDiag; ++q)
+      diagZ[r * kDiag + q] = (r0 + q <= r) ? Z[r + (r0 + q) * ldz] : 0.0;
+  }
+  __syncthreads();
+  const double inv_u = 1.0 / red[0][l];  // power of two: exact
+  for (int64_t c0 = 0; c0 < npad; c0 += 64) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int cc = w + 8 * e;
+      const int64_t c = c0 + cc;
+      const double z = (c < r0) ? Z[r + c * ldz] * inv_u : 0.0;
+      double h = naive ? from16<kBF16>(to16<kBF16>(z)) : rint(z);
+      const double rem = z - h;
+      const uint16_t s1 = to16<kBF16>(rem);
+      const uint16_t s2 = to16<kBF16>(rem - from16<kBF16>(s1));
+      sh[0][l][cc] = to16<kBF16>(h);
+      sh[1][l][cc] = s1;
+      sh[2][l][cc] = s2;
+    }
+    __syncthreads();
+    {
+      const int rl = threadIdx.x / 8, ch = threadIdx.x % 8;
+      const int64_t rr = (int64_t)blockIdx.x * 32 + rl;
+      for (int s = 0; s < S; ++s) {
+        uint4 v;
+        const uint16_t* src = &sh[s][rl][ch * 8];
+        v.x = (uint32_t)src[0] | ((uint32_t)src[1] << 16);
+        v.y = (uint32_t)src[2] | ((uint32_t)src[3] << 16);
+        v.z = (uint32_t)src[4] | ((uint32_t)src[5] << 16);
+        v.w = (uint32_t)src[6] | ((uint32_t)src[7] << 16);
+        *reinterpret_cast<uint4*>(slices + (size_t)s * npad * npad + rr * npad + c0 + ch * 8) = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void w32_kernel(const double* __restrict__ Wt, int64_t ldw, int64_t npad, int p,
+                           float* __restrict__ W32) {
+  const int64_t total = npad * p;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / p;
+    const int q = (int)(idx - r * p);
+    W32[idx] = (float)Wt[r + q * ldw];
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* ptr = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }
+  return fn;
+}
+
+}  // namespace
+
+struct MixedState {
+  int64_t n = 0, npad = 0, kmax = 0;
+  int p = 1, S = 3, stages = 3, bits = 7;
+  bool bf16 = true;
+  bool naive = false;
+  int num_sms = 1;
+  uint16_t* slices = nullptr;  // S x npad x npad, row-major per slice
+  float* rowscale = nullptr;   // npad
+  double* diagZ = nullptr;     // npad x kDiag
+  float* W32 = nullptr;        // npad x p
+  uint16_t* x16 = nullptr;     // kmax x npad
+  CUtensorMap tmA, tmB;
+  KParams kp{};
+  size_t smem = 0;
+};
+
+size_t mixed_footprint(int64_t n, int64_t npad, int p, int64_t kmax, int split_terms) {
+  (void)n;
+  const int S = split_terms ? split_terms : 3;
+  size_t b = (size_t)S * npad * npad * 2;
+  b += (size_t)npad * (4 + kDiag * 8 + 4 * p);
+  b += (size_t)kmax * npad * 2;
+  return b;
+}
+
+const char* mixed_last_error() { return g_err.c_str(); }
+
+int mixed_diag_block(const MixedState*) { return kDiag; }
+
+void mixed_free(MixedState* ms) {
+  if (!ms) return;
+  cudaFree(ms->slices);
+  cudaFree(ms->rowscale);
+  cudaFree(ms->diagZ);
+  cudaFree(ms->W32);
+  cudaFree(ms->x16);
+  delete ms;
+}
+
+gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int64_t kmax,
+                          int precision, int split_terms, uint32_t flags, cudaStream_t st) {
+  (void)st;
+  *out = nullptr;
+  if (npad % BM != 0) {
+    g_err = "npad must be a multiple of 128";
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (npad > (int64_t)1 << 24 || kmax > ((int64_t)1 << 31) - BN) {
+    g_err = "problem too large for 32-bit TMA coordinates";
+    return GLS_ERR_INVALID_ARG;
+  }
+  MixedState* ms = new MixedState();
+  ms->n = n;
+  ms->npad = npad;
+  ms->kmax = kmax;
+  ms->p = p;
+  ms->bf16 = (precision == GLS_PREC_MIXED_BF16);
+  ms->S = split_terms ? split_terms : 3;
+  ms->bits = ms->bf16 ? 7 : 10;
+  ms->naive = (flags & GLS_FLAG_NAIVE_SPLIT) != 0;
+  auto fail = [&](gls_status_t s, const char* msg) {
+    g_err = msg;
+    mixed_free(ms);
+    return s;
+  };
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&ms->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaMalloc(&ms->slices, (size_t)ms->S * npad * npad * 2) != cudaSuccess ||
+      cudaMalloc(&ms->rowscale, (size_t)npad * 4) != cudaSuccess ||
+      cudaMalloc(&ms->diagZ, (size_t)npad * kDiag * 8) != cudaSuccess ||
+      cudaMalloc(&ms->W32, (size_t)npad * p * 4) != cudaSuccess ||
+      cudaMalloc(&ms->x16, (size_t)kmax * npad * 2) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GLS_ERR_OOM, "cudaMalloc of the mixed-precision operands failed");
+  }
+  // Shared memory: stages of (S slices + genotype tile), then the epilogue buffers.
+  const uint32_t stage_bytes = (uint32_t)(ms->S + 1) * kTileBytes;
+  const uint32_t epi = (uint32_t)(BM * 32 * 4 + BM * p * 4 + 256 * 8);
+  const uint32_t bars = 8 * (2 * 4 + 5) + 16;
+  int stages = 4;
+  while (stages > 2 && (size_t)stages * stage_bytes + epi + bars + 1024 > (size_t)kMaxDynSmem)
+    --stages;
+  if ((size_t)stages * stage_bytes + epi + bars + 1024 > (size_t)kMaxDynSmem)
+    return fail(GLS_ERR_UNSUPPORTED, "shared-memory budget exceeded for this p and split");
+  ms->stages = stages;
+  KParams& kp = ms->kp;
+  kp.stage_bytes = stage_bytes;
+  kp.off_T = (uint32_t)stages * stage_bytes;
+  kp.off_W = kp.off_T + BM * 32 * 4;
+  kp.off_tab = kp.off_W + (uint32_t)(BM * p * 4);
+  kp.off_tab = (kp.off_tab + 7u) & ~7u;
+  kp.off_bar = kp.off_tab + 256 * 8;
+  ms->smem = (size_t)kp.off_bar + bars + 1024;
+  kp.S = ms->S;
+  kp.stages = stages;
+  kp.p = p;
+  kp.n = n;
+  kp.idesc = umma_idesc_f16(BM, BN, ms->bf16);
+  kp.rowscale = ms->rowscale;
+  kp.diagZ = ms->diagZ;
+  kp.W32 = ms->W32;
+  if (cudaFuncSetAttribute(trsm_gram_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ms->smem) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GLS_ERR_CUDA, "cudaFuncSetAttribute (shared memory) failed");
+  }
+  PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+  if (!enc) return fail(GLS_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
+  const CUtensorMapDataType dt =
+      ms->bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  {
+    cuuint64_t dims[3] = {(cuuint64_t)npad, (cuuint64_t)npad, (cuuint64_t)ms->S};
+    cuuint64_t strides[2] = {(cuuint64_t)npad * 2, (cuuint64_t)npad * npad * 2};
+    cuuint32_t box[3] = {BK, BM, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    if (enc(&ms->tmA, dt, 3, ms->slices, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return fail(GLS_ERR_CUDA, "tensor map encode (slices) failed");
+  }
+  {
+    cuuint64_t dims[2] = {(cuuint64_t)npad, (cuuint64_t)kmax};
+    cuuint64_t strides[1] = {(cuuint64_t)npad * 2};
+    cuuint32_t box[2] = {BK, BN};
+    cuuint32_t es[2] = {1, 1};
+    if (enc(&ms->tmB, dt, 2, ms->x16, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return fail(GLS_ERR_CUDA, "tensor map encode (genotypes) failed");
+  }
+  *out = ms;
+  return GLS_OK;
+}
+
+gls_status_t mixed_prepare(MixedState* ms, const double* Z, int64_t ldz, const double* Wt,
+                           int64_t ldw, bool new_factor, cudaStream_t st) {
+  if (new_factor) {
+    const unsigned grid = (unsigned)(ms->npad / 32);
+    if (ms->bf16)
+      split_kernel<true><<<grid, 256, 0, st>>>(Z, ldz, ms->npad, ms->S, ms->bits, ms->naive,
+                                               ms->slices, ms->rowscale, ms->diagZ);
+    else
+      split_kernel<false><<<grid, 256, 0, st>>>(Z, ldz, ms->npad, ms->S, ms->bits, ms->naive,
+                                                ms->slices, ms->rowscale, ms->diagZ);
+  }
+  w32_kernel<<<256, 256, 0, st>>>(Wt, ldw, ms->npad, ms->p, ms->W32);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    g_err = std::string("mixed prepare: ") + cudaGetErrorString(e);
+    return GLS_ERR_CUDA;
+  }
+  return GLS_OK;
+}
+
+cudaError_t mixed_trsm_gram(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,
+                            float* partials, int64_t ldp, int* flags, cudaStream_t st) {
+  if (k <= 0) return cudaSuccess;
+  const int64_t work = k * (ms->npad / 8);
+  const unsigned cgrid = (unsigned)std::min<int64_t>(ceil_div(work, 256), 65535 * 4);
+  if (ms->bf16)
+    convert_x_kernel<true><<<cgrid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, ms->x16);
+  else
+    convert_x_kernel<false><<<cgrid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, ms->x16);
+  KParams kp = ms->kp;
+  kp.x8 = xr;
+  kp.ldx8 = ldxr;
+  kp.k = k;
+  kp.nI = (int)(ms->npad / BM);
+  kp.nJ = (int)ceil_div(k, BN);
+  kp.P = partials;
+  kp.ldp = ldp;
+  kp.flags = flags;
+  const int total = kp.nI * kp.nJ;
+  const int grid = std::min(ms->num_sms, total);
+  trsm_gram_mixed_kernel<<<grid, kThreads, ms->smem, st>>>(ms->tmA, ms->tmB, kp);
+  return cudaGetLastError();
+}
+
+}  // namespace gls

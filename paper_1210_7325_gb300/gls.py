@@ -1,0 +1,239 @@
+"""Python binding of the C ABI in include/gls_gb300.h (argument marshalling only).
+
+Every step of the computation runs in the CUDA library ``libgls_gb300.so``;
+this module only converts arguments.  There is no fallback: if the library is
+missing or no sm_103 device is present, the calls raise.
+
+Matrices follow the ABI's column-major convention.  A numpy array must be
+Fortran-ordered; a torch tensor must have unit stride along its first axis
+(e.g. the transpose ``X.t()`` of a C-contiguous (k, n) genotype tensor is the
+column-major n x k matrix the ABI wants).  Host (numpy, CPU tensors, pinned or
+not) and device (CUDA tensors) buffers are both accepted.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgls_gb300.so")
+
+GLS_OK = 0
+STATUS_NAMES = {
+    0: "GLS_OK", 1: "GLS_ERR_INVALID_ARG", 2: "GLS_ERR_NOT_SPD", 3: "GLS_ERR_OOM",
+    4: "GLS_ERR_CUDA", 5: "GLS_ERR_TIMEOUT", 6: "GLS_ERR_STATE", 7: "GLS_ERR_UNSUPPORTED",
+    8: "GLS_ERR_COVARIATES_SINGULAR",
+}
+PRECISIONS = {"fp64": 0, "bf16": 1, "fp16": 2}
+GLS_FLAG_NAIVE_SPLIT = 1
+
+
+class GlsError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = "", info: int = 0):
+        self.status = status
+        self.info = info
+        name = STATUS_NAMES.get(status, str(status))
+        super().__init__(f"{where}: {name}" + (f" ({detail})" if detail else "") +
+                         (f" [info={info}]" if info else ""))
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("p", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("max_block_snps", ctypes.c_int64),
+        ("device", ctypes.c_int32),
+        ("split_terms", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+        ("flags", ctypes.c_uint32),
+        ("reserved", ctypes.c_int32 * 7),
+    ]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads (once) and returns the native library; raises if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"GLS CUDA library not found at {path}; build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    P = ctypes.POINTER
+    lib.gls_plan_create.argtypes = [P(PlanDesc), P(vp)]
+    lib.gls_plan_create.restype = i32
+    lib.gls_factor.argtypes = [vp, vp, i64, vp, i64, vp, P(i64)]
+    lib.gls_factor.restype = i32
+    lib.gls_solve_block.argtypes = [vp, vp, i64, i64, vp, i64, vp]
+    lib.gls_solve_block.restype = i32
+    lib.gls_solve_stream.argtypes = [vp, vp, i64, i64, vp, i64, vp]
+    lib.gls_solve_stream.restype = i32
+    lib.gls_synchronize.argtypes = [vp]
+    lib.gls_synchronize.restype = i32
+    lib.gls_plan_stream.argtypes = [vp]
+    lib.gls_plan_stream.restype = vp
+    lib.gls_destroy.argtypes = [vp]
+    lib.gls_destroy.restype = i32
+    lib.gls_plan_footprint_bytes.argtypes = [P(PlanDesc)]
+    lib.gls_plan_footprint_bytes.restype = ctypes.c_size_t
+    lib.gls_status_string.argtypes = [i32]
+    lib.gls_status_string.restype = ctypes.c_char_p
+    lib.gls_last_error.argtypes = []
+    lib.gls_last_error.restype = ctypes.c_char_p
+    lib.gls_version.argtypes = []
+    lib.gls_version.restype = i32
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().gls_last_error().decode()
+
+
+def _check(status: int, where: str, info: int = 0):
+    if status != GLS_OK:
+        raise GlsError(status, where, last_error(), info)
+
+
+def make_desc(n, p, max_block_snps, precision="fp64", device=0, stream=None, split_terms=0,
+              flags=0) -> PlanDesc:
+    d = PlanDesc()
+    d.n = int(n)
+    d.p = int(p)
+    d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    d.max_block_snps = int(max_block_snps)
+    d.device = int(device)
+    d.split_terms = int(split_terms)
+    d.stream = stream
+    d.flags = int(flags)
+    return d
+
+
+def footprint_bytes(n, p, max_block_snps, precision="fp64", split_terms=0) -> int:
+    return int(load().gls_plan_footprint_bytes(
+        ctypes.byref(make_desc(n, p, max_block_snps, precision, split_terms=split_terms))))
+
+
+# ------------------------------------------------------------------ marshalling
+def _colmajor(a, rows: int, itemsize: int, name: str):
+    """(pointer, leading dimension in elements) of a column-major matrix."""
+    if a is None:
+        return None, max(rows, 1)
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.element_size() != itemsize:
+                raise TypeError(f"{name}: element size {a.element_size()} != {itemsize}")
+            if a.dim() == 1:
+                return ctypes.c_void_p(a.data_ptr()), max(rows, 1)
+            if a.dim() != 2 or (a.shape[1] > 1 and a.stride(0) != 1):
+                raise ValueError(f"{name}: torch tensor must be column-major (stride(0) == 1)")
+            ld = a.stride(1) if a.shape[1] > 1 else max(a.shape[0], 1)
+            return ctypes.c_void_p(a.data_ptr()), ld
+    except ImportError:
+        pass
+    import numpy as np
+    if not isinstance(a, np.ndarray):
+        raise TypeError(f"{name}: expected a numpy array or torch tensor")
+    if a.itemsize != itemsize:
+        raise TypeError(f"{name}: element size {a.itemsize} != {itemsize}")
+    if a.ndim == 1:
+        if not a.flags.c_contiguous:
+            raise ValueError(f"{name}: vector must be contiguous")
+        return ctypes.c_void_p(a.ctypes.data), max(rows, 1)
+    if a.ndim != 2 or not a.flags.f_contiguous:
+        raise ValueError(f"{name}: numpy matrix must be Fortran-ordered (column-major)")
+    return ctypes.c_void_p(a.ctypes.data), max(a.shape[0], 1)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            return ctypes.c_void_p(a.data_ptr())
+    except ImportError:
+        pass
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Plan:
+    """One GLS sequence: ``factor`` (setup of Alg. 5) then ``solve_block`` /
+    ``solve_stream`` over SNP blocks.  Thin wrapper over the C ABI."""
+
+    def __init__(self, n, p, max_block_snps, precision="fp64", device=0, stream=None,
+                 split_terms=0, flags=0):
+        lib = load()
+        self.n, self.p, self.kmax = int(n), int(p), int(max_block_snps)
+        self.precision = precision
+        self._desc = make_desc(n, p, max_block_snps, precision, device, stream, split_terms,
+                               flags)
+        h = ctypes.c_void_p()
+        _check(lib.gls_plan_create(ctypes.byref(self._desc), ctypes.byref(h)), "gls_plan_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def stream(self) -> int:
+        return int(load().gls_plan_stream(self._h) or 0)
+
+    def factor(self, M, XL, y):
+        """M: n x n column-major (lower triangle read) or None to keep the previous
+        factor; XL: n x (p-1) column-major or None; y: n vector."""
+        lib = load()
+        pm, ldm = _colmajor(M, self.n, 8, "M")
+        px, ldx = _colmajor(XL, self.n, 8, "XL")
+        py, _ = _colmajor(y, self.n, 8, "y")
+        info = ctypes.c_int64(0)
+        st = lib.gls_factor(self._h, pm, ldm, px, ldx, py, ctypes.byref(info))
+        _check(st, "gls_factor", info.value)
+
+    def solve_block(self, XR, B, status=None, k=None):
+        """XR: n x k int8 column-major; B: p x k float64 column-major (output);
+        status: k int32 or None."""
+        lib = load()
+        px, ldx = _colmajor(XR, self.n, 1, "XR")
+        pb, ldb = _colmajor(B, self.p, 8, "B")
+        if k is None:
+            k = XR.shape[1] if XR.ndim == 2 else 1
+        _check(lib.gls_solve_block(self._h, px, ldx, int(k), pb, ldb, _ptr(status)),
+               "gls_solve_block")
+
+    def solve_stream(self, XR, B, status=None, m=None):
+        lib = load()
+        px, ldx = _colmajor(XR, self.n, 1, "XR")
+        pb, ldb = _colmajor(B, self.p, 8, "B")
+        if m is None:
+            m = XR.shape[1]
+        _check(lib.gls_solve_stream(self._h, px, ldx, int(m), pb, ldb, _ptr(status)),
+               "gls_solve_stream")
+
+    def synchronize(self):
+        _check(load().gls_synchronize(self._h), "gls_synchronize")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gls_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
