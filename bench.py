@@ -1,0 +1,453 @@
+#!/usr/bin/env python
+"""Benchmark: GLS solves/s for the GWAS sequence b_i = (X_i^T M^{-1} X_i)^{-1} X_i^T M^{-1} y.
+
+Default workload (the headline configuration): n = 10^4 individuals,
+p = 20 (intercept + 18 covariates + the SNP), m = 10^6 int8 SNPs, h = 0.5,
+mixed-precision path (BF16 slices of L^{-1}, tcgen05 tensor cores).  One step
+is the whole hot path over the batch: gls_factor (Cholesky of M, L^{-1},
+whitening, fixed Gram) + gls_solve_block over every SNP block, inputs resident
+in HBM.  Inputs (10 GB of genotypes) are far larger than L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line on rank 0.  ``--impl reference`` times the plain FP64
+CPU oracle on the host cores instead (bounded sample of the same workload).
+Multi-GPU runs are independent replicas (the method needs no exchange between
+SNP ranges): value = all ranks' solves / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLS solves/s at n=1e4 (mixed vs FP64 @1e-6 rel err); serve p50/p99 latency"
+UNIT = "solves/s"
+
+WORKLOADS = {
+    # name: n, p, m, h, precision, block
+    "n10000_p20_m1000000_bf16": dict(n=10000, p=20, m=1_000_000, h=0.5, precision="bf16",
+                                     block=65536, seed_offset=2),
+    "n1000_p4_m4096_fp64": dict(n=1000, p=4, m=4096, h=0.4, precision="fp64", block=4096,
+                                seed_offset=0),
+    "n1500_p4_m2500000_fp64": dict(n=1500, p=4, m=2_500_000, h=0.5, precision="fp64",
+                                   block=16384, seed_offset=1),
+}
+DEFAULT_WORKLOAD = "n10000_p20_m1000000_bf16"
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, \
+        "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_id_for(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev)
+
+
+# ----------------------------------------------------------------------------- inputs
+def make_inputs(wl, rank, torch):
+    from paper_1210_7325_gb300 import synth
+    seed = synth.BASE_SEED + wl["seed_offset"] + 1000 * rank
+    n, p, m = wl["n"], wl["p"], wl["m"]
+    M = synth.kinship_M(n, wl["h"], seed, device="cuda")
+    XL = synth.covariates(n, p, seed)
+    y = synth.phenotype(n, seed)
+    XR = synth.genotypes_torch(n, m, seed, device="cuda")  # (m, n) int8 = column-major n x m
+    return M, XL, y, XR
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args, wl, rank, world, torch, dist):
+    import numpy as np
+    from paper_1210_7325_gb300 import gls
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    n, p, m, kmax, prec = wl["n"], wl["p"], wl["m"], wl["block"], wl["precision"]
+    M, XL, y, XR = make_inputs(wl, rank, torch)
+    Md = torch.from_numpy(np.ascontiguousarray(M.T)).to(dev).t()  # column-major
+    XLd = torch.from_numpy(np.ascontiguousarray(XL.T)).to(dev).t()
+    yd = torch.from_numpy(y).to(dev)
+    B = torch.empty((m, p), dtype=torch.float64, device=dev)
+    st = torch.empty(m, dtype=torch.int32, device=dev)
+    plan = gls.Plan(n, p, kmax, precision=prec, device=dev.index)
+    stream = torch.cuda.ExternalStream(plan.stream, device=dev)
+
+    def step():
+        plan.factor(Md, XLd, yd)
+        for s0 in range(0, m, kmax):
+            k = min(kmax, m - s0)
+            plan.solve_block(XR[s0:s0 + k].t(), B[s0:s0 + k].t(), st[s0:s0 + k], k=k)
+
+    for _ in range(args.warmup):
+        step()
+    plan.synchronize()
+    plan.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_id_for(torch, dev)) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t = e0.elapsed_time(e1) / 1e3
+    stats = plan.stats()
+    bad = int((st != 0).sum().item())
+    nan = int(torch.isnan(B).any().item())
+    res = dict(time=t, stats=stats, clocks=clk.summary(), bad_status=bad, nan=nan)
+
+    # end to end through the public API with host buffers (pinned)
+    if not args.skip_e2e:
+        XRh = torch.empty((m, n), dtype=torch.int8, pin_memory=True)
+        XRh.copy_(XR)
+        Mh = torch.from_numpy(np.ascontiguousarray(M.T)).pin_memory().t()
+        XLh = torch.from_numpy(np.ascontiguousarray(XL.T)).pin_memory().t()
+        yh = torch.from_numpy(y).pin_memory()
+        Bh = torch.empty((m, p), dtype=torch.float64, pin_memory=True)
+        sh = torch.empty(m, dtype=torch.int32, pin_memory=True)
+        del XR
+        torch.cuda.empty_cache()
+
+        def e2e_step():
+            plan.factor(Mh, XLh, yh)
+            plan.solve_stream(XRh.t(), Bh.t(), sh, m=m)
+
+        for _ in range(max(1, min(args.warmup, 2))):
+            e2e_step()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        te = time.perf_counter() - t0
+        res["e2e_time"] = te
+        res["e2e_h2d"] = n * n * 8 + n * (p - 1) * 8 + n * 8 + n * m
+        res["e2e_d2h"] = p * m * 8 + 4 * m
+    plan.close()
+    return res
+
+
+def fp64_sample(wl, torch, m_sample=16384):
+    """FP64 GPU path on the same n, p over one block of SNPs (its full m would
+    take minutes at the binary64 rate of this part)."""
+    import numpy as np
+    from paper_1210_7325_gb300 import gls, synth
+    n, p = wl["n"], wl["p"]
+    seed = synth.BASE_SEED + wl["seed_offset"]
+    M = synth.kinship_M(n, wl["h"], seed, device="cuda")
+    XL = synth.covariates(n, p, seed)
+    y = synth.phenotype(n, seed)
+    XR = synth.genotypes_torch(n, m_sample, seed, device="cuda")
+    dev = torch.device("cuda")
+    Md = torch.from_numpy(np.ascontiguousarray(M.T)).to(dev).t()
+    XLd = torch.from_numpy(np.ascontiguousarray(XL.T)).to(dev).t()
+    yd = torch.from_numpy(y).to(dev)
+    B = torch.empty((m_sample, p), dtype=torch.float64, device=dev)
+    plan = gls.Plan(n, p, m_sample, precision="fp64")
+    plan.factor(Md, XLd, yd)
+    plan.solve_block(XR.t(), B.t(), None, k=m_sample)
+    plan.synchronize()
+    plan.set_timing(True)
+    plan.factor(Md, XLd, yd)
+    plan.solve_block(XR.t(), B.t(), None, k=m_sample)
+    s = plan.stats()
+    plan.close()
+    solve_s = (s["trsm_ms"] + s["solve_ms"]) / 1e3
+    factor_s = s["factor_ms"] / 1e3
+    return dict(m_sample=m_sample, factor_s=factor_s, solve_s=solve_s,
+                steady_solves_per_s=m_sample / solve_s,
+                trsm_fp64_tflops=n * n * m_sample / (s["trsm_ms"] / 1e3) / 1e12,
+                whole_job_solves_per_s_projected=wl["m"] / (factor_s + wl["m"] / m_sample * solve_s))
+
+
+def fp64_dgemm_tflops(torch):
+    a = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
+    b = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        a @ b
+    torch.cuda.synchronize()
+    best = 1e9
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record()
+        a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    return 2 * 8192 ** 3 / best / 1e12
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample(wl, s_snps, nthreads, M=None, XL=None, y=None):
+    """Times the oracle as it stands on the host: the Cholesky of M once, then
+    the per-SNP loop on s_snps SNPs.  Returns the timings and the projected
+    whole-job rate for the workload's m."""
+    import numpy as np
+    import oracle
+    from paper_1210_7325_gb300 import synth
+    n, p = wl["n"], wl["p"]
+    seed = synth.BASE_SEED + wl["seed_offset"]
+    if M is None:
+        M = synth.kinship_M(n, wl["h"], seed, device="cuda")
+        XL = synth.covariates(n, p, seed)
+        y = synth.phenotype(n, seed)
+    XR = synth.genotypes_np(n, s_snps, seed)
+    t0 = time.perf_counter()
+    L, info = oracle.potrf(M, nthreads=nthreads)
+    t1 = time.perf_counter()
+    B, st = oracle.gls_factored(L, XL, y, XR, tau=oracle.TAU_MIXED, nthreads=nthreads)
+    t2 = time.perf_counter()
+    assert info == 0
+    tf, ts = t1 - t0, t2 - t1
+    whole = wl["m"] / (tf + wl["m"] / s_snps * ts)
+    return dict(factor_s=tf, snp_s=ts, s_snps=s_snps, value=whole,
+                steady=s_snps / ts, cores=nthreads)
+
+
+def run_reference(args, wl):
+    """--impl reference: the FP64 oracle on the host cores, same metric/config."""
+    import numpy as np  # noqa: F401
+    import oracle
+    from paper_1210_7325_gb300 import synth
+    nthreads = oracle.default_threads()
+    n, p = wl["n"], wl["p"]
+    seed = synth.BASE_SEED + wl["seed_offset"]
+    try:
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+    except Exception:
+        dev = "cpu"
+    M = synth.kinship_M(n, wl["h"], seed, device=dev)
+    XL = synth.covariates(n, p, seed)
+    y = synth.phenotype(n, seed)
+    s_snps = args.ref_snps
+    for _ in range(args.warmup):
+        oracle_sample(wl, s_snps, nthreads, M, XL, y)
+    vals, steps = [], []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = oracle_sample(wl, s_snps, nthreads, M, XL, y)
+        steps.append(r)
+        vals.append(r["value"])
+    total = time.perf_counter() - t0
+    value = statistics.median(vals)
+    sample = (f"per step: oracle Cholesky of M (n={n}) + per-SNP loop on {s_snps} SNPs; "
+              f"value = m / (t_factor + m/{s_snps} * t_snps) for m={wl['m']}")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_for(wl, args),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                         "sample": sample,
+                         "factor_s": statistics.median(r["factor_s"] for r in steps),
+                         "snp_s": statistics.median(r["snp_s"] for r in steps)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_for(wl, args):
+    return {"workload": args.workload, "n": wl["n"], "p": wl["p"], "m": wl["m"], "h": wl["h"],
+            "precision": wl["precision"], "block_snps": wl["block"],
+            "l2": "inputs larger than L2 (int8 genotypes n*m bytes)",
+            "parallelism": f"replicas{args.gpus}"}
+
+
+# ----------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--cpu-snps", type=int, default=2048)
+    ap.add_argument("--ref-snps", type=int, default=1024)
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    args.warmup = max(args.warmup, 3) if args.impl == "gb300" else args.warmup
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, wl)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl")
+        dist = tdist
+
+    from paper_1210_7325_gb300 import build as gbuild
+    if rank == 0:
+        gbuild.build()
+    if dist:
+        dist.barrier()
+
+    res = run_gpu(args, wl, rank, world, torch, dist)
+    t_local = res["time"]
+    t_max = t_local
+    e2e_max = res.get("e2e_time")
+    if dist:
+        tt = torch.tensor([t_local, e2e_max or 0.0], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max, e2e_max = float(tt[0]), float(tt[1]) or None
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_src = load_peaks()
+    n, p, m = wl["n"], wl["p"], wl["m"]
+    K = args.steps
+    value = world * m * K / t_max
+    s = res["stats"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": t_max / K * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if wl["precision"] == "bf16" else ("f16" if wl["precision"] == "fp16"
+                                                          else "f64"),
+        "data": "synthetic (seeded kinship, covariates, phenotype, Binomial(2,f) genotypes)",
+        "config": config_for(wl, args),
+        "gpu_launches": int(s["launches"]),
+        "clocks": res["clocks"],
+        "steady_state": {"value": m * K / ((s["trsm_ms"] + s["convert_ms"] + s["solve_ms"]) / 1e3),
+                         "unit": UNIT, "note": "SNP loop kernels only (factor excluded)"},
+        "phase_ms_per_step": {"factor": s["factor_ms"] / K, "trsm_gram": s["trsm_ms"] / K,
+                              "convert": s["convert_ms"] / K, "solve_pxp": s["solve_ms"] / K},
+        "check": {"bad_status": res["bad_status"], "nan": res["nan"]},
+    }
+    # roofline of the dominant kernel (the blocked solve + Gram epilogue)
+    trsm_avg_s = s["trsm_ms"] / 1e3 / max(s["trsm_launches"], 1)
+    snps_per_launch = m * K / max(s["trsm_launches"], 1)
+    if wl["precision"] == "fp64":
+        dgemm = fp64_dgemm_tflops(torch)
+        flops = n * n * snps_per_launch
+        achieved = flops / trsm_avg_s / 1e12
+        line["roofline"] = {"bound": "fp64", "achieved": achieved, "peak": dgemm,
+                            "unit": "TFLOP/s", "frac": achieved / dgemm, "traffic": None,
+                            "peak_source": "measured torch.matmul float64 8192^3 in this run",
+                            "flops_per_launch": flops}
+    else:
+        S = 3
+        flops = S * n * n * snps_per_launch
+        achieved = flops / trsm_avg_s / 1e12
+        peak = peaks["bf16_tflops_sustained"]
+        line["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak,
+                            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                            "peak_source": f"{peak_src} bf16_tflops_sustained",
+                            "flops_per_launch": flops,
+                            "per_unit": f"{S} slices x n^2 tensor flops per SNP"}
+    if e2e_max:
+        line["e2e"] = {"value": world * m * K / e2e_max, "unit": UNIT,
+                       "h2d_bytes_per_step": res["e2e_h2d"], "d2h_bytes_per_step": res["e2e_d2h"]}
+    if not args.skip_fp64 and wl["precision"] != "fp64":
+        try:
+            line["fp64"] = fp64_sample(wl, torch)
+            line["fp64"]["dgemm_tflops_measured"] = fp64_dgemm_tflops(torch)
+        except Exception as ex:  # reported, not fatal
+            line["fp64"] = {"error": repr(ex)}
+    if not args.skip_cpu and world == 1:
+        import oracle
+        r = oracle_sample(wl, args.cpu_snps, oracle.default_threads())
+        line["cpu_baseline"] = {
+            "value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+            "sample": (f"oracle Cholesky of M (n={n}, {r['factor_s']:.1f} s) + per-SNP loop on "
+                       f"{r['s_snps']} SNPs ({r['snp_s']:.1f} s), projected to m={m}"),
+            "steady_state": r["steady"]}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

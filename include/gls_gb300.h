@@ -154,6 +154,28 @@ const char* gls_status_string(gls_status_t status);
 /* One-line description of the last failure on the calling thread ("" if none). */
 const char* gls_last_error(void);
 
+/*
+ * Device-time accounting for benchmarks.  With timing enabled, each kernel of
+ * the SNP loop and each whole setup phase is bracketed by CUDA events on the
+ * plan's stream, so the figures are the kernels' own device times; launches
+ * counts every kernel the plan enqueued.  gls_plan_set_timing resets the
+ * counters; gls_plan_stats synchronizes the plan's stream and sums.
+ */
+typedef struct {
+  int64_t launches;          /* kernels enqueued since the last reset                 */
+  double trsm_ms;            /* blocked triangular solve + Gram epilogue kernels     */
+  int64_t trsm_launches;
+  double convert_ms;         /* int8 -> 16-bit genotype operand kernels (mixed)      */
+  int64_t convert_launches;
+  double solve_ms;           /* p x p assembly + Cholesky solve kernels              */
+  int64_t solve_launches;
+  double factor_ms;          /* whole gls_factor setup phases                        */
+  int64_t factor_calls;
+} gls_stats_t;
+
+gls_status_t gls_plan_set_timing(gls_plan_t plan, int32_t enable);
+gls_status_t gls_plan_stats(gls_plan_t plan, gls_stats_t* out);
+
 /* Library version as major*10000 + minor*100 + patch. */
 int32_t gls_version(void);
 

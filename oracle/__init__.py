@@ -67,6 +67,9 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.gls_oracle_gls_sampled.argtypes = [i64, i32, vp, i64, vp, i64, vp, i64, vp, vp, i64,
                                            vp, i64, vp, dbl, i32]
     lib.gls_oracle_gls_sampled.restype = i64
+    lib.gls_oracle_gls_factored.argtypes = [i64, i32, vp, vp, i64, vp, i64, vp, i64, vp, i64,
+                                            vp, dbl, i32]
+    lib.gls_oracle_gls_factored.restype = i64
     return lib
 
 
@@ -112,7 +115,7 @@ def trsv(L: np.ndarray, b: np.ndarray) -> np.ndarray:
 
 def _prep(M, XL, y, XR, p):
     M = np.asfortranarray(M, dtype=np.float64)
-    n = M.shape[0]
+    n = np.asarray(XR).shape[0] if M.size == 0 else M.shape[0]
     if p > 1:
         XL = np.asfortranarray(XL, dtype=np.float64).reshape(n, p - 1, order="F")
     else:
@@ -155,3 +158,20 @@ def gls_sampled(M, XL, y, XR, idx, tau: float = TAU_FP64, nthreads: int = 1):
     if info < 0:
         raise ValueError("oracle rejected its arguments")
     return B, status, int(info)
+
+
+def gls_factored(L, XL, y, XR, tau: float = TAU_FP64, nthreads: int = 1):
+    """b_i for every column of XR given the Cholesky factor L of M (n x n,
+    lower, as returned by ``potrf``).  Returns (B, status)."""
+    L = np.asfortranarray(L, dtype=np.float64)
+    n = L.shape[0]
+    p = (0 if XL is None else np.asarray(XL).reshape(n, -1).shape[1]) + 1
+    _, _, XL, y, XR = _prep(np.zeros((n, 0)), XL, y, XR, p)
+    k = XR.shape[1]
+    B = np.full((p, k), np.nan, dtype=np.float64, order="F")
+    status = np.zeros(k, dtype=np.int32)
+    r = lib().gls_oracle_gls_factored(n, p, _ptr(L), _ptr(XL), n, _ptr(y), k, _ptr(XR), n,
+                                      _ptr(B), p, _ptr(status), float(tau), int(nthreads))
+    if r < 0:
+        raise ValueError("oracle rejected its arguments")
+    return B, status

@@ -268,36 +268,23 @@ static void* snp_worker(void* arg) {
 }
 
 /*
- * Full reference: returns 0, the 1-based failing pivot of M (B untouched), or
- * -1 on a bad argument / allocation failure.
- *   M      n x n, ldm >= n, lower triangle read
- *   XL     n x (p-1), ldxl >= n (ignored when p == 1)
- *   y      n
- *   XR     n x k int8, ldxr >= n
- *   B      p x k, ldb >= p (output)
- *   status k int32 (output, may be NULL): 0 ok, 1 S_i not SPD (b_i = NaN)
+ * Steps 2-3 for a given factor: L is n x n lower (ld = n) with L L^T = M.
+ * Arguments and outputs as for gls_oracle_gls below.  Returns 0, or -1 on a
+ * bad argument / allocation failure.
  */
-int64_t gls_oracle_gls(int64_t n, int32_t p, const double* M, int64_t ldm, const double* XL,
-                       int64_t ldxl, const double* y, int64_t k, const int8_t* XR, int64_t ldxr,
-                       double* B, int64_t ldb, int32_t* status, double tau, int32_t nthreads) {
-  if (n < 1 || p < 1 || k < 0 || ldm < n || ldxr < n || ldb < p) return -1;
+int64_t gls_oracle_gls_factored(int64_t n, int32_t p, const double* L, const double* XL,
+                                int64_t ldxl, const double* y, int64_t k, const int8_t* XR,
+                                int64_t ldxr, double* B, int64_t ldb, int32_t* status, double tau,
+                                int32_t nthreads) {
+  if (n < 1 || p < 1 || k < 0 || ldxr < n || ldb < p || L == NULL) return -1;
   if (p > 1 && (XL == NULL || ldxl < n)) return -1;
   if (nthreads < 1) nthreads = 1;
-  double* L = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
   double* XLt = (double*)malloc(sizeof(double) * (size_t)n * (size_t)(p > 1 ? p - 1 : 1));
   double* yt = (double*)malloc(sizeof(double) * (size_t)n);
-  if (!L || !XLt || !yt) {
-    free(L);
+  if (!XLt || !yt) {
     free(XLt);
     free(yt);
     return -1;
-  }
-  int64_t info = gls_oracle_potrf(n, M, ldm, L, n, nthreads);
-  if (info != 0) {
-    free(L);
-    free(XLt);
-    free(yt);
-    return info;
   }
   /* y~ = L^{-1} y, X~_L = L^{-1} X_L (Alg. 5 lines 2 and 4) */
   for (int64_t t = 0; t < n; ++t) yt[t] = y[t];
@@ -320,10 +307,35 @@ int64_t gls_oracle_gls(int64_t n, int32_t p, const double* M, int64_t ldm, const
   for (int t = 1; t < T; ++t) pthread_join(th[t], NULL);
   free(th);
   free(jobs);
-  free(L);
   free(XLt);
   free(yt);
   return 0;
+}
+
+/*
+ * Full reference: returns 0, the 1-based failing pivot of M (B untouched), or
+ * -1 on a bad argument / allocation failure.
+ *   M      n x n, ldm >= n, lower triangle read
+ *   XL     n x (p-1), ldxl >= n (ignored when p == 1)
+ *   y      n
+ *   XR     n x k int8, ldxr >= n
+ *   B      p x k, ldb >= p (output)
+ *   status k int32 (output, may be NULL): 0 ok, 1 S_i not SPD (b_i = NaN)
+ */
+int64_t gls_oracle_gls(int64_t n, int32_t p, const double* M, int64_t ldm, const double* XL,
+                       int64_t ldxl, const double* y, int64_t k, const int8_t* XR, int64_t ldxr,
+                       double* B, int64_t ldb, int32_t* status, double tau, int32_t nthreads) {
+  if (n < 1 || p < 1 || k < 0 || ldm < n || ldxr < n || ldb < p) return -1;
+  if (p > 1 && (XL == NULL || ldxl < n)) return -1;
+  if (nthreads < 1) nthreads = 1;
+  double* L = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+  if (!L) return -1;
+  int64_t info = gls_oracle_potrf(n, M, ldm, L, n, nthreads);
+  if (info == 0)
+    info = gls_oracle_gls_factored(n, p, L, XL, ldxl, y, k, XR, ldxr, B, ldb, status, tau,
+                                   nthreads);
+  free(L);
+  return info;
 }
 
 /*

@@ -25,9 +25,11 @@ const char* mixed_last_error();
 gls_status_t mixed_prepare(MixedState* ms, const double* Z, int64_t ldz, const double* Wt,
                            int64_t ldw, bool new_factor, cudaStream_t st);
 
-// One block: converts the int8 genotypes to the operand type and runs the
-// persistent tcgen05 solve + Gram epilogue, writing FP32 partials
-// P[I][q][j] (I < npad/128, q <= p, j < k; leading dimension ldp).
+// One block, step 1: int8 genotypes -> the 16-bit operand layout read by TMA.
+cudaError_t mixed_convert(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,
+                          cudaStream_t st);
+// One block, step 2: the persistent tcgen05 solve + Gram epilogue, writing FP32
+// partials P[I][q][j] (I < npad/128, q <= p, j < k; leading dimension ldp).
 cudaError_t mixed_trsm_gram(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,
                             float* partials, int64_t ldp, int* flags, cudaStream_t st);
 

@@ -91,12 +91,58 @@ struct gls_plan {
   double* h_b[2]{};
   int32_t* h_s[2]{};
   gls::MixedState* mixed = nullptr;
+  // device-time accounting (gls_plan_set_timing / gls_plan_stats)
+  struct Slot {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    double ms = 0.0;
+    int64_t launches = 0;
+  };
+  bool timing = false;
+  Slot t_trsm, t_convert, t_solve, t_factor;
+  int64_t launches = 0;
+  std::vector<cudaEvent_t> event_pool;
   bool has_factor = false;  // L and Z valid
   bool has_xl = false;      // X_L staged
   bool factored = false;    // ready for solves
 };
 
 namespace {
+
+cudaEvent_t pool_event(gls_plan* pl) {
+  if (!pl->event_pool.empty()) {
+    cudaEvent_t e = pl->event_pool.back();
+    pl->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Brackets one kernel (or phase) with events on the plan's stream when timing is on.
+struct Timed {
+  gls_plan* pl;
+  gls_plan::Slot* slot;
+  cudaEvent_t e0 = nullptr;
+  Timed(gls_plan* p, gls_plan::Slot* s) : pl(p), slot(s) {
+    if (pl->timing && (e0 = pool_event(pl))) cudaEventRecord(e0, pl->stream);
+  }
+  void finish() {
+    if (!e0) return;
+    cudaEvent_t e1 = pool_event(pl);
+    if (!e1) {
+      pl->event_pool.push_back(e0);
+    } else {
+      cudaEventRecord(e1, pl->stream);
+      slot->pending.emplace_back(e0, e1);
+    }
+    e0 = nullptr;
+  }
+  ~Timed() { finish(); }
+};
 
 size_t footprint(const gls_plan_desc_t& d, int64_t* npad_out = nullptr) {
   const int64_t npad = gls::round_up(d.n, 128);
@@ -181,6 +227,12 @@ void free_plan(gls_plan* pl) {
     if (pl->ev_stored[s]) cudaEventDestroy(pl->ev_stored[s]);
     if (pl->ev_staged[s]) cudaEventDestroy(pl->ev_staged[s]);
   }
+  for (gls_plan::Slot* sl : {&pl->t_trsm, &pl->t_convert, &pl->t_solve, &pl->t_factor})
+    for (auto& pr : sl->pending) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  for (cudaEvent_t e : pl->event_pool) cudaEventDestroy(e);
   if (pl->h2d) cudaStreamDestroy(pl->h2d);
   if (pl->d2h) cudaStreamDestroy(pl->d2h);
   if (pl->own_stream && pl->stream) cudaStreamDestroy(pl->stream);
@@ -236,15 +288,29 @@ gls_status_t run_block(gls_plan* pl, const int8_t* xr, int64_t ldxr, int64_t k, 
                        int64_t ldb, int32_t* status) {
   if (k == 0) return GLS_OK;
   if (pl->precision == GLS_PREC_FP64) {
-    GLS_CUDA(gls::launch_trsm_gram_fp64(pl->Z, pl->npad, pl->n, pl->npad, xr, ldxr, k, pl->Wt,
-                                        pl->npad, pl->p, pl->partials, pl->ldp, pl->stream));
+    {
+      Timed t(pl, &pl->t_trsm);
+      GLS_CUDA(gls::launch_trsm_gram_fp64(pl->Z, pl->npad, pl->n, pl->npad, xr, ldxr, k, pl->Wt,
+                                          pl->npad, pl->p, pl->partials, pl->ldp, pl->stream));
+    }
+    Timed t(pl, &pl->t_solve);
     gls::launch_assemble_solve(pl->partials, pl->ldp, pl->nI, pl->p, k, pl->RTL, pl->zT,
                                gls::kTauFP64, B, ldb, status, pl->stream);
+    pl->launches += 2;
   } else {
     float* pf = reinterpret_cast<float*>(pl->partials);
-    GLS_CUDA(gls::mixed_trsm_gram(pl->mixed, xr, ldxr, k, pf, pl->ldp, pl->flags, pl->stream));
+    {
+      Timed t(pl, &pl->t_convert);
+      GLS_CUDA(gls::mixed_convert(pl->mixed, xr, ldxr, k, pl->stream));
+    }
+    {
+      Timed t(pl, &pl->t_trsm);
+      GLS_CUDA(gls::mixed_trsm_gram(pl->mixed, xr, ldxr, k, pf, pl->ldp, pl->flags, pl->stream));
+    }
+    Timed t(pl, &pl->t_solve);
     gls::launch_assemble_solve_f32(pf, pl->ldp, pl->nI, pl->p, k, pl->RTL, pl->zT,
                                    gls::kTauMixed, B, ldb, status, pl->stream);
+    pl->launches += 3;
   }
   GLS_CUDA(cudaGetLastError());
   return GLS_OK;
@@ -418,8 +484,11 @@ gls_status_t gls_factor(gls_plan_t pl, const double* M, int64_t ldm, const doubl
   const int64_t n = pl->n, npad = pl->npad;
   const int p = pl->p;
   cudaStream_t st = pl->stream;
+  Timed phase(pl, &pl->t_factor);
   GLS_CUDA(cudaMemsetAsync(pl->flags, 0, sizeof(int) * gls::kFlagCount, st));
   if (M) {
+    const int64_t N = npad / gls::kT;
+    pl->launches += 2 + N + 4 * (N - 1);
     pl->has_factor = false;
     GLS_CUDA(cudaMemcpy2DAsync(pl->A, npad * sizeof(double), M, ldm * sizeof(double),
                                n * sizeof(double), n, cudaMemcpyDefault, st));
@@ -437,6 +506,7 @@ gls_status_t gls_factor(gls_plan_t pl, const double* M, int64_t ldm, const doubl
   gls::launch_whiten(pl->Z, npad, n, npad, pl->Wrhs, npad, p, pl->Wt, npad, pl->flags, st);
   gls::launch_fixed_gram(pl->Wt, npad, n, p, pl->gram, st);
   if (p > 1) gls::launch_small_chol(pl->gram, p, pl->RTL, pl->zT, pl->flags, st);
+  pl->launches += (p > 1) ? 3 : 2;
   GLS_CUDA(cudaGetLastError());
   int hf[gls::kFlagCount];
   GLS_TRY(check_flags(pl, hf));
@@ -453,8 +523,10 @@ gls_status_t gls_factor(gls_plan_t pl, const double* M, int64_t ldm, const doubl
   }
   if (pl->precision != GLS_PREC_FP64) {
     GLS_TRY(gls::mixed_prepare(pl->mixed, pl->Z, npad, pl->Wt, npad, M != nullptr, st));
-    GLS_TRY(check_flags(pl, hf));
+    pl->launches += (M != nullptr) ? 2 : 1;
   }
+  phase.finish();
+  if (pl->precision != GLS_PREC_FP64) GLS_TRY(check_flags(pl, hf));
   pl->factored = true;
   return GLS_OK;
 }
@@ -655,6 +727,59 @@ gls_status_t gls_synchronize(gls_plan_t pl) {
 }
 
 void* gls_plan_stream(gls_plan_t pl) { return pl ? (void*)pl->stream : nullptr; }
+
+gls_status_t gls_plan_set_timing(gls_plan_t pl, int32_t enable) {
+  g_last_error.clear();
+  if (!pl) {
+    set_error("plan is NULL");
+    return GLS_ERR_INVALID_ARG;
+  }
+  DeviceGuard guard(pl->device);
+  GLS_CUDA(cudaStreamSynchronize(pl->stream));
+  for (gls_plan::Slot* sl : {&pl->t_trsm, &pl->t_convert, &pl->t_solve, &pl->t_factor}) {
+    for (auto& pr : sl->pending) {
+      pl->event_pool.push_back(pr.first);
+      pl->event_pool.push_back(pr.second);
+    }
+    sl->pending.clear();
+    sl->ms = 0.0;
+    sl->launches = 0;
+  }
+  pl->launches = 0;
+  pl->timing = enable != 0;
+  return GLS_OK;
+}
+
+gls_status_t gls_plan_stats(gls_plan_t pl, gls_stats_t* out) {
+  g_last_error.clear();
+  if (!pl || !out) {
+    set_error("plan or out is NULL");
+    return GLS_ERR_INVALID_ARG;
+  }
+  DeviceGuard guard(pl->device);
+  GLS_CUDA(cudaStreamSynchronize(pl->stream));
+  for (gls_plan::Slot* sl : {&pl->t_trsm, &pl->t_convert, &pl->t_solve, &pl->t_factor}) {
+    for (auto& pr : sl->pending) {
+      float ms = 0.f;
+      GLS_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+      sl->ms += ms;
+      sl->launches += 1;
+      pl->event_pool.push_back(pr.first);
+      pl->event_pool.push_back(pr.second);
+    }
+    sl->pending.clear();
+  }
+  out->launches = pl->launches;
+  out->trsm_ms = pl->t_trsm.ms;
+  out->trsm_launches = pl->t_trsm.launches;
+  out->convert_ms = pl->t_convert.ms;
+  out->convert_launches = pl->t_convert.launches;
+  out->solve_ms = pl->t_solve.ms;
+  out->solve_launches = pl->t_solve.launches;
+  out->factor_ms = pl->t_factor.ms;
+  out->factor_calls = pl->t_factor.launches;
+  return GLS_OK;
+}
 
 gls_status_t gls_destroy(gls_plan_t pl) {
   g_last_error.clear();

@@ -602,8 +602,8 @@ gls_status_t mixed_prepare(MixedState* ms, const double* Z, int64_t ldz, const d
   return GLS_OK;
 }
 
-cudaError_t mixed_trsm_gram(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,
-                            float* partials, int64_t ldp, int* flags, cudaStream_t st) {
+cudaError_t mixed_convert(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,
+                          cudaStream_t st) {
   if (k <= 0) return cudaSuccess;
   const int64_t work = k * (ms->npad / 8);
   const unsigned cgrid = (unsigned)std::min<int64_t>(ceil_div(work, 256), 65535 * 4);
@@ -611,6 +611,12 @@ cudaError_t mixed_trsm_gram(MixedState* ms, const int8_t* xr, int64_t ldxr, int6
     convert_x_kernel<true><<<cgrid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, ms->x16);
   else
     convert_x_kernel<false><<<cgrid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, ms->x16);
+  return cudaGetLastError();
+}
+
+cudaError_t mixed_trsm_gram(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,
+                            float* partials, int64_t ldp, int* flags, cudaStream_t st) {
+  if (k <= 0) return cudaSuccess;
   KParams kp = ms->kp;
   kp.x8 = xr;
   kp.ldx8 = ldxr;

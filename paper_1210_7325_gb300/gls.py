@@ -51,6 +51,19 @@ class PlanDesc(ctypes.Structure):
     ]
 
 
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("launches", ctypes.c_int64),
+        ("trsm_ms", ctypes.c_double), ("trsm_launches", ctypes.c_int64),
+        ("convert_ms", ctypes.c_double), ("convert_launches", ctypes.c_int64),
+        ("solve_ms", ctypes.c_double), ("solve_launches", ctypes.c_int64),
+        ("factor_ms", ctypes.c_double), ("factor_calls", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -88,6 +101,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.gls_last_error.restype = ctypes.c_char_p
     lib.gls_version.argtypes = []
     lib.gls_version.restype = i32
+    lib.gls_plan_set_timing.argtypes = [vp, i32]
+    lib.gls_plan_set_timing.restype = i32
+    lib.gls_plan_stats.argtypes = [vp, P(Stats)]
+    lib.gls_plan_stats.restype = i32
     _lib = lib
     return lib
 
@@ -217,6 +234,15 @@ class Plan:
             m = XR.shape[1]
         _check(lib.gls_solve_stream(self._h, px, ldx, int(m), pb, ldb, _ptr(status)),
                "gls_solve_stream")
+
+    def set_timing(self, enable: bool = True):
+        """Enables per-kernel device timing (and resets the counters)."""
+        _check(load().gls_plan_set_timing(self._h, int(bool(enable))), "gls_plan_set_timing")
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(load().gls_plan_stats(self._h, ctypes.byref(st)), "gls_plan_stats")
+        return st.as_dict()
 
     def synchronize(self):
         _check(load().gls_synchronize(self._h), "gls_synchronize")

@@ -35,16 +35,20 @@ def rng(seed: int, stream: int) -> np.random.Generator:
 
 def kinship_markers(n: int, seed: int, n_markers: int = 5000) -> np.ndarray:
     """Standardized marker matrix G (n x n_markers, float64, C order)."""
+    if n < 2:
+        raise ValueError("a marker column needs n >= 2 individuals to have variance")
     g = rng(seed, _STREAM_KINSHIP)
     G = np.empty((n, n_markers), dtype=np.float64)
     f = g.uniform(0.05, 0.5, size=n_markers)
     for j in range(n_markers):
-        while True:
+        for _ in range(10000):
             col = g.binomial(2, f[j], size=n).astype(np.float64)
             sd = col.std()
             if sd > 0.0:
                 break
             f[j] = g.uniform(0.05, 0.5)
+        else:
+            raise RuntimeError("could not draw a polymorphic marker column")
         G[:, j] = (col - col.mean()) / sd
     return G
 
@@ -53,6 +57,8 @@ def kinship_M(n: int, h: float, seed: int, n_markers: int = 5000, device: str = 
     """M = h Phi + (1 - h) I as an n x n float64 array (symmetric, so C order
     equals column-major).  ``device`` selects where G G^T is multiplied
     (a torch device string); the result is always returned on the host."""
+    if n == 1:  # Phi has unit diagonal, so M = h + (1 - h) = 1
+        return np.ones((1, 1))
     G = kinship_markers(n, seed, n_markers)
     if device == "cpu":
         K = (G @ G.T) / n_markers

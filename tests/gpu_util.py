@@ -16,7 +16,7 @@ def relerr(B, Bref):
 
 def to_device(pr, dev="cuda:0"):
     import torch
-    M = torch.from_numpy(np.ascontiguousarray(pr["M"])).to(dev)  # symmetric
+    M = torch.from_numpy(np.ascontiguousarray(pr["M"].T)).to(dev).t()  # column-major
     XL = pr["XL"]
     XLd = torch.from_numpy(np.ascontiguousarray(XL.T)).to(dev).t() if XL.shape[1] else None
     y = torch.from_numpy(np.ascontiguousarray(pr["y"])).to(dev)

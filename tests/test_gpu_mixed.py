@@ -124,7 +124,7 @@ def test_full_size_sampled():
     planted = 12345
     y_pl = XL @ beta[:-1] + XRt[planted].double().cpu().numpy() * beta[-1]
     dev = "cuda:0"
-    Md = torch.from_numpy(M).to(dev)
+    Md = torch.from_numpy(np.ascontiguousarray(M.T)).to(dev).t()
     XLd = torch.from_numpy(np.ascontiguousarray(XL.T)).to(dev).t()
     out = {}
     for tag, yy in (("y", y), ("planted", y_pl)):
