@@ -55,8 +55,9 @@ cudaError_t launch_trsm_gram_fp64(const double* Z, int64_t ldz, int64_t n, int64
 void launch_assemble_solve(const double* partials, int64_t ldp, int nrowblocks, int p,
                            int64_t k, const double* RTL, const double* zT, double tau,
                            double* B, int64_t ldb, int32_t* status, cudaStream_t st);
-void launch_assemble_solve_f32(const float* partials, int64_t ldp, int nrowblocks, int p,
-                               int64_t k, const double* RTL, const double* zT, double tau,
-                               double* B, int64_t ldb, int32_t* status, cudaStream_t st);
+void launch_assemble_solve_split(const double* Glin, const double* Pbr, int64_t ldp,
+                                 int nrowblocks, int p, int64_t k, const double* RTL,
+                                 const double* zT, double tau, double* B, int64_t ldb,
+                                 int32_t* status, cudaStream_t st);
 
 }  // namespace gls

@@ -20,18 +20,21 @@ void mixed_free(MixedState* ms);
 const char* mixed_last_error();
 
 // After the FP64 setup: splits the off-diagonal part of Z = L^{-1} into
-// tensor-core slices (only when new_factor), keeps the FP64 diagonal blocks,
-// and stages [X~_L | y~] in FP32 for the Gram epilogue.
+// tensor-core slices and keeps its FP64 diagonal blocks (only when new_factor),
+// then forms W = Z^T [X~_L | y~] = M^{-1} [X_L | y] in binary64 and splits W^T
+// into the extra row block of the A operand.
 gls_status_t mixed_prepare(MixedState* ms, const double* Z, int64_t ldz, const double* Wt,
                            int64_t ldw, bool new_factor, cudaStream_t st);
 
 // One block, step 1: int8 genotypes -> the 16-bit operand layout read by TMA.
 cudaError_t mixed_convert(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,
                           cudaStream_t st);
-// One block, step 2: the persistent tcgen05 solve + Gram epilogue, writing FP32
-// partials P[I][q][j] (I < npad/128, q <= p, j < k; leading dimension ldp).
+// One block, step 2: the persistent tcgen05 solve + Gram epilogue.  Writes the
+// S_BR partials Pbr[I][j] (I < npad/128) and the linear Gram entries
+// Glin[q][j] (q < p-1: S_BL, q = p-1: b_B), j < k, leading dimension ldp.
 cudaError_t mixed_trsm_gram(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,
-                            float* partials, int64_t ldp, int* flags, cudaStream_t st);
+                            double* Pbr, double* Glin, int64_t ldp, int* flags,
+                            cudaStream_t st);
 
 // Size of the FP64 diagonal blocks kept out of the tensor-core slices.
 int mixed_diag_block(const MixedState* ms);

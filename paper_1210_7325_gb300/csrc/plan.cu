@@ -144,6 +144,13 @@ struct Timed {
   ~Timed() { finish(); }
 };
 
+// FP64 path: per 64-row block, p + 1 partial sums per SNP.  Mixed path: one S_BR
+// partial per 128-row block per SNP, plus the p linear Gram entries per SNP.
+size_t partial_doubles(int precision, int64_t npad, int p, int64_t kmax) {
+  if (precision == GLS_PREC_FP64) return (size_t)(npad / gls::kT) * (p + 1) * kmax;
+  return (size_t)(npad / 128 + p) * kmax;
+}
+
 size_t footprint(const gls_plan_desc_t& d, int64_t* npad_out = nullptr) {
   const int64_t npad = gls::round_up(d.n, 128);
   if (npad_out) *npad_out = npad;
@@ -156,8 +163,7 @@ size_t footprint(const gls_plan_desc_t& d, int64_t* npad_out = nullptr) {
   bytes += 64;                                                    // flags
   bytes += 2 * (size_t)d.n * kmax;                                // X_R staging
   bytes += 2 * (size_t)kmax * (p * sizeof(double) + sizeof(int32_t));
-  const int64_t nI = (d.precision == GLS_PREC_FP64) ? npad / gls::kT : npad / 128;
-  bytes += (size_t)nI * (p + 1) * kmax * sizeof(double);           // Gram partials
+  bytes += partial_doubles(d.precision, npad, p, kmax) * sizeof(double);  // Gram partials
   if (d.precision != GLS_PREC_FP64) bytes += gls::mixed_footprint(d.n, npad, p, kmax, d.split_terms);
   return bytes;
 }
@@ -298,18 +304,20 @@ gls_status_t run_block(gls_plan* pl, const int8_t* xr, int64_t ldxr, int64_t k, 
                                gls::kTauFP64, B, ldb, status, pl->stream);
     pl->launches += 2;
   } else {
-    float* pf = reinterpret_cast<float*>(pl->partials);
+    double* Pbr = pl->partials;                      // nI x ldp
+    double* Glin = pl->partials + (int64_t)pl->nI * pl->ldp;  // p x ldp
     {
       Timed t(pl, &pl->t_convert);
       GLS_CUDA(gls::mixed_convert(pl->mixed, xr, ldxr, k, pl->stream));
     }
     {
       Timed t(pl, &pl->t_trsm);
-      GLS_CUDA(gls::mixed_trsm_gram(pl->mixed, xr, ldxr, k, pf, pl->ldp, pl->flags, pl->stream));
+      GLS_CUDA(gls::mixed_trsm_gram(pl->mixed, xr, ldxr, k, Pbr, Glin, pl->ldp, pl->flags,
+                                    pl->stream));
     }
     Timed t(pl, &pl->t_solve);
-    gls::launch_assemble_solve_f32(pf, pl->ldp, pl->nI, pl->p, k, pl->RTL, pl->zT,
-                                   gls::kTauMixed, B, ldb, status, pl->stream);
+    gls::launch_assemble_solve_split(Glin, Pbr, pl->ldp, pl->nI, pl->p, k, pl->RTL, pl->zT,
+                                     gls::kTauMixed, B, ldb, status, pl->stream);
     pl->launches += 3;
   }
   GLS_CUDA(cudaGetLastError());
@@ -423,7 +431,8 @@ gls_status_t gls_plan_create(const gls_plan_desc_t* desc, gls_plan_t* out) {
   if ((st = dev_alloc(&pl->RTL, (size_t)32 * 32)) != GLS_OK) return fail(st);
   if ((st = dev_alloc(&pl->zT, (size_t)32)) != GLS_OK) return fail(st);
   if ((st = dev_alloc(&pl->flags, (size_t)gls::kFlagCount)) != GLS_OK) return fail(st);
-  if ((st = dev_alloc(&pl->partials, (size_t)pl->nI * (p + 1) * kmax)) != GLS_OK) return fail(st);
+  if ((st = dev_alloc(&pl->partials, partial_doubles(pl->precision, npad, p, kmax))) != GLS_OK)
+    return fail(st);
   for (int s = 0; s < 2; ++s) {
     if ((st = dev_alloc(&pl->xr[s], (size_t)n * kmax)) != GLS_OK) return fail(st);
     if ((st = dev_alloc(&pl->bdev[s], (size_t)p * kmax)) != GLS_OK) return fail(st);
@@ -523,7 +532,7 @@ gls_status_t gls_factor(gls_plan_t pl, const double* M, int64_t ldm, const doubl
   }
   if (pl->precision != GLS_PREC_FP64) {
     GLS_TRY(gls::mixed_prepare(pl->mixed, pl->Z, npad, pl->Wt, npad, M != nullptr, st));
-    pl->launches += (M != nullptr) ? 2 : 1;
+    pl->launches += (M != nullptr) ? 3 : 2;
   }
   phase.finish();
   if (pl->precision != GLS_PREC_FP64) GLS_TRY(check_flags(pl, hf));

@@ -22,29 +22,12 @@
 namespace gls {
 namespace {
 
-template <class PT>
-__global__ void __launch_bounds__(128) assemble_solve_kernel(
-    const PT* __restrict__ P, int64_t ldp, int nI, int p, int64_t k,
-    const double* __restrict__ RTL, const double* __restrict__ zT, double tau,
-    double* __restrict__ B, int64_t ldb, int32_t* __restrict__ status) {
-  __shared__ double R[kMaxP * kMaxP];
-  __shared__ double z[kMaxP];
+// The per-SNP part of the Cholesky solve of S_i, given s = S_BL_i (length q),
+// rho = b_B_i and sigma = S_BR_i.  R (q x q) and z (q) are R_TL and z_T.
+__device__ __forceinline__ void solve_one(double (&s)[kMaxP], double rho, double sigma, int p,
+                                          const double* R, const double* z, double tau,
+                                          double* out, int32_t* status_j) {
   const int q = p - 1;
-  for (int t = threadIdx.x; t < q * q; t += blockDim.x) R[t] = RTL[t];
-  for (int t = threadIdx.x; t < q; t += blockDim.x) z[t] = zT[t];
-  __syncthreads();
-  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (j >= k) return;
-
-  double s[kMaxP];
-  double rho = 0.0, sigma = 0.0;
-  for (int a = 0; a < q; ++a) s[a] = 0.0;
-  for (int I = 0; I < nI; ++I) {
-    const PT* pi = P + (int64_t)I * (p + 1) * ldp + j;
-    for (int a = 0; a < q; ++a) s[a] += (double)pi[(int64_t)a * ldp];
-    rho += (double)pi[(int64_t)q * ldp];
-    sigma += (double)pi[(int64_t)p * ldp];
-  }
   // r = R_TL^{-1} S_BL (in place in s)
   for (int a = 0; a < q; ++a) {
     double t = s[a];
@@ -53,10 +36,9 @@ __global__ void __launch_bounds__(128) assemble_solve_kernel(
   }
   double d = sigma;
   for (int a = 0; a < q; ++a) d -= s[a] * s[a];
-  double* out = B + j * ldb;
   if (!(d > tau * sigma)) {
     for (int a = 0; a < p; ++a) out[a] = __longlong_as_double(0x7ff8000000000000ll);
-    if (status) status[j] = 1;
+    if (status_j) *status_j = 1;
     return;
   }
   const double delta = sqrt(d);
@@ -73,7 +55,55 @@ __global__ void __launch_bounds__(128) assemble_solve_kernel(
   }
   for (int a = 0; a < q; ++a) out[a] = bt[a];
   out[q] = bsnp;
-  if (status) status[j] = 0;
+  if (status_j) *status_j = 0;
+}
+
+// FP64 path: partials P[I][a][j] for a <= p (S_BL..., b_B, S_BR), summed over I
+// in ascending order.
+__global__ void __launch_bounds__(128) assemble_solve_kernel(
+    const double* __restrict__ P, int64_t ldp, int nI, int p, int64_t k,
+    const double* __restrict__ RTL, const double* __restrict__ zT, double tau,
+    double* __restrict__ B, int64_t ldb, int32_t* __restrict__ status) {
+  __shared__ double R[kMaxP * kMaxP];
+  __shared__ double z[kMaxP];
+  const int q = p - 1;
+  for (int t = threadIdx.x; t < q * q; t += blockDim.x) R[t] = RTL[t];
+  for (int t = threadIdx.x; t < q; t += blockDim.x) z[t] = zT[t];
+  __syncthreads();
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  double s[kMaxP];
+  double rho = 0.0, sigma = 0.0;
+  for (int a = 0; a < q; ++a) s[a] = 0.0;
+  for (int I = 0; I < nI; ++I) {
+    const double* pi = P + (int64_t)I * (p + 1) * ldp + j;
+    for (int a = 0; a < q; ++a) s[a] += pi[(int64_t)a * ldp];
+    rho += pi[(int64_t)q * ldp];
+    sigma += pi[(int64_t)p * ldp];
+  }
+  solve_one(s, rho, sigma, p, R, z, tau, B + j * ldb, status ? status + j : nullptr);
+}
+
+// Mixed path: S_BL and b_B arrive whole in Glin[a][j]; S_BR as row-block
+// partials Pbr[I][j], summed over I in ascending order.
+__global__ void __launch_bounds__(128) assemble_solve_split_kernel(
+    const double* __restrict__ Glin, const double* __restrict__ Pbr, int64_t ldp, int nI, int p,
+    int64_t k, const double* __restrict__ RTL, const double* __restrict__ zT, double tau,
+    double* __restrict__ B, int64_t ldb, int32_t* __restrict__ status) {
+  __shared__ double R[kMaxP * kMaxP];
+  __shared__ double z[kMaxP];
+  const int q = p - 1;
+  for (int t = threadIdx.x; t < q * q; t += blockDim.x) R[t] = RTL[t];
+  for (int t = threadIdx.x; t < q; t += blockDim.x) z[t] = zT[t];
+  __syncthreads();
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  double s[kMaxP];
+  for (int a = 0; a < q; ++a) s[a] = Glin[(int64_t)a * ldp + j];
+  const double rho = Glin[(int64_t)q * ldp + j];
+  double sigma = 0.0;
+  for (int I = 0; I < nI; ++I) sigma += Pbr[(int64_t)I * ldp + j];
+  solve_one(s, rho, sigma, p, R, z, tau, B + j * ldb, status ? status + j : nullptr);
 }
 
 }  // namespace
@@ -82,16 +112,17 @@ void launch_assemble_solve(const double* partials, int64_t ldp, int nI, int p, i
                            const double* RTL, const double* zT, double tau, double* B,
                            int64_t ldb, int32_t* status, cudaStream_t st) {
   if (k <= 0) return;
-  assemble_solve_kernel<double><<<(unsigned)ceil_div(k, 128), 128, 0, st>>>(
+  assemble_solve_kernel<<<(unsigned)ceil_div(k, 128), 128, 0, st>>>(
       partials, ldp, nI, p, k, RTL, zT, tau, B, ldb, status);
 }
 
-void launch_assemble_solve_f32(const float* partials, int64_t ldp, int nI, int p, int64_t k,
-                               const double* RTL, const double* zT, double tau, double* B,
-                               int64_t ldb, int32_t* status, cudaStream_t st) {
+void launch_assemble_solve_split(const double* Glin, const double* Pbr, int64_t ldp, int nI,
+                                 int p, int64_t k, const double* RTL, const double* zT,
+                                 double tau, double* B, int64_t ldb, int32_t* status,
+                                 cudaStream_t st) {
   if (k <= 0) return;
-  assemble_solve_kernel<float><<<(unsigned)ceil_div(k, 128), 128, 0, st>>>(
-      partials, ldp, nI, p, k, RTL, zT, tau, B, ldb, status);
+  assemble_solve_split_kernel<<<(unsigned)ceil_div(k, 128), 128, 0, st>>>(
+      Glin, Pbr, ldp, nI, p, k, RTL, zT, tau, B, ldb, status);
 }
 
 }  // namespace gls

@@ -18,8 +18,18 @@
 // is negligible.  Slice H accumulates in one TMEM accumulator, R1 + R2 in a
 // second one.  The epilogue forms
 //     x~_r = u_r (acc_H + acc_R) + sum_{c in diag block} Z_rc x_c    (that sum in FP64)
-// and reduces the Gram partials of Fig. 1 over the tile's 128 rows:
-//     P[I][q][j] = sum_r W(r, q) x~(r, j) (q < p),  P[I][p][j] = sum_r x~(r, j)^2.
+// and reduces S_BR = x~^T x~ over the tile's 128 rows with compensated FP32
+// sums (a sum of squares: no cancellation), written as FP64 partials.
+//
+// The other Gram entries of Fig. 1 are linear in x~, and
+//     S_BL_i = X~_L^T x~_i = (Z^T X~_L)^T x_i,   b_B_i = y~^T x~_i = (Z^T y~)^T x_i,
+// so they are computed from the exact genotypes with W = Z^T [X~_L | y~]
+// (= M^{-1} [X_L | y], binary64, once per factor) split the same way as Z: one
+// extra 128-row block of the A operand holds the p rows of W^T, its K range
+// is all n, and its accumulators give the p products per SNP directly, with
+// no cross-row reduction.  (In FP32 those cross products lose accuracy to
+// cancellation; through the exact split they keep about 2^-25 relative to
+// each row's scale.)
 //
 // Kernel shape (one persistent CTA per SM, 192 threads):
 //   warp 0      TMA producer: A slices of Z (128 x 64 each) and the 128-SNP x 64
@@ -28,9 +38,9 @@
 //               (M = 128, N = 128, K = 16) into two double-buffered accumulator pairs
 //   warps 2-5   epilogue: tcgen05.ld of the accumulators, FP64 diagonal block,
 //               Gram reduction, FP32 partial write-out
-// Work items (row block I, SNP tile J) are visited heaviest row block first;
-// consecutive CTAs share I, so the Z slices of a row block are read from HBM
-// once and served to the other CTAs from L2.
+// Work items (row block I, SNP tile J), I = 0..nI (I = nI is the W^T block),
+// are visited heaviest row block first; consecutive CTAs share I, so the
+// slices of a row block are read from HBM once and served to the others from L2.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -70,13 +80,13 @@ struct KParams {
   int64_t n, k;
   int nI, nJ, p, S, stages;
   uint32_t idesc;
-  const float* rowscale;  // u_r
+  const float* rowscale;  // u_r, npad + 128 rows
   const double* diagZ;    // npad x kDiag
-  const float* W32;       // npad x p, row-major
-  float* P;
+  double* Pbr;            // S_BR partials, nI x ldp
+  double* Glin;           // S_BL and b_B, p x ldp
   int64_t ldp;
   int* flags;
-  uint32_t off_T, off_W, off_tab, off_bar, stage_bytes;
+  uint32_t off_T, off_tab, off_bar, stage_bytes;
 };
 
 __device__ void raise_error(int* flags, int site) {
@@ -117,7 +127,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* T = reinterpret_cast<float*>(base + kp.off_T);
-  float* Ws = reinterpret_cast<float*>(base + kp.off_W);
   double* dtab = reinterpret_cast<double*>(base + kp.off_tab);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -149,7 +158,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int total = kp.nI * kp.nJ;
+  const int nIt = kp.nI + 1;  // row blocks of Z plus the W^T block
+  const int total = nIt * kp.nJ;
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -157,8 +167,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t g = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-        const int I = kp.nI - 1 - t / kp.nJ, J = t % kp.nJ;
-        const int kblocks = 2 * (I + 1);
+        const int I = nIt - 1 - t / kp.nJ, J = t % kp.nJ;
+        const int kblocks = (I == kp.nI) ? 2 * kp.nI : 2 * (I + 1);
         for (int kb = 0; kb < kblocks; ++kb, ++g) {
           const int st = (int)(g % stages);
           const uint32_t w = g / stages;
@@ -188,8 +198,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       int it = 0;
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
-        const int I = kp.nI - 1 - t / kp.nJ;
-        const int kblocks = 2 * (I + 1);
+        const int I = nIt - 1 - t / kp.nJ;
+        const int kblocks = (I == kp.nI) ? 2 * kp.nI : 2 * (I + 1);
         const int buf = it & 1;
         const uint32_t u = (uint32_t)it >> 1;
         if (!mbar_wait_bounded(&tempty[buf], (u & 1) ^ 1, abort_flag, kWaitLimitNs)) {
@@ -232,21 +242,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int quarter = warp & 3;            // TMEM lanes this warp may read
     const int row = quarter * 32 + lane;     // row of the tile owned by this thread
     const int et = threadIdx.x - 64;         // 0..127
-    const int gj = et >> 2, gg = et & 3;     // Gram mapping: SNP column, row group
+    const int gj = et >> 2, gg = et & 3;     // S_BR mapping: SNP column, row group
     const int p = kp.p;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
     int it = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
-      const int I = kp.nI - 1 - t / kp.nJ, J = t % kp.nJ;
+      const int I = nIt - 1 - t / kp.nJ, J = t % kp.nJ;
+      const bool lin = (I == kp.nI);
       const int buf = it & 1;
       const uint32_t u = (uint32_t)it >> 1;
       const int64_t r = (int64_t)I * BM + row;
       const float ur = kp.rowscale[r];
       double dz[kDiag];
+      int64_t r0 = 0;
 #pragma unroll
-      for (int q = 0; q < kDiag; ++q) dz[q] = kp.diagZ[r * kDiag + q];
-      const int64_t r0 = r - (r % kDiag);
-      for (int q = 0; q < p; ++q) Ws[row * p + q] = kp.W32[r * p + q];
+      for (int q = 0; q < kDiag; ++q) dz[q] = 0.0;
+      if (!lin) {
+#pragma unroll
+        for (int q = 0; q < kDiag; ++q) dz[q] = kp.diagZ[r * kDiag + q];
+        r0 = r - (r % kDiag);
+      }
       const bool got = mbar_wait_bounded(&tfull[buf], u & 1, abort_flag, kWaitLimitNs);
       if (!epilogue_all(got)) {  // all 128 threads leave together
         if (!got && lane == 0) raise_error(kp.flags, 3);
@@ -265,6 +280,20 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (lane == 0) mbar_arrive(&tempty[buf]);
         }
         const int64_t jbase = (int64_t)J * BN + c * 32;
+        if (lin) {
+          // W^T block: lane q < p holds (M^{-1}[X_L | y])_q^T x_j for 32 SNPs
+          if (row < p) {
+            double* out = kp.Glin + (int64_t)row * kp.ldp;
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+              const int64_t j = jbase + jj;
+              if (j < kp.k)
+                out[j] = (double)ur * ((double)__uint_as_float(aH[jj]) +
+                                       (double)__uint_as_float(aR[jj]));
+            }
+          }
+          continue;
+        }
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj) {
           const int64_t j = jbase + jj;
@@ -279,30 +308,31 @@ __global__ void __launch_bounds__(kThreads, 1)
           T[row * 32 + (jj ^ lane)] = v;
         }
         named_barrier_sync(1, 128);
-        float acc[kMaxP + 1];
-#pragma unroll
-        for (int q = 0; q <= kMaxP; ++q) acc[q] = 0.f;
+        // S_BR partial: sum of x~^2 over the 128 rows, error-free transforms in FP32
+        float sum = 0.f, comp = 0.f;
         for (int i = 0; i < BM / 4; ++i) {
           const int rr = gg + 4 * i;
           const float x = T[rr * 32 + (gj ^ (rr & 31))];
-#pragma unroll
-          for (int q = 0; q < kMaxP; ++q)
-            if (q < p) acc[q] = fmaf(Ws[rr * p + q], x, acc[q]);
-          acc[kMaxP] = fmaf(x, x, acc[kMaxP]);
+          const float pr = __fmul_rn(x, x);
+          const float pe = fmaf(x, x, -pr);  // x^2 = pr + pe exactly
+          const float tt = __fadd_rn(sum, pr);
+          const float bp = __fsub_rn(tt, sum);
+          const float er = __fadd_rn(__fsub_rn(sum, __fsub_rn(tt, bp)), __fsub_rn(pr, bp));
+          sum = tt;
+          comp = __fadd_rn(comp, __fadd_rn(er, pe));
         }
 #pragma unroll
-        for (int q = 0; q <= kMaxP; ++q) {
-          acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 1);
-          acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 2);
+        for (int msk = 1; msk <= 2; msk <<= 1) {
+          const float so = __shfl_xor_sync(0xffffffffu, sum, msk);
+          const float co = __shfl_xor_sync(0xffffffffu, comp, msk);
+          const float tt = __fadd_rn(sum, so);
+          const float bp = __fsub_rn(tt, sum);
+          const float er = __fadd_rn(__fsub_rn(sum, __fsub_rn(tt, bp)), __fsub_rn(so, bp));
+          sum = tt;
+          comp = __fadd_rn(__fadd_rn(comp, co), er);
         }
         const int64_t j = jbase + gj;
-        if (gg == 0 && j < kp.k) {
-          float* out = kp.P + (int64_t)I * (p + 1) * kp.ldp + j;
-#pragma unroll
-          for (int q = 0; q < kMaxP; ++q)
-            if (q < p) out[(int64_t)q * kp.ldp] = acc[q];
-          out[(int64_t)p * kp.ldp] = acc[kMaxP];
-        }
+        if (gg == 0 && j < kp.k) kp.Pbr[(int64_t)I * kp.ldp + j] = (double)sum + (double)comp;
         named_barrier_sync(1, 128);
       }
     }
@@ -411,21 +441,92 @@ __global__ void __launch_bounds__(256) split_kernel(const double* __restrict__ Z
         v.y = (uint32_t)src[2] | ((uint32_t)src[3] << 16);
         v.z = (uint32_t)src[4] | ((uint32_t)src[5] << 16);
         v.w = (uint32_t)src[6] | ((uint32_t)src[7] << 16);
-        *reinterpret_cast<uint4*>(slices + (size_t)s * npad * npad + rr * npad + c0 + ch * 8) = v;
+        *reinterpret_cast<uint4*>(slices + (size_t)s * (npad + 128) * npad + rr * npad + c0 +
+                                  ch * 8) = v;
       }
     }
     __syncthreads();
   }
 }
 
-__global__ void w32_kernel(const double* __restrict__ Wt, int64_t ldw, int64_t npad, int p,
-                           float* __restrict__ W32) {
-  const int64_t total = npad * p;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = idx / p;
-    const int q = (int)(idx - r * p);
-    W32[idx] = (float)Wt[r + q * ldw];
+// W = Z^T Wt (= M^{-1} [X_L | y]), binary64: W(c, q) = sum_{r >= c} Z(r, c) Wt(r, q).
+// One CTA per 64 columns c; Z is read column-major (coalesced along r).
+__global__ void __launch_bounds__(256) wtrans_kernel(const double* __restrict__ Z, int64_t ldz,
+                                                     int64_t npad, const double* __restrict__ Wt,
+                                                     int64_t ldw, int p, double* __restrict__ W) {
+  __shared__ double Zs[64][65];              // Zs[rr][cc]
+  __shared__ double Rs[64][kMaxP + 1];       // Rs[rr][q]
+  const int64_t c0 = (int64_t)blockIdx.x * 64;
+  const int tid = threadIdx.x;
+  const int cc = tid % 64, qg = tid / 64;
+  double acc[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) acc[t] = 0.0;
+  for (int64_t r0 = c0; r0 < npad; r0 += 64) {
+    for (int idx = tid; idx < 64 * 64; idx += 256) {
+      const int rr = idx % 64, c = idx / 64;
+      Zs[rr][c] = Z[(r0 + rr) + (c0 + c) * ldz];
+    }
+    for (int idx = tid; idx < 64 * p; idx += 256) {
+      const int rr = idx % 64, q = idx / 64;
+      Rs[rr][q] = Wt[(r0 + rr) + (int64_t)q * ldw];
+    }
+    __syncthreads();
+    for (int rr = 0; rr < 64; ++rr) {
+      const double z = Zs[rr][cc];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int q = qg + 4 * t;
+        if (q < p) acc[t] = fma(z, Rs[rr][q], acc[t]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int q = qg + 4 * t;
+    if (q < p) W[(c0 + cc) + (int64_t)q * npad] = acc[t];
+  }
+}
+
+// Splits row q of W^T (column q of W) into the slices of A-operand row npad + q,
+// with its own scale u = 2^(E - bits) over the whole row.  One CTA per q.
+template <bool kBF16>
+__global__ void __launch_bounds__(256) split_w_kernel(const double* __restrict__ W, int64_t npad,
+                                                      int bits, int naive,
+                                                      uint16_t* __restrict__ slices,
+                                                      float* __restrict__ rowscale) {
+  __shared__ double red[256];
+  const int q = blockIdx.x;
+  const double* w = W + (int64_t)q * npad;
+  double m = 0.0;
+  for (int64_t c = threadIdx.x; c < npad; c += blockDim.x) m = fmax(m, fabs(w[c]));
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  m = red[0];
+  double u = 1.0;
+  if (!naive && m > 0.0) {
+    int e;
+    frexp(m, &e);
+    u = ldexp(1.0, e - bits);
+  }
+  const int64_t row = npad + q;
+  if (threadIdx.x == 0) rowscale[row] = (float)u;
+  const double inv_u = 1.0 / u;
+  const size_t plane = (size_t)(npad + 128) * npad;
+  for (int64_t c = threadIdx.x; c < npad; c += blockDim.x) {
+    const double z = w[c] * inv_u;
+    const double h = naive ? from16<kBF16>(to16<kBF16>(z)) : rint(z);
+    const double rem = z - h;
+    const uint16_t s1 = to16<kBF16>(rem);
+    const uint16_t s2 = to16<kBF16>(rem - from16<kBF16>(s1));
+    slices[row * npad + c] = to16<kBF16>(h);
+    slices[plane + row * npad + c] = s1;
+    slices[2 * plane + row * npad + c] = s2;
   }
 }
 
@@ -453,10 +554,10 @@ struct MixedState {
   bool bf16 = true;
   bool naive = false;
   int num_sms = 1;
-  uint16_t* slices = nullptr;  // S x npad x npad, row-major per slice
-  float* rowscale = nullptr;   // npad
+  uint16_t* slices = nullptr;  // 3 planes x (npad + 128) x npad, row-major (K-major)
+  float* rowscale = nullptr;   // npad + 128
   double* diagZ = nullptr;     // npad x kDiag
-  float* W32 = nullptr;        // npad x p
+  double* Wm = nullptr;        // W = M^{-1} [X_L | y], npad x p
   uint16_t* x16 = nullptr;     // kmax x npad
   CUtensorMap tmA, tmB;
   KParams kp{};
@@ -465,9 +566,9 @@ struct MixedState {
 
 size_t mixed_footprint(int64_t n, int64_t npad, int p, int64_t kmax, int split_terms) {
   (void)n;
-  const int S = split_terms ? split_terms : 3;
-  size_t b = (size_t)S * npad * npad * 2;
-  b += (size_t)npad * (4 + kDiag * 8 + 4 * p);
+  (void)split_terms;
+  size_t b = (size_t)3 * (npad + 128) * npad * 2;
+  b += (size_t)(npad + 128) * 4 + (size_t)npad * (kDiag * 8 + 8 * p);
   b += (size_t)kmax * npad * 2;
   return b;
 }
@@ -481,14 +582,13 @@ void mixed_free(MixedState* ms) {
   cudaFree(ms->slices);
   cudaFree(ms->rowscale);
   cudaFree(ms->diagZ);
-  cudaFree(ms->W32);
+  cudaFree(ms->Wm);
   cudaFree(ms->x16);
   delete ms;
 }
 
 gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int64_t kmax,
                           int precision, int split_terms, uint32_t flags, cudaStream_t st) {
-  (void)st;
   *out = nullptr;
   if (npad % BM != 0) {
     g_err = "npad must be a multiple of 128";
@@ -515,30 +615,35 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&ms->num_sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaMalloc(&ms->slices, (size_t)ms->S * npad * npad * 2) != cudaSuccess ||
-      cudaMalloc(&ms->rowscale, (size_t)npad * 4) != cudaSuccess ||
+  const size_t rows = (size_t)npad + 128;
+  if (cudaMalloc(&ms->slices, 3 * rows * npad * 2) != cudaSuccess ||
+      cudaMalloc(&ms->rowscale, rows * 4) != cudaSuccess ||
       cudaMalloc(&ms->diagZ, (size_t)npad * kDiag * 8) != cudaSuccess ||
-      cudaMalloc(&ms->W32, (size_t)npad * p * 4) != cudaSuccess ||
+      cudaMalloc(&ms->Wm, (size_t)npad * p * 8) != cudaSuccess ||
       cudaMalloc(&ms->x16, (size_t)kmax * npad * 2) != cudaSuccess) {
     cudaGetLastError();
     return fail(GLS_ERR_OOM, "cudaMalloc of the mixed-precision operands failed");
   }
+  // the W^T block's unused rows stay zero
+  if (cudaMemsetAsync(ms->slices, 0, 3 * rows * npad * 2, st) != cudaSuccess ||
+      cudaMemsetAsync(ms->rowscale, 0, rows * 4, st) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GLS_ERR_CUDA, "cudaMemset of the operand slices failed");
+  }
   // Shared memory: stages of (S slices + genotype tile), then the epilogue buffers.
   const uint32_t stage_bytes = (uint32_t)(ms->S + 1) * kTileBytes;
-  const uint32_t epi = (uint32_t)(BM * 32 * 4 + BM * p * 4 + 256 * 8);
+  const uint32_t epi = (uint32_t)(BM * 32 * 4 + 256 * 8);
   const uint32_t bars = 8 * (2 * 4 + 5) + 16;
   int stages = 4;
   while (stages > 2 && (size_t)stages * stage_bytes + epi + bars + 1024 > (size_t)kMaxDynSmem)
     --stages;
   if ((size_t)stages * stage_bytes + epi + bars + 1024 > (size_t)kMaxDynSmem)
-    return fail(GLS_ERR_UNSUPPORTED, "shared-memory budget exceeded for this p and split");
+    return fail(GLS_ERR_UNSUPPORTED, "shared-memory budget exceeded for this split");
   ms->stages = stages;
   KParams& kp = ms->kp;
   kp.stage_bytes = stage_bytes;
   kp.off_T = (uint32_t)stages * stage_bytes;
-  kp.off_W = kp.off_T + BM * 32 * 4;
-  kp.off_tab = kp.off_W + (uint32_t)(BM * p * 4);
-  kp.off_tab = (kp.off_tab + 7u) & ~7u;
+  kp.off_tab = kp.off_T + BM * 32 * 4;
   kp.off_bar = kp.off_tab + 256 * 8;
   ms->smem = (size_t)kp.off_bar + bars + 1024;
   kp.S = ms->S;
@@ -548,7 +653,6 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   kp.idesc = umma_idesc_f16(BM, BN, ms->bf16);
   kp.rowscale = ms->rowscale;
   kp.diagZ = ms->diagZ;
-  kp.W32 = ms->W32;
   if (cudaFuncSetAttribute(trsm_gram_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)ms->smem) != cudaSuccess) {
     cudaGetLastError();
@@ -559,8 +663,8 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   const CUtensorMapDataType dt =
       ms->bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   {
-    cuuint64_t dims[3] = {(cuuint64_t)npad, (cuuint64_t)npad, (cuuint64_t)ms->S};
-    cuuint64_t strides[2] = {(cuuint64_t)npad * 2, (cuuint64_t)npad * npad * 2};
+    cuuint64_t dims[3] = {(cuuint64_t)npad, (cuuint64_t)rows, (cuuint64_t)ms->S};
+    cuuint64_t strides[2] = {(cuuint64_t)npad * 2, (cuuint64_t)rows * npad * 2};
     cuuint32_t box[3] = {BK, BM, 1};
     cuuint32_t es[3] = {1, 1, 1};
     if (enc(&ms->tmA, dt, 3, ms->slices, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -593,7 +697,14 @@ gls_status_t mixed_prepare(MixedState* ms, const double* Z, int64_t ldz, const d
       split_kernel<false><<<grid, 256, 0, st>>>(Z, ldz, ms->npad, ms->S, ms->bits, ms->naive,
                                                 ms->slices, ms->rowscale, ms->diagZ);
   }
-  w32_kernel<<<256, 256, 0, st>>>(Wt, ldw, ms->npad, ms->p, ms->W32);
+  wtrans_kernel<<<(unsigned)(ms->npad / 64), 256, 0, st>>>(Z, ldz, ms->npad, Wt, ldw, ms->p,
+                                                           ms->Wm);
+  if (ms->bf16)
+    split_w_kernel<true><<<(unsigned)ms->p, 256, 0, st>>>(ms->Wm, ms->npad, ms->bits, ms->naive,
+                                                         ms->slices, ms->rowscale);
+  else
+    split_w_kernel<false><<<(unsigned)ms->p, 256, 0, st>>>(ms->Wm, ms->npad, ms->bits, ms->naive,
+                                                          ms->slices, ms->rowscale);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     g_err = std::string("mixed prepare: ") + cudaGetErrorString(e);
@@ -615,7 +726,7 @@ cudaError_t mixed_convert(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_
 }
 
 cudaError_t mixed_trsm_gram(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,
-                            float* partials, int64_t ldp, int* flags, cudaStream_t st) {
+                            double* Pbr, double* Glin, int64_t ldp, int* flags, cudaStream_t st) {
   if (k <= 0) return cudaSuccess;
   KParams kp = ms->kp;
   kp.x8 = xr;
@@ -623,10 +734,11 @@ cudaError_t mixed_trsm_gram(MixedState* ms, const int8_t* xr, int64_t ldxr, int6
   kp.k = k;
   kp.nI = (int)(ms->npad / BM);
   kp.nJ = (int)ceil_div(k, BN);
-  kp.P = partials;
+  kp.Pbr = Pbr;
+  kp.Glin = Glin;
   kp.ldp = ldp;
   kp.flags = flags;
-  const int total = kp.nI * kp.nJ;
+  const int total = (kp.nI + 1) * kp.nJ;
   const int grid = std::min(ms->num_sms, total);
   trsm_gram_mixed_kernel<<<grid, kThreads, ms->smem, st>>>(ms->tmA, ms->tmB, kp);
   return cudaGetLastError();
