@@ -18,8 +18,9 @@
 // is negligible.  Slice H accumulates in one TMEM accumulator, R1 + R2 in a
 // second one.  The epilogue forms
 //     x~_r = u_r (acc_H + acc_R) + sum_{c in diag block} Z_rc x_c    (that sum in FP64)
-// and reduces S_BR = x~^T x~ over the tile's 128 rows with compensated FP32
-// sums (a sum of squares: no cancellation), written as FP64 partials.
+// (the tensor part exactly, as an unevaluated pair of floats) and reduces
+// S_BR = x~^T x~ over the tile's 128 rows with error-free transforms in FP32,
+// written as FP64 partials.
 //
 // The other Gram entries of Fig. 1 are linear in x~, and
 //     S_BL_i = X~_L^T x~_i = (Z^T X~_L)^T x_i,   b_B_i = y~^T x~_i = (Z^T y~)^T x_i,
@@ -126,7 +127,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* drain = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  float* T = reinterpret_cast<float*>(base + kp.off_T);
+  float* T = reinterpret_cast<float*>(base + kp.off_T);                  // x~ hi, 128 x 32
+  __nv_bfloat16* Tlo = reinterpret_cast<__nv_bfloat16*>(base + kp.off_T + BM * 32 * 4);  // lo
   double* dtab = reinterpret_cast<double*>(base + kp.off_tab);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -304,22 +306,40 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int q = 0; q < kDiag; ++q)
               if (r0 + q < kp.n) dg = fma(dz[q], dtab[(uint8_t)xc[q]], dg);
           }
-          const float v = (__uint_as_float(aH[jj]) + __uint_as_float(aR[jj])) * ur + (float)dg;
-          T[row * 32 + (jj ^ lane)] = v;
+          // x~ = u (acc_H + acc_R) + dg as an unevaluated float pair (hi, lo):
+          // both tensor terms scale exactly by the power of two u; their sum and
+          // the FP64 diagonal term (rounded once to FP32) join by error-free
+          // two-sums, so hi + lo carries the tensor part without FP32 rounding.
+          const float th = __fmul_rn(__uint_as_float(aH[jj]), ur);
+          const float tr = __fmul_rn(__uint_as_float(aR[jj]), ur);
+          const float dh = __double2float_rn(dg);
+          float s1 = __fadd_rn(th, tr);
+          float bp = __fsub_rn(s1, th);
+          const float e1 = __fadd_rn(__fsub_rn(th, __fsub_rn(s1, bp)), __fsub_rn(tr, bp));
+          const float s2 = __fadd_rn(s1, dh);
+          bp = __fsub_rn(s2, s1);
+          const float e2 = __fadd_rn(__fsub_rn(s1, __fsub_rn(s2, bp)), __fsub_rn(dh, bp));
+          T[row * 32 + (jj ^ lane)] = s2;
+          Tlo[row * 32 + (jj ^ lane)] = __float2bfloat16_rn(__fadd_rn(e1, e2));
         }
         named_barrier_sync(1, 128);
-        // S_BR partial: sum of x~^2 over the 128 rows, error-free transforms in FP32
+        // S_BR partial: sum of (hi + lo)^2 over the 128 rows with error-free
+        // transforms in FP32 (hi^2 split exactly, the cross term 2 hi lo added
+        // to the compensation; lo^2 is below the FP32 resolution of the sum).
         float sum = 0.f, comp = 0.f;
         for (int i = 0; i < BM / 4; ++i) {
           const int rr = gg + 4 * i;
-          const float x = T[rr * 32 + (gj ^ (rr & 31))];
+          const int at = rr * 32 + (gj ^ (rr & 31));
+          const float x = T[at];
+          const float xl = __bfloat162float(Tlo[at]);
           const float pr = __fmul_rn(x, x);
           const float pe = fmaf(x, x, -pr);  // x^2 = pr + pe exactly
+          const float cr = __fmul_rn(__fmul_rn(2.f, x), xl);
           const float tt = __fadd_rn(sum, pr);
-          const float bp = __fsub_rn(tt, sum);
-          const float er = __fadd_rn(__fsub_rn(sum, __fsub_rn(tt, bp)), __fsub_rn(pr, bp));
+          const float bq = __fsub_rn(tt, sum);
+          const float er = __fadd_rn(__fsub_rn(sum, __fsub_rn(tt, bq)), __fsub_rn(pr, bq));
           sum = tt;
-          comp = __fadd_rn(comp, __fadd_rn(er, pe));
+          comp = __fadd_rn(comp, __fadd_rn(er, __fadd_rn(pe, cr)));
         }
 #pragma unroll
         for (int msk = 1; msk <= 2; msk <<= 1) {
@@ -632,7 +652,7 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   }
   // Shared memory: stages of (S slices + genotype tile), then the epilogue buffers.
   const uint32_t stage_bytes = (uint32_t)(ms->S + 1) * kTileBytes;
-  const uint32_t epi = (uint32_t)(BM * 32 * 4 + 256 * 8);
+  const uint32_t epi = (uint32_t)(BM * 32 * 4 + BM * 32 * 2 + 256 * 8);
   const uint32_t bars = 8 * (2 * 4 + 5) + 16;
   int stages = 4;
   while (stages > 2 && (size_t)stages * stage_bytes + epi + bars + 1024 > (size_t)kMaxDynSmem)
@@ -643,7 +663,7 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   KParams& kp = ms->kp;
   kp.stage_bytes = stage_bytes;
   kp.off_T = (uint32_t)stages * stage_bytes;
-  kp.off_tab = kp.off_T + BM * 32 * 4;
+  kp.off_tab = kp.off_T + BM * 32 * 6;
   kp.off_bar = kp.off_tab + 256 * 8;
   ms->smem = (size_t)kp.off_bar + bars + 1024;
   kp.S = ms->S;
