@@ -36,6 +36,11 @@ WORKLOADS = {
     # name: n, p, m, h, precision, block
     "n10000_p20_m1000000_bf16": dict(n=10000, p=20, m=1_000_000, h=0.5, precision="bf16",
                                      block=65536, seed_offset=2),
+    "n10000_p20_m1000000_fp16": dict(n=10000, p=20, m=1_000_000, h=0.5, precision="fp16",
+                                     block=65536, seed_offset=2),
+    # mid-size case for profiler captures: genotypes 268 MB (> L2), ~2 GB on the device
+    "n4096_p20_m65536_bf16": dict(n=4096, p=20, m=65536, h=0.5, precision="bf16",
+                                  block=65536, seed_offset=2),
     "n1000_p4_m4096_fp64": dict(n=1000, p=4, m=4096, h=0.4, precision="fp64", block=4096,
                                 seed_offset=0),
     "n1500_p4_m2500000_fp64": dict(n=1500, p=4, m=2_500_000, h=0.5, precision="fp64",
