@@ -176,6 +176,34 @@ typedef struct {
 gls_status_t gls_plan_set_timing(gls_plan_t plan, int32_t enable);
 gls_status_t gls_plan_stats(gls_plan_t plan, gls_stats_t* out);
 
+/*
+ * Allocation-free FP64 block solve, for callers that cannot call cudaMalloc
+ * (code whose device memory belongs to another allocator, such as a
+ * framework's caching pool, or loops that must not enter the driver's
+ * allocator).  It has no counterpart in the paper: it is gls_solve_block's
+ * binary64 path with every buffer supplied by the caller.
+ *
+ * All pointers are device memory of the current device; the call is
+ * asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream).
+ *   Zinv  n x n, ldz >= n: L^{-1} with L L^T = M; only the lower triangle is read.
+ *   W     n x p, ldw >= n: [L^{-1} X_L | L^{-1} y].
+ *   RTL   (p-1) x (p-1) column-major lower Cholesky factor of W[:,0:p-1]^T W[:,0:p-1];
+ *   zT    p-1: RTL^{-1} W[:,0:p-1]^T W[:,p-1].  Both may be NULL when p == 1.
+ *   XR, B, snp_status as for gls_solve_block (snp_status may be NULL).
+ * The only scratch is a 4 MiB array inside the library (every GPU that loads
+ * the library holds it until the process exits): ceil(n/64) * (p+1) * k must
+ * not exceed 524288, otherwise GLS_ERR_INVALID_ARG (see gls_last_error).  The
+ * first call on a device looks up that array's device address; make it before
+ * any stream capture.  Every call shares the array: calls whose work can
+ * overlap on the GPU (other streams, other threads) race and must be ordered
+ * by the caller.  Nothing is allocated or freed.
+ */
+gls_status_t gls_solve_block_fp64_static(int64_t n, int32_t p, const double* Zinv, int64_t ldz,
+                                         const double* W, int64_t ldw, const double* RTL,
+                                         const double* zT, const int8_t* XR, int64_t ldxr,
+                                         int64_t k, double* B, int64_t ldb,
+                                         int32_t* snp_status, void* stream);
+
 /* Library version as major*10000 + minor*100 + patch. */
 int32_t gls_version(void);
 

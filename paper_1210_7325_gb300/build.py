@@ -19,7 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libgls_gb300.so")
-SOURCES = ["plan.cu", "factor_fp64.cu", "trsm_fp64.cu", "solve_small.cu", "trsm_mixed.cu"]
+SOURCES = ["plan.cu", "factor_fp64.cu", "trsm_fp64.cu", "solve_small.cu", "trsm_mixed.cu",
+           "static_solve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

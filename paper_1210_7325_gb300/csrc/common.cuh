@@ -51,6 +51,9 @@ cudaError_t launch_trsm_gram_fp64(const double* Z, int64_t ldz, int64_t n, int64
                                   int64_t ldw, int p, double* partials, int64_t ldp,
                                   cudaStream_t st);
 
+// plan.cu: replaces the calling thread's gls_last_error() text.
+void set_last_error_text(const char* msg);
+
 // solve_small.cu
 void launch_assemble_solve(const double* partials, int64_t ldp, int nrowblocks, int p,
                            int64_t k, const double* RTL, const double* zT, double tau,

@@ -62,6 +62,10 @@ Mem classify(const void* p) {
 
 }  // namespace
 
+namespace gls {
+void set_last_error_text(const char* msg) { g_last_error = msg ? msg : ""; }
+}  // namespace gls
+
 struct gls_plan {
   gls_plan_desc_t desc{};
   int device = 0;
