@@ -33,15 +33,18 @@
 // each row's scale.)
 //
 // Kernel shape (one persistent CTA per SM, 192 threads):
-//   warp 0      TMA producer: A slices of Z (128 x 64 each) and the 128-SNP x 64
-//               genotype tile per stage, 128-byte swizzled, one mbarrier per stage
+//   warp 0      TMA producer: per stage the 128-SNP x 64 genotype tile and the S
+//               slices of Z (128 rows x 64 each), 128-byte swizzled, one mbarrier
 //   warp 1      TMEM allocator and the single thread issuing tcgen05.mma
-//               (M = 128, N = 128, K = 16) into two double-buffered accumulator pairs
-//   warps 2-5   epilogue: tcgen05.ld of the accumulators, FP64 diagonal block,
-//               Gram reduction, FP32 partial write-out
-// Work items (row block I, SNP tile J), I = 0..nI (I = nI is the W^T block),
-// are visited heaviest row block first; consecutive CTAs share I, so the
-// slices of a row block are read from HBM once and served to the others from L2.
+//               (M = 128 SNPs, N = 128 rows of x~, K = 16) into two
+//               double-buffered accumulator pairs; genotypes are operand A
+//   warps 2-5   epilogue, one SNP per thread (its TMEM lane): tcgen05.ld of 32
+//               rows at a time, the FP64 4 x 4 diagonal blocks from the SNP's own
+//               128 genotypes of the row block, and the S_BR sum in registers
+// Work items (row block I, SNP tile J), I = 0..nI (I = nI is the W^T block), run
+// heaviest row blocks first in groups of kGroup row blocks x all SNP tiles, so
+// the concurrently running CTAs share both the Z slices of a few row blocks and
+// the genotype panels of a few dozen SNP tiles in L2.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -72,12 +75,13 @@ constexpr int kMaxDynSmem = 232448;     // 227 KB
 constexpr int kDiag = 4;                // nd: FP64 diagonal block edge
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // bounded waits give up after 1 s
 constexpr uint64_t kDrainLimitNs = 100000000ull;
+constexpr int kGroup = 8;               // row blocks per rasterization group
 
 thread_local std::string g_err;
 
 struct KParams {
-  const int8_t* x8;
-  int64_t ldx8;
+  const uint8_t* x8a;     // genotypes as bytes, SNP-major [j][npad], zero rows >= n
+  int64_t npad;
   int64_t n, k;
   int nI, nJ, p, S, stages;
   uint32_t idesc;
@@ -87,8 +91,28 @@ struct KParams {
   double* Glin;           // S_BL and b_B, p x ldp
   int64_t ldp;
   int* flags;
-  uint32_t off_T, off_tab, off_bar, stage_bytes;
+  uint32_t off_rows, off_tab, off_bar, stage_bytes;
 };
+
+// Work item t -> (row block I, SNP tile J): groups of kGroup row blocks, heaviest
+// first; within a group SNP tiles advance slowest, row blocks fastest.
+__device__ __forceinline__ void decode_item(int t, int nIt, int nJ, int& I, int& J) {
+  const int per = kGroup * nJ;
+  const int full = nIt / kGroup, tail = nIt - full * kGroup;
+  int g, ii;
+  if (t < full * per) {
+    g = t / per;
+    const int rem = t - g * per;
+    J = rem / kGroup;
+    ii = rem - J * kGroup;
+  } else {
+    g = full;
+    const int rem = t - full * per;
+    J = rem / tail;
+    ii = rem - J * tail;
+  }
+  I = nIt - 1 - (g * kGroup + ii);
+}
 
 __device__ void raise_error(int* flags, int site) {
   atomicOr(&flags[kFlagKernel], kErrTimeout);
@@ -114,6 +138,33 @@ __device__ __forceinline__ bool wait_drain(uint64_t* bar, uint32_t parity) {
   return mbar_wait_bounded(bar, parity, &never, kDrainLimitNs);
 }
 
+__device__ __forceinline__ float two_sum(float a, float b, float& err) {
+  const float s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+  return s;
+}
+
+// Adds (u (aH + aR) + dg)^2 to the compensated sum (sum, comp).  The tensor
+// terms scale exactly by the power of two u; their sum and the FP64 diagonal
+// term (rounded once to FP32) join by error-free two-sums into hi + lo; hi^2 is
+// split exactly and 2 hi lo goes to the compensation.
+__device__ __forceinline__ void add_square(uint32_t aH, uint32_t aR, float u, double dg,
+                                           float& sum, float& comp) {
+  const float th = __fmul_rn(__uint_as_float(aH), u);
+  const float tr = __fmul_rn(__uint_as_float(aR), u);
+  const float dh = __double2float_rn(dg);
+  float e1, e2, e3;
+  const float s1 = two_sum(th, tr, e1);
+  const float hi = two_sum(s1, dh, e2);
+  const float lo = __fadd_rn(e1, e2);
+  const float pr = __fmul_rn(hi, hi);
+  const float pe = fmaf(hi, hi, -pr);
+  const float cr = __fmul_rn(__fmul_rn(2.f, hi), lo);
+  sum = two_sum(sum, pr, e3);
+  comp = __fadd_rn(comp, __fadd_rn(e3, __fadd_rn(pe, cr)));
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     trsm_gram_mixed_kernel(const __grid_constant__ CUtensorMap tmA,
                            const __grid_constant__ CUtensorMap tmB, const KParams kp) {
@@ -127,8 +178,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* drain = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  float* T = reinterpret_cast<float*>(base + kp.off_T);                  // x~ hi, 128 x 32
-  __nv_bfloat16* Tlo = reinterpret_cast<__nv_bfloat16*>(base + kp.off_T + BM * 32 * 4);  // lo
+  // per-item row data, double-buffered: u_r (128 floats) then Z diagonal blocks (128 x 4 doubles)
+  uint8_t* rows_base = base + kp.off_rows;
   double* dtab = reinterpret_cast<double*>(base + kp.off_tab);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -169,7 +220,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t g = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-        const int I = nIt - 1 - t / kp.nJ, J = t % kp.nJ;
+        int I, J;
+        decode_item(t, nIt, kp.nJ, I, J);
         const int kblocks = (I == kp.nI) ? 2 * kp.nI : 2 * (I + 1);
         for (int kb = 0; kb < kblocks; ++kb, ++g) {
           const int st = (int)(g % stages);
@@ -200,7 +252,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       int it = 0;
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
-        const int I = nIt - 1 - t / kp.nJ;
+        int I, J;
+        decode_item(t, nIt, kp.nJ, I, J);
         const int kblocks = (I == kp.nI) ? 2 * kp.nI : 2 * (I + 1);
         const int buf = it & 1;
         const uint32_t u = (uint32_t)it >> 1;
@@ -219,15 +272,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t sa = smem_u32(base + (size_t)st * kp.stage_bytes);
-          const uint32_t sbB = sa + (uint32_t)S * kTileBytes;
+          const uint32_t sz = smem_u32(base + (size_t)st * kp.stage_bytes);  // Z slices
+          const uint32_t sx = sz + (uint32_t)S * kTileBytes;                  // genotypes
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t bdesc = umma_desc_sw128(sbB + kk * 32);
+            const uint64_t adesc = umma_desc_sw128(sx + kk * 32);
             const uint32_t first = (kb | kk) != 0;
-            umma_f16(dH, umma_desc_sw128(sa + kk * 32), bdesc, kp.idesc, first);
+            umma_f16(dH, adesc, umma_desc_sw128(sz + kk * 32), kp.idesc, first);
             for (int s = 1; s < S; ++s)
-              umma_f16(dR, umma_desc_sw128(sa + s * kTileBytes + kk * 32), bdesc, kp.idesc,
+              umma_f16(dR, adesc, umma_desc_sw128(sz + s * kTileBytes + kk * 32), kp.idesc,
                        first | (s > 1));
           }
           umma_commit(&empty[st]);
@@ -242,34 +295,64 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ------------------------------------------------------------ epilogue
     const int quarter = warp & 3;            // TMEM lanes this warp may read
-    const int row = quarter * 32 + lane;     // row of the tile owned by this thread
-    const int et = threadIdx.x - 64;         // 0..127
-    const int gj = et >> 2, gg = et & 3;     // S_BR mapping: SNP column, row group
+    const int lrow = quarter * 32 + lane;    // accumulator lane = SNP within the tile
+    const int et = threadIdx.x - 64;         // 0..127: row of the block this thread stages
     const int p = kp.p;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
     int it = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
-      const int I = nIt - 1 - t / kp.nJ, J = t % kp.nJ;
+      int I, J;
+      decode_item(t, nIt, kp.nJ, I, J);
       const bool lin = (I == kp.nI);
       const int buf = it & 1;
       const uint32_t u = (uint32_t)it >> 1;
-      const int64_t r = (int64_t)I * BM + row;
-      const float ur = kp.rowscale[r];
-      double dz[kDiag];
-      int64_t r0 = 0;
+      const int64_t j = (int64_t)J * BN + lrow;
+      const bool jv = j < kp.k;
+      float* su = reinterpret_cast<float*>(rows_base + buf * (BM * 4 + BM * kDiag * 8));
+      double* sz = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(su) + BM * 4);
+      {
+        const int64_t r = (int64_t)I * BM + et;
+        su[et] = kp.rowscale[r];
+        if (!lin) {
 #pragma unroll
-      for (int q = 0; q < kDiag; ++q) dz[q] = 0.0;
-      if (!lin) {
+          for (int q = 0; q < kDiag; ++q) sz[et * kDiag + q] = kp.diagZ[r * kDiag + q];
+        }
+      }
+      uint4 xv[BM / 16];  // this SNP's genotypes of rows I*128 .. I*128+127
 #pragma unroll
-        for (int q = 0; q < kDiag; ++q) dz[q] = kp.diagZ[r * kDiag + q];
-        r0 = r - (r % kDiag);
+      for (int i = 0; i < BM / 16; ++i) xv[i] = make_uint4(0, 0, 0, 0);
+      if (!lin && jv) {
+        const uint4* src = reinterpret_cast<const uint4*>(kp.x8a + j * kp.npad + (int64_t)I * BM);
+#pragma unroll
+        for (int i = 0; i < BM / 16; ++i) xv[i] = __ldg(src + i);
       }
       const bool got = mbar_wait_bounded(&tfull[buf], u & 1, abort_flag, kWaitLimitNs);
-      if (!epilogue_all(got)) {  // all 128 threads leave together
+      if (!epilogue_all(got)) {  // all 128 threads leave together; also orders the row data
         if (!got && lane == 0) raise_error(kp.flags, 3);
         break;
       }
       tc_fence_after();
+      if (lin) {
+        // W^T block: column q < p holds (M^{-1}[X_L | y])_q^T x_j
+        uint32_t aH[32], aR[32];
+        tmem_ld32(lane_base + (uint32_t)buf * 256u, aH);
+        tmem_ld32(lane_base + (uint32_t)buf * 256u + 128u, aR);
+        tmem_ld_wait(aH);
+        tmem_ld_fence(aR);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
+        if (jv) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            if (q < p)
+              kp.Glin[(int64_t)q * kp.ldp + j] =
+                  (double)su[q] * ((double)__uint_as_float(aH[q]) + (double)__uint_as_float(aR[q]));
+        }
+        continue;
+      }
+      float sum = 0.f, comp = 0.f;
+#pragma unroll 1
       for (int c = 0; c < BN / 32; ++c) {
         uint32_t aH[32], aR[32];
         tmem_ld32(lane_base + (uint32_t)buf * 256u + (uint32_t)c * 32u, aH);
@@ -281,80 +364,28 @@ __global__ void __launch_bounds__(kThreads, 1)
           __syncwarp();
           if (lane == 0) mbar_arrive(&tempty[buf]);
         }
-        const int64_t jbase = (int64_t)J * BN + c * 32;
-        if (lin) {
-          // W^T block: lane q < p holds (M^{-1}[X_L | y])_q^T x_j for 32 SNPs
-          if (row < p) {
-            double* out = kp.Glin + (int64_t)row * kp.ldp;
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj) {
-              const int64_t j = jbase + jj;
-              if (j < kp.k)
-                out[j] = (double)ur * ((double)__uint_as_float(aH[jj]) +
-                                       (double)__uint_as_float(aR[jj]));
-            }
-          }
-          continue;
+        for (int g4 = 0; g4 < 8; ++g4) {
+          // rows 4*g4 .. 4*g4+3 of this chunk form one FP64 diagonal block
+          const int word = c * 8 + g4;  // genotype word: rows 4*word .. 4*word+3
+          const uint4 v4 = xv[word >> 2];
+          const uint32_t wv = (word & 3) == 0 ? v4.x : (word & 3) == 1 ? v4.y
+                            : (word & 3) == 2 ? v4.z : v4.w;
+          const double x0 = dtab[wv & 0xffu], x1 = dtab[(wv >> 8) & 0xffu];
+          const double x2 = dtab[(wv >> 16) & 0xffu], x3 = dtab[wv >> 24];
+          const int rl = c * 32 + g4 * 4;
+          const double* z = sz + rl * kDiag;
+          const double d0 = z[0] * x0;
+          const double d1 = fma(z[4], x0, z[5] * x1);
+          const double d2 = fma(z[8], x0, fma(z[9], x1, z[10] * x2));
+          const double d3 = fma(z[12], x0, fma(z[13], x1, fma(z[14], x2, z[15] * x3)));
+          add_square(aH[g4 * 4 + 0], aR[g4 * 4 + 0], su[rl + 0], d0, sum, comp);
+          add_square(aH[g4 * 4 + 1], aR[g4 * 4 + 1], su[rl + 1], d1, sum, comp);
+          add_square(aH[g4 * 4 + 2], aR[g4 * 4 + 2], su[rl + 2], d2, sum, comp);
+          add_square(aH[g4 * 4 + 3], aR[g4 * 4 + 3], su[rl + 3], d3, sum, comp);
         }
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-          const int64_t j = jbase + jj;
-          double dg = 0.0;
-          if (j < kp.k) {
-            const int8_t* xc = kp.x8 + j * kp.ldx8 + r0;
-#pragma unroll
-            for (int q = 0; q < kDiag; ++q)
-              if (r0 + q < kp.n) dg = fma(dz[q], dtab[(uint8_t)xc[q]], dg);
-          }
-          // x~ = u (acc_H + acc_R) + dg as an unevaluated float pair (hi, lo):
-          // both tensor terms scale exactly by the power of two u; their sum and
-          // the FP64 diagonal term (rounded once to FP32) join by error-free
-          // two-sums, so hi + lo carries the tensor part without FP32 rounding.
-          const float th = __fmul_rn(__uint_as_float(aH[jj]), ur);
-          const float tr = __fmul_rn(__uint_as_float(aR[jj]), ur);
-          const float dh = __double2float_rn(dg);
-          float s1 = __fadd_rn(th, tr);
-          float bp = __fsub_rn(s1, th);
-          const float e1 = __fadd_rn(__fsub_rn(th, __fsub_rn(s1, bp)), __fsub_rn(tr, bp));
-          const float s2 = __fadd_rn(s1, dh);
-          bp = __fsub_rn(s2, s1);
-          const float e2 = __fadd_rn(__fsub_rn(s1, __fsub_rn(s2, bp)), __fsub_rn(dh, bp));
-          T[row * 32 + (jj ^ lane)] = s2;
-          Tlo[row * 32 + (jj ^ lane)] = __float2bfloat16_rn(__fadd_rn(e1, e2));
-        }
-        named_barrier_sync(1, 128);
-        // S_BR partial: sum of (hi + lo)^2 over the 128 rows with error-free
-        // transforms in FP32 (hi^2 split exactly, the cross term 2 hi lo added
-        // to the compensation; lo^2 is below the FP32 resolution of the sum).
-        float sum = 0.f, comp = 0.f;
-        for (int i = 0; i < BM / 4; ++i) {
-          const int rr = gg + 4 * i;
-          const int at = rr * 32 + (gj ^ (rr & 31));
-          const float x = T[at];
-          const float xl = __bfloat162float(Tlo[at]);
-          const float pr = __fmul_rn(x, x);
-          const float pe = fmaf(x, x, -pr);  // x^2 = pr + pe exactly
-          const float cr = __fmul_rn(__fmul_rn(2.f, x), xl);
-          const float tt = __fadd_rn(sum, pr);
-          const float bq = __fsub_rn(tt, sum);
-          const float er = __fadd_rn(__fsub_rn(sum, __fsub_rn(tt, bq)), __fsub_rn(pr, bq));
-          sum = tt;
-          comp = __fadd_rn(comp, __fadd_rn(er, __fadd_rn(pe, cr)));
-        }
-#pragma unroll
-        for (int msk = 1; msk <= 2; msk <<= 1) {
-          const float so = __shfl_xor_sync(0xffffffffu, sum, msk);
-          const float co = __shfl_xor_sync(0xffffffffu, comp, msk);
-          const float tt = __fadd_rn(sum, so);
-          const float bp = __fsub_rn(tt, sum);
-          const float er = __fadd_rn(__fsub_rn(sum, __fsub_rn(tt, bp)), __fsub_rn(so, bp));
-          sum = tt;
-          comp = __fadd_rn(__fadd_rn(comp, co), er);
-        }
-        const int64_t j = jbase + gj;
-        if (gg == 0 && j < kp.k) kp.Pbr[(int64_t)I * kp.ldp + j] = (double)sum + (double)comp;
-        named_barrier_sync(1, 128);
       }
+      if (jv) kp.Pbr[(int64_t)I * kp.ldp + j] = (double)sum + (double)comp;
     }
   }
   tc_fence_before();
@@ -363,10 +394,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 1) tmem_dealloc(tmem, kTmemCols);
 }
 
-// X_R block (n x k int8, ldx) -> operand layout X16[j][c], c < npad (zero rows >= n).
+// X_R block (n x k int8, ldx) -> operand layout X16[j][c] (16-bit) and the
+// aligned byte copy X8a[j][c], c < npad (zero rows >= n).
 template <bool kBF16>
 __global__ void convert_x_kernel(const int8_t* __restrict__ x8, int64_t ldx, int64_t n,
-                                 int64_t k, int64_t npad, uint16_t* __restrict__ x16) {
+                                 int64_t k, int64_t npad, uint16_t* __restrict__ x16,
+                                 uint8_t* __restrict__ x8a) {
   const int64_t per_col = npad / 8;
   const int64_t total = k * per_col;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -374,10 +407,13 @@ __global__ void convert_x_kernel(const int8_t* __restrict__ x8, int64_t ldx, int
     const int64_t j = idx / per_col;
     const int64_t c0 = (idx - j * per_col) * 8;
     uint16_t v[8];
+    uint32_t b[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int64_t c = c0 + e;
-      const float xf = (c < n) ? (float)x8[c + j * ldx] : 0.f;
+      const int xi = (c < n) ? (int)x8[c + j * ldx] : 0;
+      b[e] = (uint32_t)(uint8_t)(int8_t)xi;
+      const float xf = (float)xi;
       v[e] = kBF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(xf))
                    : __half_as_ushort(__float2half_rn(xf));
     }
@@ -387,6 +423,10 @@ __global__ void convert_x_kernel(const int8_t* __restrict__ x8, int64_t ldx, int
     w.z = (uint32_t)v[4] | ((uint32_t)v[5] << 16);
     w.w = (uint32_t)v[6] | ((uint32_t)v[7] << 16);
     *reinterpret_cast<uint4*>(x16 + j * npad + c0) = w;
+    uint2 bb;
+    bb.x = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
+    bb.y = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
+    *reinterpret_cast<uint2*>(x8a + j * npad + c0) = bb;
   }
 }
 
@@ -579,6 +619,7 @@ struct MixedState {
   double* diagZ = nullptr;     // npad x kDiag
   double* Wm = nullptr;        // W = M^{-1} [X_L | y], npad x p
   uint16_t* x16 = nullptr;     // kmax x npad
+  uint8_t* x8a = nullptr;      // kmax x npad
   CUtensorMap tmA, tmB;
   KParams kp{};
   size_t smem = 0;
@@ -589,7 +630,7 @@ size_t mixed_footprint(int64_t n, int64_t npad, int p, int64_t kmax, int split_t
   (void)split_terms;
   size_t b = (size_t)3 * (npad + 128) * npad * 2;
   b += (size_t)(npad + 128) * 4 + (size_t)npad * (kDiag * 8 + 8 * p);
-  b += (size_t)kmax * npad * 2;
+  b += (size_t)kmax * npad * 3;
   return b;
 }
 
@@ -604,6 +645,7 @@ void mixed_free(MixedState* ms) {
   cudaFree(ms->diagZ);
   cudaFree(ms->Wm);
   cudaFree(ms->x16);
+  cudaFree(ms->x8a);
   delete ms;
 }
 
@@ -640,7 +682,8 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
       cudaMalloc(&ms->rowscale, rows * 4) != cudaSuccess ||
       cudaMalloc(&ms->diagZ, (size_t)npad * kDiag * 8) != cudaSuccess ||
       cudaMalloc(&ms->Wm, (size_t)npad * p * 8) != cudaSuccess ||
-      cudaMalloc(&ms->x16, (size_t)kmax * npad * 2) != cudaSuccess) {
+      cudaMalloc(&ms->x16, (size_t)kmax * npad * 2) != cudaSuccess ||
+      cudaMalloc(&ms->x8a, (size_t)kmax * npad) != cudaSuccess) {
     cudaGetLastError();
     return fail(GLS_ERR_OOM, "cudaMalloc of the mixed-precision operands failed");
   }
@@ -652,7 +695,8 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   }
   // Shared memory: stages of (S slices + genotype tile), then the epilogue buffers.
   const uint32_t stage_bytes = (uint32_t)(ms->S + 1) * kTileBytes;
-  const uint32_t epi = (uint32_t)(BM * 32 * 4 + BM * 32 * 2 + 256 * 8);
+  const uint32_t rows_bytes = 2u * (BM * 4 + BM * kDiag * 8);  // double-buffered row data
+  const uint32_t epi = rows_bytes + 256 * 8;
   const uint32_t bars = 8 * (2 * 4 + 5) + 16;
   int stages = 4;
   while (stages > 2 && (size_t)stages * stage_bytes + epi + bars + 1024 > (size_t)kMaxDynSmem)
@@ -662,14 +706,15 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   ms->stages = stages;
   KParams& kp = ms->kp;
   kp.stage_bytes = stage_bytes;
-  kp.off_T = (uint32_t)stages * stage_bytes;
-  kp.off_tab = kp.off_T + BM * 32 * 6;
+  kp.off_rows = (uint32_t)stages * stage_bytes;
+  kp.off_tab = kp.off_rows + rows_bytes;
   kp.off_bar = kp.off_tab + 256 * 8;
   ms->smem = (size_t)kp.off_bar + bars + 1024;
   kp.S = ms->S;
   kp.stages = stages;
   kp.p = p;
   kp.n = n;
+  kp.npad = npad;
   kp.idesc = umma_idesc_f16(BM, BN, ms->bf16);
   kp.rowscale = ms->rowscale;
   kp.diagZ = ms->diagZ;
@@ -739,9 +784,11 @@ cudaError_t mixed_convert(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_
   const int64_t work = k * (ms->npad / 8);
   const unsigned cgrid = (unsigned)std::min<int64_t>(ceil_div(work, 256), 65535 * 4);
   if (ms->bf16)
-    convert_x_kernel<true><<<cgrid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, ms->x16);
+    convert_x_kernel<true><<<cgrid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, ms->x16,
+                                                  ms->x8a);
   else
-    convert_x_kernel<false><<<cgrid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, ms->x16);
+    convert_x_kernel<false><<<cgrid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, ms->x16,
+                                                   ms->x8a);
   return cudaGetLastError();
 }
 
@@ -749,8 +796,9 @@ cudaError_t mixed_trsm_gram(MixedState* ms, const int8_t* xr, int64_t ldxr, int6
                             double* Pbr, double* Glin, int64_t ldp, int* flags, cudaStream_t st) {
   if (k <= 0) return cudaSuccess;
   KParams kp = ms->kp;
-  kp.x8 = xr;
-  kp.ldx8 = ldxr;
+  (void)xr;
+  (void)ldxr;
+  kp.x8a = ms->x8a;
   kp.k = k;
   kp.nI = (int)(ms->npad / BM);
   kp.nJ = (int)ceil_div(k, BN);
