@@ -32,15 +32,16 @@
 // cancellation; through the exact split they keep about 2^-25 relative to
 // each row's scale.)
 //
-// Kernel shape (one persistent CTA per SM, 192 threads):
+// Kernel shape (one persistent CTA per SM, 320 threads):
 //   warp 0      TMA producer: per stage the 128-SNP x 64 genotype tile and the S
 //               slices of Z (128 rows x 64 each), 128-byte swizzled, one mbarrier
 //   warp 1      TMEM allocator and the single thread issuing tcgen05.mma
 //               (M = 128 SNPs, N = 128 rows of x~, K = 16) into two
 //               double-buffered accumulator pairs; genotypes are operand A
-//   warps 2-5   epilogue, one SNP per thread (its TMEM lane): tcgen05.ld of 32
-//               rows at a time, the FP64 4 x 4 diagonal blocks from the SNP's own
-//               128 genotypes of the row block, and the S_BR sum in registers
+//   warps 2-9   epilogue, one SNP per thread (its TMEM lane), two warps per lane
+//               quarter each taking 64 of the 128 rows: tcgen05.ld of 32 rows at a
+//               time, the FP64 4 x 4 diagonal blocks from the SNP's own genotypes,
+//               and the S_BR sum in registers (the two halves meet in shared memory)
 // Work items (row block I, SNP tile J), I = 0..nI (I = nI is the W^T block), run
 // heaviest row blocks first in groups of kGroup row blocks x all SNP tiles, so
 // the concurrently running CTAs share both the Z slices of a few row blocks and
@@ -69,7 +70,8 @@ constexpr int BM = 128;                 // rows of x~ per tile (TMEM lanes)
 constexpr int BN = 128;                 // SNPs per tile (accumulator columns)
 constexpr int BK = 64;                  // K per stage: 64 x 16-bit = one 128-byte swizzle row
 constexpr int kTileBytes = BM * BK * 2;  // one A slice or the B tile per stage
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;             // two per TMEM lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kTmemCols = 512;     // 2 buffers x (acc_H + acc_R) x 128 columns
 constexpr int kMaxDynSmem = 232448;     // 227 KB
 constexpr int kDiag = 4;                // nd: FP64 diagonal block edge
@@ -91,7 +93,7 @@ struct KParams {
   double* Glin;           // S_BL and b_B, p x ldp
   int64_t ldp;
   int* flags;
-  uint32_t off_rows, off_tab, off_bar, stage_bytes;
+  uint32_t off_rows, off_tab, off_red, off_bar, stage_bytes;
 };
 
 // Work item t -> (row block I, SNP tile J): groups of kGroup row blocks, heaviest
@@ -119,16 +121,16 @@ __device__ void raise_error(int* flags, int site) {
   atomicExch(&flags[kFlagWhere], site);
 }
 
-// True when every one of the 128 epilogue threads passes ok = true (named barrier 1).
+// True when every epilogue thread passes ok = true (named barrier 1).
 __device__ __forceinline__ bool epilogue_all(bool ok) {
   uint32_t r;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\t"
       "setp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.and.pred q, 1, 128, p;\n\t"
+      "bar.red.and.pred q, 1, %2, p;\n\t"
       "selp.u32 %0, 1, 0, q;\n\t}"
       : "=r"(r)
-      : "r"((uint32_t)ok)
+      : "r"((uint32_t)ok), "r"(32 * kEpiWarps)
       : "memory");
   return r != 0;
 }
@@ -191,14 +193,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 4);
+      mbar_init(&tempty[b], kEpiWarps);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
     fence_barrier_init();
   }
   if (warp >= 2)
-    for (int i = threadIdx.x - 64; i < 256; i += 128) dtab[i] = (double)(int8_t)(uint8_t)i;
+    for (int i = threadIdx.x - 64; i < 256; i += 32 * kEpiWarps)
+      dtab[i] = (double)(int8_t)(uint8_t)i;
   if (warp == 1) {
     tmem_alloc(tmem_slot, kTmemCols);
     tmem_relinquish();
@@ -295,10 +298,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ------------------------------------------------------------ epilogue
     const int quarter = warp & 3;            // TMEM lanes this warp may read
+    const int half = (warp - 2) >> 2;        // which 64 of the 128 rows this warp handles
     const int lrow = quarter * 32 + lane;    // accumulator lane = SNP within the tile
-    const int et = threadIdx.x - 64;         // 0..127: row of the block this thread stages
+    const int et = threadIdx.x - 64;         // 0..255
     const int p = kp.p;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    float* red = reinterpret_cast<float*>(base + kp.off_red);  // [BM][2]
     int it = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
       int I, J;
@@ -310,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool jv = j < kp.k;
       float* su = reinterpret_cast<float*>(rows_base + buf * (BM * 4 + BM * kDiag * 8));
       double* sz = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(su) + BM * 4);
-      {
+      if (et < BM) {
         const int64_t r = (int64_t)I * BM + et;
         su[et] = kp.rowscale[r];
         if (!lin) {
@@ -318,48 +323,57 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int q = 0; q < kDiag; ++q) sz[et * kDiag + q] = kp.diagZ[r * kDiag + q];
         }
       }
-      uint4 xv[BM / 16];  // this SNP's genotypes of rows I*128 .. I*128+127
+      uint4 xv[BM / 32];  // this SNP's genotypes of the 64 rows this warp handles
 #pragma unroll
-      for (int i = 0; i < BM / 16; ++i) xv[i] = make_uint4(0, 0, 0, 0);
+      for (int i = 0; i < BM / 32; ++i) xv[i] = make_uint4(0, 0, 0, 0);
       if (!lin && jv) {
-        const uint4* src = reinterpret_cast<const uint4*>(kp.x8a + j * kp.npad + (int64_t)I * BM);
+        const uint4* src = reinterpret_cast<const uint4*>(kp.x8a + j * kp.npad +
+                                                          (int64_t)I * BM + half * 64);
 #pragma unroll
-        for (int i = 0; i < BM / 16; ++i) xv[i] = __ldg(src + i);
+        for (int i = 0; i < BM / 32; ++i) xv[i] = __ldg(src + i);
       }
       const bool got = mbar_wait_bounded(&tfull[buf], u & 1, abort_flag, kWaitLimitNs);
-      if (!epilogue_all(got)) {  // all 128 threads leave together; also orders the row data
+      if (!epilogue_all(got)) {  // all epilogue threads leave together; also orders the row data
         if (!got && lane == 0) raise_error(kp.flags, 3);
         break;
       }
       tc_fence_after();
       if (lin) {
         // W^T block: column q < p holds (M^{-1}[X_L | y])_q^T x_j
-        uint32_t aH[32], aR[32];
-        tmem_ld32(lane_base + (uint32_t)buf * 256u, aH);
-        tmem_ld32(lane_base + (uint32_t)buf * 256u + 128u, aR);
-        tmem_ld_wait(aH);
-        tmem_ld_fence(aR);
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[buf]);
-        if (jv) {
+        if (half == 0) {
+          uint32_t aH[32], aR[32];
+          tmem_ld32(lane_base + (uint32_t)buf * 256u, aH);
+          tmem_ld32(lane_base + (uint32_t)buf * 256u + 128u, aR);
+          tmem_ld_wait(aH);
+          tmem_ld_fence(aR);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[buf]);
+          if (jv) {
 #pragma unroll
-          for (int q = 0; q < 32; ++q)
-            if (q < p)
-              kp.Glin[(int64_t)q * kp.ldp + j] =
-                  (double)su[q] * ((double)__uint_as_float(aH[q]) + (double)__uint_as_float(aR[q]));
+            for (int q = 0; q < 32; ++q)
+              if (q < p)
+                kp.Glin[(int64_t)q * kp.ldp + j] =
+                    (double)su[q] *
+                    ((double)__uint_as_float(aH[q]) + (double)__uint_as_float(aR[q]));
+          }
+        } else {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[buf]);
         }
         continue;
       }
       float sum = 0.f, comp = 0.f;
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
+      for (int cc = 0; cc < 2; ++cc) {
+        const int c = half * 2 + cc;  // 32-row chunk of the item
         uint32_t aH[32], aR[32];
         tmem_ld32(lane_base + (uint32_t)buf * 256u + (uint32_t)c * 32u, aH);
         tmem_ld32(lane_base + (uint32_t)buf * 256u + 128u + (uint32_t)c * 32u, aR);
         tmem_ld_wait(aH);
         tmem_ld_fence(aR);
-        if (c == BN / 32 - 1) {
+        if (cc == 1) {
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&tempty[buf]);
@@ -367,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int g4 = 0; g4 < 8; ++g4) {
           // rows 4*g4 .. 4*g4+3 of this chunk form one FP64 diagonal block
-          const int word = c * 8 + g4;  // genotype word: rows 4*word .. 4*word+3
+          const int word = cc * 8 + g4;  // genotype word within this warp's 64 rows
           const uint4 v4 = xv[word >> 2];
           const uint32_t wv = (word & 3) == 0 ? v4.x : (word & 3) == 1 ? v4.y
                             : (word & 3) == 2 ? v4.z : v4.w;
@@ -385,7 +399,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           add_square(aH[g4 * 4 + 3], aR[g4 * 4 + 3], su[rl + 3], d3, sum, comp);
         }
       }
-      if (jv) kp.Pbr[(int64_t)I * kp.ldp + j] = (double)sum + (double)comp;
+      // the two halves of each SNP meet in shared memory; half 0 writes
+      if (half == 1) {
+        red[lrow * 2 + 0] = sum;
+        red[lrow * 2 + 1] = comp;
+      }
+      named_barrier_sync(1, 32 * kEpiWarps);
+      if (half == 0 && jv) {
+        float e;
+        const float s = two_sum(sum, red[lrow * 2 + 0], e);
+        const float cmp = __fadd_rn(__fadd_rn(comp, red[lrow * 2 + 1]), e);
+        kp.Pbr[(int64_t)I * kp.ldp + j] = (double)s + (double)cmp;
+      }
     }
   }
   tc_fence_before();
@@ -696,7 +721,7 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   // Shared memory: stages of (S slices + genotype tile), then the epilogue buffers.
   const uint32_t stage_bytes = (uint32_t)(ms->S + 1) * kTileBytes;
   const uint32_t rows_bytes = 2u * (BM * 4 + BM * kDiag * 8);  // double-buffered row data
-  const uint32_t epi = rows_bytes + 256 * 8;
+  const uint32_t epi = rows_bytes + 256 * 8 + BM * 2 * 4;
   const uint32_t bars = 8 * (2 * 4 + 5) + 16;
   int stages = 4;
   while (stages > 2 && (size_t)stages * stage_bytes + epi + bars + 1024 > (size_t)kMaxDynSmem)
@@ -708,7 +733,8 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   kp.stage_bytes = stage_bytes;
   kp.off_rows = (uint32_t)stages * stage_bytes;
   kp.off_tab = kp.off_rows + rows_bytes;
-  kp.off_bar = kp.off_tab + 256 * 8;
+  kp.off_red = kp.off_tab + 256 * 8;
+  kp.off_bar = kp.off_red + BM * 2 * 4;
   ms->smem = (size_t)kp.off_bar + bars + 1024;
   kp.S = ms->S;
   kp.stages = stages;
