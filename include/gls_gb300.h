@@ -135,6 +135,34 @@ gls_status_t gls_solve_block(gls_plan_t plan, const int8_t* XR, int64_t ldxr, in
 gls_status_t gls_solve_stream(gls_plan_t plan, const int8_t* XR, int64_t ldxr, int64_t m,
                               double* B, int64_t ldb, int32_t* snp_status);
 
+/*
+ * Batched uneven scans: several independent sequences (each its own plan, with
+ * its own M, n, p and SNP block) solved by ONE persistent launch of the
+ * mixed-precision blocked solve, so that small scans fill the GPU together.
+ * All plans must use the same mixed precision (BF16 or FP16) and split_terms,
+ * live on the same device, and be factored before gls_batch_solve.  At most 64
+ * plans.  The batch keeps pointers to the plans; destroy it before them.
+ */
+typedef struct gls_batch* gls_batch_t;
+
+gls_status_t gls_batch_create(const gls_plan_t* plans, int32_t nplans, gls_batch_t* out);
+
+/*
+ * One block per plan, all in one launch: plan i solves k[i] SNP columns of
+ * XR[i] (device memory, n_i x k[i] int8, ldxr[i] >= n_i) into B[i] (device,
+ * p_i x k[i], ldb[i] >= p_i) and snp_status[i] (device, may be NULL; the array
+ * snp_status itself may be NULL).  0 <= k[i] <= max_block_snps of plan i.
+ * group: row blocks per L2 rasterization group of the launch (0 = default 8;
+ * a tuning knob only, results do not depend on it).  Runs on the first plan's
+ * stream after the work already queued on every plan's stream, and returns
+ * when the launch has finished.  Errors: INVALID_ARG, STATE, CUDA, TIMEOUT.
+ */
+gls_status_t gls_batch_solve(gls_batch_t batch, const int8_t* const* XR, const int64_t* ldxr,
+                             const int64_t* k, double* const* B, const int64_t* ldb,
+                             int32_t* const* snp_status, int32_t group);
+
+gls_status_t gls_batch_destroy(gls_batch_t batch);
+
 /* Waits for all work of the plan (all its streams).  */
 gls_status_t gls_synchronize(gls_plan_t plan);
 

@@ -12,6 +12,8 @@ __host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return ceil_
 // FP64 factor/solve tile edge: L, L^{-1} and the FP64 blocked solve use 64 x 64 tiles.
 constexpr int kT = 64;
 constexpr int kMaxP = 32;
+// Largest number of problems one batched launch serves.
+constexpr int kMaxBatch = 64;
 
 // Device-side status words of a plan (one int32 each).
 enum FlagSlot : int {

@@ -38,5 +38,22 @@ cudaError_t mixed_trsm_gram(MixedState* ms, const int8_t* xr, int64_t ldxr, int6
 
 // Size of the FP64 diagonal blocks kept out of the tensor-core slices.
 int mixed_diag_block(const MixedState* ms);
+int mixed_split_terms(const MixedState* ms);
+bool mixed_is_bf16(const MixedState* ms);
+int64_t mixed_n(const MixedState* ms);
+
+// Several problems in one persistent launch.  Pbr / Glin / ldp are each
+// problem's partial buffers (as for mixed_trsm_gram); all states need the same
+// split and 16-bit type.  The genotypes of each problem must have been
+// converted (mixed_convert) on the launch stream before mixed_batch_run.
+struct MixedBatch;
+gls_status_t mixed_batch_create(MixedState* const* states, const double* const* Pbr,
+                                const double* const* Glin, const int64_t* ldp, int count,
+                                MixedBatch** out);
+void mixed_batch_free(MixedBatch* b);
+// k[i]: SNPs of problem i in this launch (input order); group: row blocks per
+// rasterization group (0 = default).
+cudaError_t mixed_batch_run(MixedBatch* b, const int64_t* k, int group, int* flags,
+                            cudaStream_t st);
 
 }  // namespace gls

@@ -726,6 +726,159 @@ gls_status_t gls_solve_stream(gls_plan_t pl, const int8_t* XR, int64_t ldxr, int
   return GLS_OK;
 }
 
+}  // extern "C"
+
+struct gls_batch {
+  std::vector<gls_plan*> plans;
+  gls::MixedBatch* mb = nullptr;
+  int* flags = nullptr;
+  cudaEvent_t ev = nullptr;
+  int device = 0;
+};
+
+extern "C" {
+
+gls_status_t gls_batch_create(const gls_plan_t* plans, int32_t nplans, gls_batch_t* out) {
+  g_last_error.clear();
+  if (!out) {
+    set_error("out is NULL");
+    return GLS_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (!plans || nplans < 1 || nplans > gls::kMaxBatch) {
+    set_error("nplans must be in [1, %d]", gls::kMaxBatch);
+    return GLS_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < nplans; ++i) {
+    if (!plans[i] || plans[i]->precision == GLS_PREC_FP64 || !plans[i]->mixed) {
+      set_error("plan %d is NULL or not a mixed-precision plan", i);
+      return GLS_ERR_INVALID_ARG;
+    }
+    if (plans[i]->device != plans[0]->device) {
+      set_error("plans of a batch must share one device");
+      return GLS_ERR_INVALID_ARG;
+    }
+  }
+  DeviceGuard guard(plans[0]->device);
+  std::vector<gls::MixedState*> st(nplans);
+  std::vector<const double*> pbr(nplans), glin(nplans);
+  std::vector<int64_t> ldp(nplans);
+  for (int i = 0; i < nplans; ++i) {
+    st[i] = plans[i]->mixed;
+    pbr[i] = plans[i]->partials;
+    glin[i] = plans[i]->partials + (int64_t)plans[i]->nI * plans[i]->ldp;
+    ldp[i] = plans[i]->ldp;
+  }
+  gls_batch* b = new gls_batch();
+  b->device = plans[0]->device;
+  b->plans.assign(plans, plans + nplans);
+  gls_status_t s = gls::mixed_batch_create(st.data(), pbr.data(), glin.data(), ldp.data(), nplans,
+                                           &b->mb);
+  if (s != GLS_OK) {
+    set_error("%s", gls::mixed_last_error());
+    delete b;
+    return s;
+  }
+  if (cudaMalloc(&b->flags, sizeof(int) * gls::kFlagCount) != cudaSuccess ||
+      cudaMemset(b->flags, 0, sizeof(int) * gls::kFlagCount) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    gls::mixed_batch_free(b->mb);
+    cudaFree(b->flags);
+    delete b;
+    set_error("batch allocation failed");
+    return GLS_ERR_OOM;
+  }
+  *out = b;
+  return GLS_OK;
+}
+
+gls_status_t gls_batch_solve(gls_batch_t b, const int8_t* const* XR, const int64_t* ldxr,
+                             const int64_t* k, double* const* B, const int64_t* ldb,
+                             int32_t* const* snp_status, int32_t group) {
+  g_last_error.clear();
+  if (!b || !XR || !ldxr || !k || !B || !ldb || group < 0) {
+    set_error("NULL batch or argument array, or negative group");
+    return GLS_ERR_INVALID_ARG;
+  }
+  const int count = (int)b->plans.size();
+  for (int i = 0; i < count; ++i) {
+    gls_plan* pl = b->plans[i];
+    if (!pl->factored) {
+      set_error("plan %d of the batch has no successful gls_factor", i);
+      return GLS_ERR_STATE;
+    }
+    if (k[i] < 0 || k[i] > pl->kmax) {
+      set_error("k[%d] = %lld outside [0, max_block_snps]", i, (long long)k[i]);
+      return GLS_ERR_INVALID_ARG;
+    }
+    if (k[i] == 0) continue;
+    if (!XR[i] || !B[i] || ldxr[i] < pl->n || ldb[i] < pl->p) {
+      set_error("plan %d: bad XR/B pointer or leading dimension", i);
+      return GLS_ERR_INVALID_ARG;
+    }
+    if (classify(XR[i]) != Mem::Device || classify(B[i]) != Mem::Device ||
+        (snp_status && snp_status[i] && classify(snp_status[i]) != Mem::Device)) {
+      set_error("plan %d: batched solves take device buffers only", i);
+      return GLS_ERR_INVALID_ARG;
+    }
+  }
+  DeviceGuard guard(b->device);
+  gls_plan* p0 = b->plans[0];
+  cudaStream_t st = p0->stream;
+  // order after the work already queued on every plan's stream
+  for (int i = 1; i < count; ++i) {
+    GLS_CUDA(cudaEventRecord(b->ev, b->plans[i]->stream));
+    GLS_CUDA(cudaStreamWaitEvent(st, b->ev, 0));
+  }
+  GLS_CUDA(cudaMemsetAsync(b->flags, 0, sizeof(int) * gls::kFlagCount, st));
+  for (int i = 0; i < count; ++i) {
+    if (k[i] == 0) continue;
+    Timed t(p0, &p0->t_convert);
+    GLS_CUDA(gls::mixed_convert(b->plans[i]->mixed, XR[i], ldxr[i], k[i], st));
+    p0->launches += 1;
+  }
+  {
+    Timed t(p0, &p0->t_trsm);
+    GLS_CUDA(gls::mixed_batch_run(b->mb, k, group, b->flags, st));
+    p0->launches += 1;
+  }
+  for (int i = 0; i < count; ++i) {
+    if (k[i] == 0) continue;
+    gls_plan* pl = b->plans[i];
+    Timed t(p0, &p0->t_solve);
+    gls::launch_assemble_solve_split(pl->partials + (int64_t)pl->nI * pl->ldp, pl->partials,
+                                     pl->ldp, pl->nI, pl->p, k[i], pl->RTL, pl->zT,
+                                     gls::kTauMixed, B[i], ldb[i],
+                                     snp_status ? snp_status[i] : nullptr, st);
+    p0->launches += 1;
+  }
+  GLS_CUDA(cudaGetLastError());
+  GLS_CUDA(cudaEventRecord(b->ev, st));
+  for (int i = 1; i < count; ++i) GLS_CUDA(cudaStreamWaitEvent(b->plans[i]->stream, b->ev, 0));
+  int hf[gls::kFlagCount];
+  GLS_CUDA(cudaMemcpyAsync(hf, b->flags, sizeof(hf), cudaMemcpyDeviceToHost, st));
+  GLS_CUDA(cudaStreamSynchronize(st));
+  if (hf[gls::kFlagKernel] & gls::kErrTimeout) {
+    set_error("a bounded device wait gave up (site %d)", hf[gls::kFlagWhere]);
+    return GLS_ERR_TIMEOUT;
+  }
+  return GLS_OK;
+}
+
+gls_status_t gls_batch_destroy(gls_batch_t b) {
+  g_last_error.clear();
+  if (!b) return GLS_OK;
+  DeviceGuard guard(b->device);
+  if (!b->plans.empty()) cudaStreamSynchronize(b->plans[0]->stream);
+  gls::mixed_batch_free(b->mb);
+  cudaFree(b->flags);
+  if (b->ev) cudaEventDestroy(b->ev);
+  cudaGetLastError();
+  delete b;
+  return GLS_OK;
+}
+
 gls_status_t gls_synchronize(gls_plan_t pl) {
   g_last_error.clear();
   if (!pl) {

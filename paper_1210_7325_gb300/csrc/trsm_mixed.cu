@@ -43,9 +43,15 @@
 //               time, the FP64 4 x 4 diagonal blocks from the SNP's own genotypes,
 //               and the S_BR sum in registers (the two halves meet in shared memory)
 // Work items (row block I, SNP tile J), I = 0..nI (I = nI is the W^T block), run
-// heaviest row blocks first in groups of kGroup row blocks x all SNP tiles, so
+// heaviest row blocks first in groups of `group` row blocks x all SNP tiles, so
 // the concurrently running CTAs share both the Z slices of a few row blocks and
 // the genotype panels of a few dozen SNP tiles in L2.
+//
+// One launch can serve many independent problems (scans with their own M, n,
+// p and SNP block): each problem has a descriptor in device memory (its TMA
+// maps and buffers) and the launch's by-value run parameters give each
+// problem's block size and the prefix of its work items; the persistent CTAs
+// walk the concatenated item list, largest problems first.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -53,8 +59,11 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <string.h>
+
 #include <algorithm>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 #include "mixed.cuh"
@@ -77,43 +86,79 @@ constexpr int kMaxDynSmem = 232448;     // 227 KB
 constexpr int kDiag = 4;                // nd: FP64 diagonal block edge
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // bounded waits give up after 1 s
 constexpr uint64_t kDrainLimitNs = 100000000ull;
-constexpr int kGroup = 8;               // row blocks per rasterization group
+constexpr int kDefaultGroup = 8;        // row blocks per rasterization group
 
 thread_local std::string g_err;
 
-struct KParams {
+// Per-problem constants, in device memory (64-byte aligned for the TMA maps).
+struct alignas(64) ProblemDesc {
+  CUtensorMap tmA;        // slices of Z and W^T: (npad, npad + 128, S), 16-bit
+  CUtensorMap tmB;        // genotype operand X16: (npad, kmax), 16-bit
   const uint8_t* x8a;     // genotypes as bytes, SNP-major [j][npad], zero rows >= n
-  int64_t npad;
-  int64_t n, k;
-  int nI, nJ, p, S, stages;
-  uint32_t idesc;
   const float* rowscale;  // u_r, npad + 128 rows
   const double* diagZ;    // npad x kDiag
   double* Pbr;            // S_BR partials, nI x ldp
   double* Glin;           // S_BL and b_B, p x ldp
-  int64_t ldp;
+  int64_t npad, ldp;
+  int nI, p;
+};
+
+// Per-launch values, by value: each problem's block size and item range.
+struct RunParams {
+  int nprob, total, group;
+  int nJ[kMaxBatch];
+  int item_begin[kMaxBatch + 1];
+  int64_t k[kMaxBatch];
+};
+
+struct KConst {
+  int S, stages;
+  uint32_t idesc;
   int* flags;
   uint32_t off_rows, off_tab, off_red, off_bar, stage_bytes;
 };
 
-// Work item t -> (row block I, SNP tile J): groups of kGroup row blocks, heaviest
-// first; within a group SNP tiles advance slowest, row blocks fastest.
-__device__ __forceinline__ void decode_item(int t, int nIt, int nJ, int& I, int& J) {
-  const int per = kGroup * nJ;
-  const int full = nIt / kGroup, tail = nIt - full * kGroup;
+// Work item t of one problem -> (row block I, SNP tile J): groups of `group` row
+// blocks, heaviest first; within a group SNP tiles advance slowest.
+__device__ __forceinline__ void decode_item(int t, int nIt, int nJ, int group, int& I, int& J) {
+  const int per = group * nJ;
+  const int full = nIt / group, tail = nIt - full * group;
   int g, ii;
   if (t < full * per) {
     g = t / per;
     const int rem = t - g * per;
-    J = rem / kGroup;
-    ii = rem - J * kGroup;
+    J = rem / group;
+    ii = rem - J * group;
   } else {
     g = full;
     const int rem = t - full * per;
     J = rem / tail;
     ii = rem - J * tail;
   }
-  I = nIt - 1 - (g * kGroup + ii);
+  I = nIt - 1 - (g * group + ii);
+}
+
+// Global item t -> problem index (the item ranges are in ascending order).
+__device__ __forceinline__ int find_problem(const RunParams& run, int t) {
+  int lo = 0, hi = run.nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (run.item_begin[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+struct Item {
+  int pi, I, J, nI;
+};
+
+__device__ __forceinline__ Item item_at(const ProblemDesc* probs, const RunParams& run, int t) {
+  Item w;
+  w.pi = find_problem(run, t);
+  w.nI = probs[w.pi].nI;
+  decode_item(t - run.item_begin[w.pi], w.nI + 1, run.nJ[w.pi], run.group, w.I, w.J);
+  return w;
 }
 
 __device__ void raise_error(int* flags, int site) {
@@ -168,24 +213,24 @@ __device__ __forceinline__ void add_square(uint32_t aH, uint32_t aR, float u, do
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-    trsm_gram_mixed_kernel(const __grid_constant__ CUtensorMap tmA,
-                           const __grid_constant__ CUtensorMap tmB, const KParams kp) {
+    trsm_gram_mixed_kernel(const ProblemDesc* __restrict__ probs,
+                           const __grid_constant__ RunParams run, const KConst kc) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-  uint64_t* full = reinterpret_cast<uint64_t*>(base + kp.off_bar);
-  uint64_t* empty = full + kp.stages;
-  uint64_t* tfull = empty + kp.stages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + kc.off_bar);
+  uint64_t* empty = full + kc.stages;
+  uint64_t* tfull = empty + kc.stages;
   uint64_t* tempty = tfull + 2;
   uint64_t* drain = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   // per-item row data, double-buffered: u_r (128 floats) then Z diagonal blocks (128 x 4 doubles)
-  uint8_t* rows_base = base + kp.off_rows;
-  double* dtab = reinterpret_cast<double*>(base + kp.off_tab);
+  uint8_t* rows_base = base + kc.off_rows;
+  double* dtab = reinterpret_cast<double*>(base + kc.off_tab);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int S = kp.S, stages = kp.stages;
+  const int S = kc.S, stages = kc.stages;
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
@@ -206,42 +251,43 @@ __global__ void __launch_bounds__(kThreads, 1)
     tmem_alloc(tmem_slot, kTmemCols);
     tmem_relinquish();
   }
-  if (threadIdx.x == 0) {
-    tma_prefetch_desc(&tmA);
-    tma_prefetch_desc(&tmB);
-  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int nIt = kp.nI + 1;  // row blocks of Z plus the W^T block
-  const int total = nIt * kp.nJ;
+  const int total = run.total;
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       uint32_t g = 0;
       bool ok = true;
+      int last_pi = -1;
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-        int I, J;
-        decode_item(t, nIt, kp.nJ, I, J);
-        const int kblocks = (I == kp.nI) ? 2 * kp.nI : 2 * (I + 1);
+        const Item w = item_at(probs, run, t);
+        const ProblemDesc* pd = probs + w.pi;
+        if (w.pi != last_pi) {
+          tma_prefetch_desc(&pd->tmA);
+          tma_prefetch_desc(&pd->tmB);
+          last_pi = w.pi;
+        }
+        const int kblocks = (w.I == w.nI) ? 2 * w.nI : 2 * (w.I + 1);
         for (int kb = 0; kb < kblocks; ++kb, ++g) {
           const int st = (int)(g % stages);
-          const uint32_t w = g / stages;
-          if (!mbar_wait_bounded(&empty[st], (w & 1) ^ 1, abort_flag, kWaitLimitNs)) {
+          const uint32_t ph = g / stages;
+          if (!mbar_wait_bounded(&empty[st], (ph & 1) ^ 1, abort_flag, kWaitLimitNs)) {
             ok = false;
             break;
           }
           mbar_arrive_expect_tx(&full[st], (uint32_t)(S + 1) * kTileBytes);
-          uint8_t* sb = base + (size_t)st * kp.stage_bytes;
+          uint8_t* sb = base + (size_t)st * kc.stage_bytes;
           for (int s = 0; s < S; ++s)
-            tma_load_3d(sb + s * kTileBytes, &tmA, &full[st], kb * BK, I * BM, s);
-          tma_load_2d(sb + S * kTileBytes, &tmB, &full[st], kb * BK, J * BN);
+            tma_load_3d(sb + s * kTileBytes, &pd->tmA, &full[st], kb * BK, w.I * BM, s);
+          tma_load_2d(sb + S * kTileBytes, &pd->tmB, &full[st], kb * BK, w.J * BN);
         }
       }
       if (!ok) {
-        raise_error(kp.flags, 1);
+        raise_error(kc.flags, 1);
         // let the loads already issued land before the CTA's shared memory goes away
         const uint32_t first = g > (uint32_t)stages ? g - stages : 0;
         for (uint32_t g2 = first; g2 < g; ++g2)
@@ -255,9 +301,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       int it = 0;
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
-        int I, J;
-        decode_item(t, nIt, kp.nJ, I, J);
-        const int kblocks = (I == kp.nI) ? 2 * kp.nI : 2 * (I + 1);
+        const Item w = item_at(probs, run, t);
+        const int kblocks = (w.I == w.nI) ? 2 * w.nI : 2 * (w.I + 1);
         const int buf = it & 1;
         const uint32_t u = (uint32_t)it >> 1;
         if (!mbar_wait_bounded(&tempty[buf], (u & 1) ^ 1, abort_flag, kWaitLimitNs)) {
@@ -269,28 +314,28 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t dR = dH + 128u;
         for (int kb = 0; kb < kblocks; ++kb, ++g) {
           const int st = (int)(g % stages);
-          const uint32_t w = g / stages;
-          if (!mbar_wait_bounded(&full[st], w & 1, abort_flag, kWaitLimitNs)) {
+          const uint32_t ph = g / stages;
+          if (!mbar_wait_bounded(&full[st], ph & 1, abort_flag, kWaitLimitNs)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t sz = smem_u32(base + (size_t)st * kp.stage_bytes);  // Z slices
+          const uint32_t sz = smem_u32(base + (size_t)st * kc.stage_bytes);  // Z slices
           const uint32_t sx = sz + (uint32_t)S * kTileBytes;                  // genotypes
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint64_t adesc = umma_desc_sw128(sx + kk * 32);
             const uint32_t first = (kb | kk) != 0;
-            umma_f16(dH, adesc, umma_desc_sw128(sz + kk * 32), kp.idesc, first);
+            umma_f16(dH, adesc, umma_desc_sw128(sz + kk * 32), kc.idesc, first);
             for (int s = 1; s < S; ++s)
-              umma_f16(dR, adesc, umma_desc_sw128(sz + s * kTileBytes + kk * 32), kp.idesc,
+              umma_f16(dR, adesc, umma_desc_sw128(sz + s * kTileBytes + kk * 32), kc.idesc,
                        first | (s > 1));
           }
           umma_commit(&empty[st]);
         }
         if (ok) umma_commit(&tfull[buf]);
       }
-      if (!ok) raise_error(kp.flags, 2);
+      if (!ok) raise_error(kc.flags, 2);
       // every issued MMA completes before the accumulators are released
       umma_commit(drain);
       wait_drain(drain, 0);
@@ -301,40 +346,43 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int half = (warp - 2) >> 2;        // which 64 of the 128 rows this warp handles
     const int lrow = quarter * 32 + lane;    // accumulator lane = SNP within the tile
     const int et = threadIdx.x - 64;         // 0..255
-    const int p = kp.p;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-    float* red = reinterpret_cast<float*>(base + kp.off_red);  // [BM][2]
+    float* red = reinterpret_cast<float*>(base + kc.off_red);  // [BM][2]
     int it = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
-      int I, J;
-      decode_item(t, nIt, kp.nJ, I, J);
-      const bool lin = (I == kp.nI);
+      const Item w = item_at(probs, run, t);
+      const ProblemDesc* pd = probs + w.pi;
+      const int I = w.I, J = w.J;
+      const bool lin = (I == w.nI);
+      const int p = pd->p;
+      const int64_t kk_j = run.k[w.pi];
+      const int64_t ldp = pd->ldp;
       const int buf = it & 1;
       const uint32_t u = (uint32_t)it >> 1;
       const int64_t j = (int64_t)J * BN + lrow;
-      const bool jv = j < kp.k;
+      const bool jv = j < kk_j;
       float* su = reinterpret_cast<float*>(rows_base + buf * (BM * 4 + BM * kDiag * 8));
       double* sz = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(su) + BM * 4);
       if (et < BM) {
         const int64_t r = (int64_t)I * BM + et;
-        su[et] = kp.rowscale[r];
+        su[et] = pd->rowscale[r];
         if (!lin) {
 #pragma unroll
-          for (int q = 0; q < kDiag; ++q) sz[et * kDiag + q] = kp.diagZ[r * kDiag + q];
+          for (int q = 0; q < kDiag; ++q) sz[et * kDiag + q] = pd->diagZ[r * kDiag + q];
         }
       }
       uint4 xv[BM / 32];  // this SNP's genotypes of the 64 rows this warp handles
 #pragma unroll
       for (int i = 0; i < BM / 32; ++i) xv[i] = make_uint4(0, 0, 0, 0);
       if (!lin && jv) {
-        const uint4* src = reinterpret_cast<const uint4*>(kp.x8a + j * kp.npad +
+        const uint4* src = reinterpret_cast<const uint4*>(pd->x8a + j * pd->npad +
                                                           (int64_t)I * BM + half * 64);
 #pragma unroll
         for (int i = 0; i < BM / 32; ++i) xv[i] = __ldg(src + i);
       }
       const bool got = mbar_wait_bounded(&tfull[buf], u & 1, abort_flag, kWaitLimitNs);
       if (!epilogue_all(got)) {  // all epilogue threads leave together; also orders the row data
-        if (!got && lane == 0) raise_error(kp.flags, 3);
+        if (!got && lane == 0) raise_error(kc.flags, 3);
         break;
       }
       tc_fence_after();
@@ -353,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int q = 0; q < 32; ++q)
               if (q < p)
-                kp.Glin[(int64_t)q * kp.ldp + j] =
+                pd->Glin[(int64_t)q * ldp + j] =
                     (double)su[q] *
                     ((double)__uint_as_float(aH[q]) + (double)__uint_as_float(aR[q]));
           }
@@ -409,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         float e;
         const float s = two_sum(sum, red[lrow * 2 + 0], e);
         const float cmp = __fadd_rn(__fadd_rn(comp, red[lrow * 2 + 1]), e);
-        kp.Pbr[(int64_t)I * kp.ldp + j] = (double)s + (double)cmp;
+        pd->Pbr[(int64_t)I * ldp + j] = (double)s + (double)cmp;
       }
     }
   }
@@ -645,17 +693,41 @@ struct MixedState {
   double* Wm = nullptr;        // W = M^{-1} [X_L | y], npad x p
   uint16_t* x16 = nullptr;     // kmax x npad
   uint8_t* x8a = nullptr;      // kmax x npad
-  CUtensorMap tmA, tmB;
-  KParams kp{};
+  ProblemDesc desc;            // host copy (buffers filled in by the plan per call)
+  ProblemDesc* d_desc = nullptr;  // device copy used by single-problem launches
+  double* d_Pbr = nullptr;     // buffers the device copy currently points to
+  double* d_Glin = nullptr;
+  KConst kc{};
   size_t smem = 0;
 };
+
+struct MixedBatch {
+  std::vector<MixedState*> states;  // launch order (largest n first)
+  std::vector<int> order;           // states[i] = input[order[i]]
+  ProblemDesc* d_desc = nullptr;
+  std::vector<double*> Pbr, Glin;
+};
+
+namespace {
+
+size_t smem_bytes(int S, int stages) {
+  const uint32_t stage_bytes = (uint32_t)(S + 1) * kTileBytes;
+  const uint32_t rows_bytes = 2u * (BM * 4 + BM * kDiag * 8);
+  const uint32_t epi = rows_bytes + 256 * 8 + BM * 2 * 4;
+  const uint32_t bars = 8 * (2 * 4 + 5) + 16;
+  return (size_t)stages * stage_bytes + epi + bars + 1024;
+}
+
+bool g_attr_done = false;
+
+}  // namespace
 
 size_t mixed_footprint(int64_t n, int64_t npad, int p, int64_t kmax, int split_terms) {
   (void)n;
   (void)split_terms;
   size_t b = (size_t)3 * (npad + 128) * npad * 2;
   b += (size_t)(npad + 128) * 4 + (size_t)npad * (kDiag * 8 + 8 * p);
-  b += (size_t)kmax * npad * 3;
+  b += (size_t)kmax * npad * 3 + sizeof(ProblemDesc);
   return b;
 }
 
@@ -671,6 +743,7 @@ void mixed_free(MixedState* ms) {
   cudaFree(ms->Wm);
   cudaFree(ms->x16);
   cudaFree(ms->x8a);
+  cudaFree(ms->d_desc);
   delete ms;
 }
 
@@ -708,7 +781,8 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
       cudaMalloc(&ms->diagZ, (size_t)npad * kDiag * 8) != cudaSuccess ||
       cudaMalloc(&ms->Wm, (size_t)npad * p * 8) != cudaSuccess ||
       cudaMalloc(&ms->x16, (size_t)kmax * npad * 2) != cudaSuccess ||
-      cudaMalloc(&ms->x8a, (size_t)kmax * npad) != cudaSuccess) {
+      cudaMalloc(&ms->x8a, (size_t)kmax * npad) != cudaSuccess ||
+      cudaMalloc(&ms->d_desc, sizeof(ProblemDesc)) != cudaSuccess) {
     cudaGetLastError();
     return fail(GLS_ERR_OOM, "cudaMalloc of the mixed-precision operands failed");
   }
@@ -718,47 +792,41 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
     cudaGetLastError();
     return fail(GLS_ERR_CUDA, "cudaMemset of the operand slices failed");
   }
-  // Shared memory: stages of (S slices + genotype tile), then the epilogue buffers.
-  const uint32_t stage_bytes = (uint32_t)(ms->S + 1) * kTileBytes;
-  const uint32_t rows_bytes = 2u * (BM * 4 + BM * kDiag * 8);  // double-buffered row data
-  const uint32_t epi = rows_bytes + 256 * 8 + BM * 2 * 4;
-  const uint32_t bars = 8 * (2 * 4 + 5) + 16;
   int stages = 4;
-  while (stages > 2 && (size_t)stages * stage_bytes + epi + bars + 1024 > (size_t)kMaxDynSmem)
-    --stages;
-  if ((size_t)stages * stage_bytes + epi + bars + 1024 > (size_t)kMaxDynSmem)
+  while (stages > 2 && smem_bytes(ms->S, stages) > (size_t)kMaxDynSmem) --stages;
+  if (smem_bytes(ms->S, stages) > (size_t)kMaxDynSmem)
     return fail(GLS_ERR_UNSUPPORTED, "shared-memory budget exceeded for this split");
   ms->stages = stages;
-  KParams& kp = ms->kp;
-  kp.stage_bytes = stage_bytes;
-  kp.off_rows = (uint32_t)stages * stage_bytes;
-  kp.off_tab = kp.off_rows + rows_bytes;
-  kp.off_red = kp.off_tab + 256 * 8;
-  kp.off_bar = kp.off_red + BM * 2 * 4;
-  ms->smem = (size_t)kp.off_bar + bars + 1024;
-  kp.S = ms->S;
-  kp.stages = stages;
-  kp.p = p;
-  kp.n = n;
-  kp.npad = npad;
-  kp.idesc = umma_idesc_f16(BM, BN, ms->bf16);
-  kp.rowscale = ms->rowscale;
-  kp.diagZ = ms->diagZ;
-  if (cudaFuncSetAttribute(trsm_gram_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)ms->smem) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(GLS_ERR_CUDA, "cudaFuncSetAttribute (shared memory) failed");
+  ms->smem = smem_bytes(ms->S, stages);
+  KConst& kc = ms->kc;
+  kc.S = ms->S;
+  kc.stages = stages;
+  kc.stage_bytes = (uint32_t)(ms->S + 1) * kTileBytes;
+  kc.off_rows = (uint32_t)stages * kc.stage_bytes;
+  kc.off_tab = kc.off_rows + 2u * (BM * 4 + BM * kDiag * 8);
+  kc.off_red = kc.off_tab + 256 * 8;
+  kc.off_bar = kc.off_red + BM * 2 * 4;
+  kc.idesc = umma_idesc_f16(BM, BN, ms->bf16);
+  if (!g_attr_done) {
+    if (cudaFuncSetAttribute(trsm_gram_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kMaxDynSmem) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(GLS_ERR_CUDA, "cudaFuncSetAttribute (shared memory) failed");
+    }
+    g_attr_done = true;
   }
   PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
   if (!enc) return fail(GLS_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
   const CUtensorMapDataType dt =
       ms->bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  ProblemDesc& d = ms->desc;
+  memset(&d, 0, sizeof(d));
   {
     cuuint64_t dims[3] = {(cuuint64_t)npad, (cuuint64_t)rows, (cuuint64_t)ms->S};
     cuuint64_t strides[2] = {(cuuint64_t)npad * 2, (cuuint64_t)rows * npad * 2};
     cuuint32_t box[3] = {BK, BM, 1};
     cuuint32_t es[3] = {1, 1, 1};
-    if (enc(&ms->tmA, dt, 3, ms->slices, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    if (enc(&d.tmA, dt, 3, ms->slices, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return fail(GLS_ERR_CUDA, "tensor map encode (slices) failed");
@@ -768,11 +836,17 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
     cuuint64_t strides[1] = {(cuuint64_t)npad * 2};
     cuuint32_t box[2] = {BK, BN};
     cuuint32_t es[2] = {1, 1};
-    if (enc(&ms->tmB, dt, 2, ms->x16, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    if (enc(&d.tmB, dt, 2, ms->x16, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return fail(GLS_ERR_CUDA, "tensor map encode (genotypes) failed");
   }
+  d.x8a = ms->x8a;
+  d.rowscale = ms->rowscale;
+  d.diagZ = ms->diagZ;
+  d.npad = npad;
+  d.nI = (int)(npad / BM);
+  d.p = p;
   *out = ms;
   return GLS_OK;
 }
@@ -818,24 +892,120 @@ cudaError_t mixed_convert(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_
   return cudaGetLastError();
 }
 
+namespace {
+
+int items_of(const MixedState* ms, int64_t k) {
+  return (int)(ms->npad / BM + 1) * (int)ceil_div(k, BN);
+}
+
+cudaError_t launch(const MixedState* ms0, const ProblemDesc* d_desc, const RunParams& run,
+                   int* flags, cudaStream_t st) {
+  KConst kc = ms0->kc;
+  kc.flags = flags;
+  const int grid = std::min(ms0->num_sms, std::max(run.total, 1));
+  trsm_gram_mixed_kernel<<<grid, kThreads, ms0->smem, st>>>(d_desc, run, kc);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t mixed_trsm_gram(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,
                             double* Pbr, double* Glin, int64_t ldp, int* flags, cudaStream_t st) {
-  if (k <= 0) return cudaSuccess;
-  KParams kp = ms->kp;
   (void)xr;
   (void)ldxr;
-  kp.x8a = ms->x8a;
-  kp.k = k;
-  kp.nI = (int)(ms->npad / BM);
-  kp.nJ = (int)ceil_div(k, BN);
-  kp.Pbr = Pbr;
-  kp.Glin = Glin;
-  kp.ldp = ldp;
-  kp.flags = flags;
-  const int total = (kp.nI + 1) * kp.nJ;
-  const int grid = std::min(ms->num_sms, total);
-  trsm_gram_mixed_kernel<<<grid, kThreads, ms->smem, st>>>(ms->tmA, ms->tmB, kp);
-  return cudaGetLastError();
+  if (k <= 0) return cudaSuccess;
+  if (Pbr != ms->d_Pbr || Glin != ms->d_Glin || ms->desc.ldp != ldp) {
+    ms->desc.Pbr = Pbr;
+    ms->desc.Glin = Glin;
+    ms->desc.ldp = ldp;
+    cudaError_t e = cudaMemcpyAsync(ms->d_desc, &ms->desc, sizeof(ProblemDesc),
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(st);  // the host copy may change on a later call
+    if (e != cudaSuccess) return e;
+    ms->d_Pbr = Pbr;
+    ms->d_Glin = Glin;
+  }
+  RunParams run;
+  memset(&run, 0, sizeof(run));
+  run.nprob = 1;
+  run.group = kDefaultGroup;
+  run.k[0] = k;
+  run.nJ[0] = (int)ceil_div(k, BN);
+  run.item_begin[0] = 0;
+  run.total = run.item_begin[1] = items_of(ms, k);
+  return launch(ms, ms->d_desc, run, flags, st);
+}
+
+int mixed_split_terms(const MixedState* ms) { return ms->S; }
+bool mixed_is_bf16(const MixedState* ms) { return ms->bf16; }
+int64_t mixed_n(const MixedState* ms) { return ms->n; }
+
+gls_status_t mixed_batch_create(MixedState* const* states, const double* const* Pbr,
+                                const double* const* Glin, const int64_t* ldp, int count,
+                                MixedBatch** out) {
+  *out = nullptr;
+  if (count < 1 || count > kMaxBatch) {
+    g_err = "batch size must be in [1, " + std::to_string(kMaxBatch) + "]";
+    return GLS_ERR_INVALID_ARG;
+  }
+  for (int i = 1; i < count; ++i)
+    if (states[i]->S != states[0]->S || states[i]->bf16 != states[0]->bf16) {
+      g_err = "all plans of a batch need the same mixed precision and split_terms";
+      return GLS_ERR_INVALID_ARG;
+    }
+  MixedBatch* b = new MixedBatch();
+  b->order.resize(count);
+  for (int i = 0; i < count; ++i) b->order[i] = i;
+  std::stable_sort(b->order.begin(), b->order.end(),
+                   [&](int a, int c) { return states[a]->n > states[c]->n; });
+  std::vector<ProblemDesc> h(count);
+  for (int i = 0; i < count; ++i) {
+    const int o = b->order[i];
+    b->states.push_back(states[o]);
+    h[i] = states[o]->desc;
+    h[i].Pbr = const_cast<double*>(Pbr[o]);
+    h[i].Glin = const_cast<double*>(Glin[o]);
+    h[i].ldp = ldp[o];
+  }
+  if (cudaMalloc(&b->d_desc, sizeof(ProblemDesc) * count) != cudaSuccess ||
+      cudaMemcpy(b->d_desc, h.data(), sizeof(ProblemDesc) * count, cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(b->d_desc);
+    delete b;
+    g_err = "batch descriptor allocation failed";
+    return GLS_ERR_OOM;
+  }
+  *out = b;
+  return GLS_OK;
+}
+
+void mixed_batch_free(MixedBatch* b) {
+  if (!b) return;
+  cudaFree(b->d_desc);
+  delete b;
+}
+
+cudaError_t mixed_batch_run(MixedBatch* b, const int64_t* k, int group, int* flags,
+                            cudaStream_t st) {
+  RunParams run;
+  memset(&run, 0, sizeof(run));
+  const int count = (int)b->states.size();
+  run.nprob = count;
+  run.group = group > 0 ? group : kDefaultGroup;
+  int total = 0;
+  for (int i = 0; i < count; ++i) {
+    const int o = b->order[i];
+    run.k[i] = k[o];
+    run.nJ[i] = (int)ceil_div(k[o], BN);
+    run.item_begin[i] = total;
+    total += k[o] > 0 ? items_of(b->states[i], k[o]) : 0;
+  }
+  run.item_begin[count] = total;
+  run.total = total;
+  if (total == 0) return cudaSuccess;
+  return launch(b->states[0], b->d_desc, run, flags, st);
 }
 
 }  // namespace gls

@@ -101,6 +101,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.gls_last_error.restype = ctypes.c_char_p
     lib.gls_version.argtypes = []
     lib.gls_version.restype = i32
+    lib.gls_batch_create.argtypes = [P(vp), i32, P(vp)]
+    lib.gls_batch_create.restype = i32
+    lib.gls_batch_solve.argtypes = [vp, P(vp), P(i64), P(i64), P(vp), P(i64), P(vp), i32]
+    lib.gls_batch_solve.restype = i32
+    lib.gls_batch_destroy.argtypes = [vp]
+    lib.gls_batch_destroy.restype = i32
     lib.gls_plan_set_timing.argtypes = [vp, i32]
     lib.gls_plan_set_timing.restype = i32
     lib.gls_plan_stats.argtypes = [vp, P(Stats)]
@@ -250,6 +256,58 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None):
             load().gls_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several factored mixed-precision plans solved by one persistent launch
+    (gls_batch_create / gls_batch_solve).  Device buffers only."""
+
+    def __init__(self, plans):
+        lib = load()
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(lib.gls_batch_create(arr, len(self.plans), ctypes.byref(h)), "gls_batch_create")
+        self._h = h
+
+    def solve(self, XRs, Bs, statuses=None, ks=None, group=0):
+        """XRs[i]: n_i x k_i int8 column-major device tensors (e.g. X.t() of a
+        (k_i, n_i) tensor); Bs[i]: p_i x k_i float64 column-major device tensors."""
+        lib = load()
+        n = len(self.plans)
+        xs, lx, bs, lb = [], [], [], []
+        for pl, X, B in zip(self.plans, XRs, Bs):
+            px, ldx = _colmajor(X, pl.n, 1, "XR")
+            pb, ldb = _colmajor(B, pl.p, 8, "B")
+            xs.append(px.value or 0)
+            lx.append(ldx)
+            bs.append(pb.value or 0)
+            lb.append(ldb)
+        if ks is None:
+            ks = [X.shape[1] for X in XRs]
+        VP, I64 = ctypes.c_void_p * n, ctypes.c_int64 * n
+        st = None
+        if statuses is not None:
+            st = VP(*[(_ptr(s).value if s is not None else None) for s in statuses])
+        _check(lib.gls_batch_solve(self._h, VP(*xs), I64(*lx), I64(*[int(k) for k in ks]),
+                                   VP(*bs), I64(*lb), st, int(group)), "gls_batch_solve")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gls_batch_destroy(self._h)
             self._h = None
 
     def __enter__(self):
