@@ -48,6 +48,24 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "n10000_p20_m1000000_bf16"
 
+# Batched uneven scans: each scan its own kinship, h ~ U(0.1, 0.9); one persistent
+# launch per round serves one block of every scan.
+BATCH_WORKLOADS = {
+    "batch48_uneven_bf16": dict(scans=48, n=(500, 8000), p=(2, 20), m=(10_000, 500_000),
+                                h=(0.1, 0.9), precision="bf16", block=65536, seed_offset=3),
+    "batch48_uneven_fp16": dict(scans=48, n=(500, 8000), p=(2, 20), m=(10_000, 500_000),
+                                h=(0.1, 0.9), precision="fp16", block=65536, seed_offset=3),
+    # The FP64 path needs about 4 minutes per step at full m (2.8e14 FP64 flops),
+    # so the FP64 comparison runs every scan's first m/32 SNPs, beside the mixed
+    # path on the same reduced scans.
+    "batch48_uneven_m32_fp64": dict(scans=48, n=(500, 8000), p=(2, 20), m=(10_000, 500_000),
+                                    h=(0.1, 0.9), precision="fp64", block=16384, seed_offset=3,
+                                    m_div=32),
+    "batch48_uneven_m32_bf16": dict(scans=48, n=(500, 8000), p=(2, 20), m=(10_000, 500_000),
+                                    h=(0.1, 0.9), precision="bf16", block=65536, seed_offset=3,
+                                    m_div=32),
+}
+
 
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -332,6 +350,211 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def batch_specs(bw):
+    """Seeded (n, p, m, h, seed) per scan."""
+    import numpy as np
+    from paper_1210_7325_gb300 import synth
+    g = synth.rng(synth.BASE_SEED + bw["seed_offset"], 99)
+    out = []
+    for i in range(bw["scans"]):
+        n = int(g.integers(bw["n"][0], bw["n"][1] + 1))
+        p = int(g.integers(bw["p"][0], bw["p"][1] + 1))
+        m = int(g.integers(bw["m"][0], bw["m"][1] + 1))
+        h = float(g.uniform(*bw["h"]))
+        m = max(1, m // bw.get("m_div", 1))
+        out.append((n, p, m, h, synth.BASE_SEED + bw["seed_offset"] * 1000 + i))
+    return out
+
+
+def run_batch_workload(args, bw, torch):
+    """Config: 48 uneven scans.  One step = every scan's gls_factor (concurrent
+    streams) + rounds until every scan is solved.  A mixed-precision round is ONE
+    batched persistent launch over the next block of every scan; an FP64 round
+    launches every scan's block on its own plan stream (they overlap)."""
+    import concurrent.futures as cf
+    import numpy as np
+    from paper_1210_7325_gb300 import autotune, gls, synth
+    specs = batch_specs(bw)
+    plans, inputs, outs, blocks = [], [], [], []
+    fp64 = bw["precision"] == "fp64"
+    for (n, p, m, h, seed) in specs:
+        Md = synth.kinship_M_torch(n, h, seed, device="cuda").t()
+        XL = synth.covariates(n, p, seed)
+        y = synth.phenotype(n, seed)
+        XR = synth.genotypes_torch(n, m, seed, device="cuda")
+        XLd = torch.from_numpy(np.ascontiguousarray(XL.T)).cuda().t()
+        yd = torch.from_numpy(y).cuda()
+        kb = autotune.choose_block(m, bw["block"])
+        plans.append(gls.Plan(n, p, kb, precision=bw["precision"]))
+        inputs.append((Md, XLd, yd, XR))
+        outs.append((torch.empty((m, p), dtype=torch.float64, device="cuda"),
+                     torch.empty(m, dtype=torch.int32, device="cuda")))
+        blocks.append(kb)
+    rounds = max(-(-m // kb) for (_, _, m, _, _), kb in zip(specs, blocks))
+    pool = cf.ThreadPoolExecutor(max_workers=8)
+
+    def factor_all():
+        list(pool.map(lambda i: plans[i].factor(*inputs[i][:3]), range(len(plans))))
+
+    def round_args(r):
+        XRs, Bs, sts, ks = [], [], [], []
+        for i, (n, p, m, h, seed) in enumerate(specs):
+            s0 = min(r * blocks[i], m)
+            k = min(blocks[i], m - s0)
+            XRs.append(inputs[i][3][s0:s0 + k].t())
+            Bs.append(outs[i][0][s0:s0 + k].t())
+            sts.append(outs[i][1][s0:s0 + k])
+            ks.append(k)
+        return XRs, Bs, sts, ks
+
+    factor_all()
+    if fp64:
+        batch, group, tune_times = None, None, None
+    else:
+        batch = gls.Batch(plans)
+        group, tune_times = autotune.tune_group(batch, *round_args(0))
+    rargs = [round_args(r) for r in range(rounds)]
+
+    def step():
+        factor_all()
+        for r in range(rounds):
+            if fp64:
+                XRs, Bs, sts, ks = rargs[r]
+                for i, pl in enumerate(plans):
+                    if ks[i] > 0:
+                        pl.solve_block(XRs[i], Bs[i], sts[i], k=ks[i])
+            else:
+                batch.solve(*rargs[r], group=group)
+        for pl in plans:
+            pl.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # timing of phases: on plan 0 for the batch (it carries every batched
+    # launch); on every plan for FP64 (each runs on its own stream)
+    for i, pl in enumerate(plans):
+        pl.set_timing(fp64 or i == 0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    sts = [pl.stats() for pl in plans]
+    st0 = {key: (sum(s[key] for s in sts) if fp64 else sts[0][key]) for key in sts[0]}
+    total_m = sum(sp[2] for sp in specs)
+    unit_flops = 1 if fp64 else 3
+    tensor_flops = sum(unit_flops * n * n * m for (n, p, m, h, seed) in specs) * args.steps
+    bad = sum(int((o[1] != 0).sum().item()) for o in outs)
+    peaks, peak_src = load_peaks()
+    trsm_s = st0["trsm_ms"] / 1e3
+    achieved = tensor_flops / trsm_s / 1e12 if trsm_s > 0 else None
+    if fp64:
+        fpk = fp64_dgemm_tflops(torch)
+        roof = {"bound": "fp64", "achieved": achieved, "peak": fpk, "unit": "TFLOP/s",
+                "frac": achieved / fpk if achieved else None, "traffic": None,
+                "peak_source": "measured torch.matmul float64 8192^3 in this run",
+                "per_unit": "n^2 FP64 flops per SNP; achieved uses the summed kernel time of "
+                            "the 48 streams, so overlap makes it a lower bound"}
+    else:
+        roof = {"bound": "tensor", "achieved": achieved,
+                "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                "frac": achieved / peaks["bf16_tflops_sustained"] if achieved else None,
+                "traffic": None, "peak_source": f"{peak_src} bf16_tflops_sustained",
+                "per_unit": "3 slices x n^2 tensor flops per SNP"}
+    line = {
+        "metric": METRIC, "value": total_m * args.steps / t, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16": "bf16", "fp16": "f16", "fp64": "f64"}[bw["precision"]],
+        "data": "synthetic (48 seeded scans, own kinship each)",
+        "config": {"workload": args.workload, "scans": bw["scans"], "total_snps": total_m,
+                   "n_range": bw["n"], "p_range": bw["p"], "m_range": bw["m"],
+                   "m_divisor": bw.get("m_div", 1),
+                   "rounds": rounds, "group_autotuned": group,
+                   "group_trials_s": tune_times, "parallelism": "replicas1"},
+        "gpu_launches": None,
+        "phase_ms_per_step": {"solve_kernels": st0["trsm_ms"] / args.steps,
+                              "convert": st0["convert_ms"] / args.steps,
+                              "solve_pxp": st0["solve_ms"] / args.steps},
+        "roofline": roof,
+        "check": {"bad_status": bad},
+    }
+    line["gpu_launches"] = int(sum(s["launches"] for s in sts))
+    if batch is not None:
+        batch.close()
+    for pl in plans:
+        pl.close()
+    return line
+
+
+SERVE_WORKLOADS = {
+    "serve2000_bf16": dict(requests=2000, rate=20.0, n=(1000, 10000), p=(2, 12),
+                           m=(10_000, 200_000), reuse=0.3, precision="bf16", block=32768,
+                           seed_offset=4, budget=200e9, time_cap=420.0),
+    "serve2000_fp64": dict(requests=2000, rate=20.0, n=(1000, 10000), p=(2, 12),
+                           m=(10_000, 200_000), reuse=0.3, precision="fp64", block=32768,
+                           seed_offset=4, budget=200e9, time_cap=120.0),
+}
+
+
+def serve_inputs_factory(seed_base):
+    import numpy as np
+    from paper_1210_7325_gb300 import serve, synth
+
+    def make_inputs(req, torch, reuse):
+        seed = seed_base + req.mkey
+        M = XL = None
+        if not reuse:
+            M = synth.kinship_M_torch(req.n, req.h, seed, device="cuda").t()
+            XL = torch.from_numpy(np.ascontiguousarray(synth.covariates(req.n, req.p, seed).T))
+            XL = XL.cuda().t()
+        y = torch.from_numpy(synth.phenotype(req.n, req.y_seed)).cuda()
+        XR = synth.genotypes_torch(req.n, req.m, seed, device="cuda")
+        return serve.Inputs(M, XL, XR, y)
+    return make_inputs
+
+
+def run_serve_workload(args, sw, torch):
+    """Config: Poisson stream of scan requests served with continuous batching."""
+    from paper_1210_7325_gb300 import serve, synth
+    seed = synth.BASE_SEED + sw["seed_offset"]
+    count = args.requests or sw["requests"]
+    reqs = serve.poisson_requests(count, sw["rate"], seed, sw["n"], sw["p"], sw["m"],
+                                  sw["reuse"])
+    make = serve_inputs_factory(seed * 10)
+    # warm-up: load kernels and encode maps on a few small requests (not timed)
+    warm = serve.poisson_requests(4, 100.0, seed + 1, (1000, 1200), (2, 4), (2000, 4000), 0.0)
+    srv = serve.Server(make, sw["precision"], sw["budget"], sw["block"])
+    srv.run(warm)
+    srv.close()
+    srv = serve.Server(make, sw["precision"], sw["budget"], sw["block"])
+    cap = args.time_cap if args.time_cap else sw["time_cap"]
+    t0 = time.perf_counter()
+    results = srv.run(reqs, time_cap=cap)
+    wall = time.perf_counter() - t0
+    summ = serve.latency_summary(results)
+    depth = [d[1] for d in srv.queue_depth]
+    srv.close()
+    line = {
+        "metric": METRIC, "value": summ.get("solves_per_s", 0.0), "unit": UNIT, "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": wall * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16": "bf16", "fp16": "f16", "fp64": "f64"}[sw["precision"]],
+        "data": "synthetic Poisson request stream (seeded)",
+        "config": {"workload": args.workload, "requests": count, "rate_per_s": sw["rate"],
+                   "n_range": sw["n"], "p_range": sw["p"], "m_range": sw["m"],
+                   "reuse_fraction": sw["reuse"], "hbm_budget_bytes": sw["budget"],
+                   "block_snps": sw["block"], "time_cap_s": cap, "parallelism": "replicas1"},
+        "latency": {k: v for k, v in summ.items() if k.endswith("_s")},
+        "completed": summ.get("completed", 0), "reused_factors": summ.get("reused", 0),
+        "queue_depth_max": max(depth) if depth else 0,
+        "queue_depth_last": depth[-1] if depth else 0,
+        "wall_s": wall,
+    }
+    return line
+
+
 def config_for(wl, args):
     return {"workload": args.workload, "n": wl["n"], "p": wl["p"], "m": wl["m"], "h": wl["h"],
             "precision": wl["precision"], "block_snps": wl["block"],
@@ -346,13 +569,31 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload",
+                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(SERVE_WORKLOADS),
+                    default=DEFAULT_WORKLOAD)
+    ap.add_argument("--requests", type=int, default=0, help="serving: number of requests")
+    ap.add_argument("--time-cap", type=float, default=0.0, help="serving: wall-time cap (s)")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--cpu-snps", type=int, default=2048)
     ap.add_argument("--ref-snps", type=int, default=1024)
     args = ap.parse_args()
+    if args.workload in SERVE_WORKLOADS:
+        import torch
+        from paper_1210_7325_gb300 import build as gbuild
+        gbuild.build()
+        print(json.dumps(run_serve_workload(args, SERVE_WORKLOADS[args.workload], torch)),
+              flush=True)
+        return
+    if args.workload in BATCH_WORKLOADS:
+        import torch
+        from paper_1210_7325_gb300 import build as gbuild
+        gbuild.build()
+        print(json.dumps(run_batch_workload(args, BATCH_WORKLOADS[args.workload], torch)),
+              flush=True)
+        return
     wl = WORKLOADS[args.workload]
     args.warmup = max(args.warmup, 3) if args.impl == "gb300" else args.warmup
 

@@ -1,0 +1,103 @@
+"""Autotuner for the batched mixed-precision solve.
+
+The tunable knobs do not change results (each work item's arithmetic is the
+same whichever CTA runs it), only speed:
+  * group  -- row blocks per L2 rasterization group of a launch;
+  * block  -- SNPs per plan per launch (bounded by max_block_snps).
+``tune_group`` times each candidate group on the caller's real launch with CUDA
+events on the launching stream and keeps the fastest; results are cached in a
+small JSON file keyed by device name and a signature of the batch, so later
+runs with the same shapes skip the trials.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+DEFAULT_GROUPS = (2, 4, 8, 16)
+_lock = threading.Lock()
+
+
+def cache_path() -> str:
+    base = os.environ.get("GLS_GB300_CACHE") or os.path.join(
+        os.path.expanduser("~"), ".cache", "gls_gb300")
+    return os.path.join(base, "autotune.json")
+
+
+def _load() -> dict:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(d: dict) -> None:
+    path = cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(d, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass  # a read-only home only loses the cache
+
+
+def signature(plans, ks) -> str:
+    """Shapes that determine the launch: (n, p, k) per plan, sorted, and precision."""
+    shapes = sorted((p.n, p.p, int(k)) for p, k in zip(plans, ks))
+    prec = plans[0].precision if plans else "?"
+    return f"{prec}:" + ";".join(f"{n}x{p}x{k}" for n, p, k in shapes)
+
+
+def device_name() -> str:
+    try:
+        import torch
+        return torch.cuda.get_device_name(0)
+    except Exception:
+        return "unknown"
+
+
+def tune_group(batch, XRs, Bs, statuses=None, ks=None, candidates=DEFAULT_GROUPS, reps: int = 2,
+               use_cache: bool = True) -> tuple[int, dict]:
+    """Returns (best group, {group: seconds}) for this batch launch."""
+    import torch
+    if ks is None:
+        ks = [X.shape[1] for X in XRs]
+    key = device_name() + "|" + signature(batch.plans, ks)
+    if use_cache:
+        with _lock:
+            hit = _load().get(key)
+        if hit:
+            return int(hit["group"]), {int(g): t for g, t in hit["times"].items()}
+    stream = torch.cuda.ExternalStream(batch.plans[0].stream)
+    times = {}
+    for g in candidates:
+        batch.solve(XRs, Bs, statuses, ks, group=g)  # warm-up (also validates)
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            batch.solve(XRs, Bs, statuses, ks, group=g)
+            e1.record(stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        times[int(g)] = best
+    group = min(times, key=times.get)
+    if use_cache:
+        with _lock:
+            d = _load()
+            d[key] = {"group": group, "times": {str(g): t for g, t in times.items()}}
+            _store(d)
+    return group, times
+
+
+def choose_block(m: int, kmax: int, rounds_hint: int = 0) -> int:
+    """SNPs per launch for a scan of m SNPs: the largest block up to kmax that
+    splits m into equal rounds (fewer ragged tails across the batch)."""
+    if m <= kmax:
+        return max(m, 1)
+    rounds = max(rounds_hint, -(-m // kmax))
+    return -(-m // rounds)

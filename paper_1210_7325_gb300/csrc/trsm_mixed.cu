@@ -663,19 +663,20 @@ __global__ void __launch_bounds__(256) split_w_kernel(const double* __restrict__
   }
 }
 
+// Looked up once; the initialisation of a function-local static is
+// thread-safe, so plans created on several host threads share it.
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() {
     cudaDriverEntryPointQueryResult q;
     void* ptr = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
                                          &q) != cudaSuccess ||
         q != cudaDriverEntryPointSuccess) {
       cudaGetLastError();
-      return nullptr;
+      return static_cast<PFN_cuTensorMapEncodeTiled_v12000>(nullptr);
     }
-    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-  }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }();
   return fn;
 }
 

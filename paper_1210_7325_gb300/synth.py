@@ -38,18 +38,19 @@ def kinship_markers(n: int, seed: int, n_markers: int = 5000) -> np.ndarray:
     if n < 2:
         raise ValueError("a marker column needs n >= 2 individuals to have variance")
     g = rng(seed, _STREAM_KINSHIP)
-    G = np.empty((n, n_markers), dtype=np.float64)
     f = g.uniform(0.05, 0.5, size=n_markers)
-    for j in range(n_markers):
-        for _ in range(10000):
-            col = g.binomial(2, f[j], size=n).astype(np.float64)
-            sd = col.std()
-            if sd > 0.0:
-                break
-            f[j] = g.uniform(0.05, 0.5)
-        else:
-            raise RuntimeError("could not draw a polymorphic marker column")
-        G[:, j] = (col - col.mean()) / sd
+    G = g.binomial(2, f[None, :], size=(n, n_markers)).astype(np.float64)
+    for _ in range(10000):
+        sd = G.std(axis=0)
+        bad = np.flatnonzero(sd == 0.0)
+        if bad.size == 0:
+            break
+        fb = g.uniform(0.05, 0.5, size=bad.size)
+        G[:, bad] = g.binomial(2, fb[None, :], size=(n, bad.size))
+    else:
+        raise RuntimeError("could not draw polymorphic marker columns")
+    G -= G.mean(axis=0)
+    G /= G.std(axis=0)
     return G
 
 
@@ -73,6 +74,48 @@ def kinship_M(n: int, h: float, seed: int, n_markers: int = 5000, device: str = 
     M = h * Phi
     M[np.diag_indices(n)] += (1.0 - h)
     return np.ascontiguousarray(M)
+
+
+def kinship_M_torch(n: int, h: float, seed: int, n_markers: int = 5000, device="cuda"):
+    """The kinship recipe above drawn with torch on ``device`` and multiplied in
+    FP32 (fast enough to generate one M per request at serving rates).  The
+    marker draws use torch's generator, so the matrix differs from
+    ``kinship_M`` for the same seed.  Returns an (n, n) float64 tensor
+    (symmetric, so row- and column-major storage coincide)."""
+    import torch
+    dev = torch.device(device)
+    if n < 2:  # one sample: Phi = [1]
+        return torch.ones((n, n), dtype=torch.float64, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed) * 1000003 + _STREAM_KINSHIP)
+    f = torch.rand(n_markers, generator=gen, device=dev) * 0.45 + 0.05
+
+    def draw(fcols):
+        a = torch.rand((n, fcols.numel()), generator=gen, device=dev) < fcols
+        b = torch.rand((n, fcols.numel()), generator=gen, device=dev) < fcols
+        return a.float() + b.float()
+
+    G = draw(f)
+    for _ in range(10000):
+        bad = torch.nonzero(G.std(dim=0, unbiased=False) == 0).flatten()
+        if bad.numel() == 0:
+            break
+        fb = torch.rand(bad.numel(), generator=gen, device=dev) * 0.45 + 0.05
+        G[:, bad] = draw(fb)
+    G = (G - G.mean(dim=0)) / G.std(dim=0, unbiased=False)
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        K = (G @ G.T) / n_markers
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    d = torch.sqrt(torch.diagonal(K))
+    Phi = (K / d[:, None] / d[None, :]).double()
+    Phi = 0.5 * (Phi + Phi.T)
+    Phi.fill_diagonal_(1.0)
+    M = h * Phi
+    M.diagonal().add_(1.0 - h)
+    return M
 
 
 def covariates(n: int, p: int, seed: int) -> np.ndarray:
@@ -108,6 +151,8 @@ def genotypes_torch(n: int, m: int, seed: int, device="cpu", chunk: int = 8192, 
     Binomial(2, f) is drawn as the sum of two Bernoulli(f) draws."""
     import torch
     dev = torch.device(device)
+    if n < 2:  # one sample: Phi = [1]
+        return torch.ones((n, n), dtype=torch.float64, device=dev)
     gen = torch.Generator(device=dev)
     gen.manual_seed(int(seed) * 1000003 + _STREAM_GENOTYPES)
     if out is None:

@@ -1,0 +1,146 @@
+"""Host logic of the serving loop (admission by memory budget, LRU eviction of
+idle factors, reuse of a resident factor for a new phenotype, continuous
+batching), run on the CPU against a fake of the GLS binding that records
+every call.  The GPU behaviour is covered by tests/test_gpu_serve.py."""
+import threading
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1210_7325_gb300 import serve
+
+
+class FakeGls:
+    def __init__(self):
+        self.lock = threading.Lock()
+        self.factors = []      # (plan id, with_M)
+        self.batches = []      # number of plans per batched launch
+        self.closed_use = 0
+
+    def footprint_bytes(self, n, p, block, precision):
+        return 8 * n * n + 1000
+
+    def make(self):
+        fake = self
+
+        class Plan:
+            ids = iter(range(10**6))
+
+            def __init__(self, n, p, block, precision="fp64"):
+                self.n, self.p, self.block, self.precision = n, p, block, precision
+                self.id = next(Plan.ids)
+                self.closed = False
+                self.yv = None
+
+            def factor(self, M, XL, y):
+                time.sleep(0.002)
+                with fake.lock:
+                    if self.closed:
+                        fake.closed_use += 1
+                        raise RuntimeError("factor on a closed plan")
+                    fake.factors.append((self.id, M is not None))
+                self.yv = float(y.sum())
+
+            def _fill(self, XR, B, st):
+                # b_i := (sum of the SNP column + y sum) in every row: a function of
+                # the request's own data only
+                v = XR.t().double().sum(dim=1) + self.yv
+                B.t()[:] = v[:, None]
+                st[:] = 0
+
+            def solve_block(self, XR, B, st, k=None):
+                if self.closed:
+                    fake.closed_use += 1
+                self._fill(XR, B, st)
+
+            def synchronize(self):
+                pass
+
+            def close(self):
+                self.closed = True
+
+        class Batch:
+            def __init__(self, plans):
+                self.plans = plans
+
+            def solve(self, XRs, Bs, sts, ks, group=0):
+                fake.batches.append(len(self.plans))
+                for pl, X, B, s in zip(self.plans, XRs, Bs, sts):
+                    if pl.closed:
+                        fake.closed_use += 1
+                    pl._fill(X, B, s)
+
+            def close(self):
+                pass
+
+        self.Plan, self.Batch = Plan, Batch
+        return self
+
+
+def make_inputs(req, torch_mod, reuse):
+    g = torch.Generator().manual_seed(req.mkey)
+    XR = torch.randint(0, 3, (req.m, req.n), generator=g, dtype=torch.int8)
+    y = torch.full((req.n,), float(req.y_seed % 97), dtype=torch.float64)
+    M = None if reuse else torch.eye(req.n, dtype=torch.float64)
+    XL = None if reuse else torch.ones((req.n, max(req.p - 1, 0)), dtype=torch.float64)
+    return serve.Inputs(M, XL, XR, y)
+
+
+def expected(req):
+    g = torch.Generator().manual_seed(req.mkey)
+    XR = torch.randint(0, 3, (req.m, req.n), generator=g, dtype=torch.int8)
+    return XR.double().sum(dim=1) + float(req.y_seed % 97) * req.n
+
+
+@pytest.fixture
+def fake(monkeypatch):
+    f = FakeGls().make()
+    monkeypatch.setattr(serve, "gls", f)
+    return f
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp64"])
+@pytest.mark.parametrize("budget", [1e9, 2.2e6])
+def test_every_request_served_once_within_budget(fake, prec, budget):
+    reqs = serve.poisson_requests(40, 400.0, 5, (100, 300), (2, 5), (50, 700), 0.4)
+    srv = serve.Server(make_inputs, prec, hbm_budget=budget, block=128, device="cpu")
+    res = srv.run(reqs, time_cap=60.0, keep_outputs=True)
+    srv.close()
+    assert not srv.rejected
+    assert sorted(res) == [r.rid for r in reqs]
+    assert srv.peak_used <= budget
+    assert fake.closed_use == 0
+    for r in reqs:
+        B = res[r.rid]["B"]
+        assert torch.equal(B[:, 0], expected(r)), r.rid
+        assert torch.equal(B[:, -1], expected(r))
+    # each resident factor serves a new phenotype with M = None
+    reused = sum(1 for r in reqs if r.reuse)
+    with_m = sum(1 for _, m in fake.factors if m)
+    assert with_m + sum(1 for _, m in fake.factors if not m) == len(reqs)
+    if budget >= 1e9:
+        assert with_m == len(reqs) - reused       # nothing evicted
+    else:
+        assert with_m > len(reqs) - reused        # evictions forced re-factoring
+    if prec != "fp64":
+        assert max(fake.batches) > 1               # requests shared launches
+
+
+def test_request_larger_than_budget_is_rejected(fake):
+    reqs = [serve.Request(0, 0.0, 2000, 3, 100, 0, 1), serve.Request(1, 0.0, 100, 3, 100, 1, 2)]
+    srv = serve.Server(make_inputs, "bf16", hbm_budget=1e6, block=128, device="cpu")
+    res = srv.run(reqs, time_cap=30.0)
+    srv.close()
+    assert [rid for rid, _ in srv.rejected] == [0]
+    assert list(res) == [1]
+
+
+def test_latency_summary():
+    res = {i: dict(latency=float(i), done=float(i) + 1, arrival=0.0, m=10, reuse=i % 2 == 0)
+           for i in range(1, 101)}
+    s = serve.latency_summary(res)
+    assert s["completed"] == 100 and s["reused"] == 50
+    assert s["p50_s"] == pytest.approx(50.5) and s["p99_s"] == pytest.approx(99.01)
+    assert s["solves_per_s"] == pytest.approx(1000 / 101)
