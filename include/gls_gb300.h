@@ -65,6 +65,13 @@ typedef enum {
  * (hi/lo terms, no per-row fixed-point hi part).  FP32 accumulation of the hi
  * products is then inexact; kept to measure what the fixed-point hi part buys. */
 #define GLS_FLAG_NAIVE_SPLIT 1u
+/* Mixed paths factor M (Cholesky, L^{-1}, whitening) with binary64 products
+ * evaluated exactly on the tensor cores (integer slices, see gls_factor); this
+ * flag selects the plain binary64 CUDA-core kernels instead. */
+#define GLS_FLAG_FACTOR_NATIVE 2u
+/* FP64 path: factor M with the tensor-core binary64 products instead of the
+ * default plain binary64 CUDA-core kernels. */
+#define GLS_FLAG_FACTOR_TENSOR 4u
 
 /* Plan description.  Zero-initialise and fill the fields that matter. */
 typedef struct {
@@ -91,6 +98,11 @@ gls_status_t gls_plan_create(const gls_plan_desc_t* desc, gls_plan_t* out);
  * Setup phase of Alg. 5 (lines 1, 2, 4, 5, 6):
  *   L L^T = M (potrf); X~_L = L^{-1} X_L; y~ = L^{-1} y;
  *   S_TL = X~_L^T X~_L; b_T = X~_L^T y~ (Fig. 1), all in binary64.
+ * Two implementations give binary64 results: plain FP64 kernels, and (default
+ * for the mixed paths, see GLS_FLAG_FACTOR_*) a recursive Cholesky with
+ * inverse whose dense products are split into exact 8-bit integer slices and
+ * summed exactly on the tensor cores, rounded once to binary64; only its
+ * 64 x 64 diagonal blocks use FP64 arithmetic.
  * M   n x n (ldm >= n), only the lower triangle is read.  M == NULL keeps the
  *     factor of the previous call (a new phenotype for the same M).
  * XL  n x (p-1) (ldxl >= n); NULL when p == 1.  With M == NULL, XL == NULL
@@ -231,6 +243,15 @@ gls_status_t gls_solve_block_fp64_static(int64_t n, int32_t p, const double* Zin
                                          const double* zT, const int8_t* XR, int64_t ldxr,
                                          int64_t k, double* B, int64_t ldb,
                                          int32_t* snp_status, void* stream);
+
+/*
+ * Copies the factor of the last successful gls_factor: L (n x n lower
+ * triangular, zeros above the diagonal, ldl >= n) and Zinv = L^{-1} (same
+ * shape, ldz >= n).  Either pointer may be NULL; host or device memory.
+ * Synchronous.  Errors: STATE (no factor yet), INVALID_ARG, CUDA.
+ */
+gls_status_t gls_plan_get_factor(gls_plan_t plan, double* L, int64_t ldl, double* Zinv,
+                                 int64_t ldz);
 
 /* Library version as major*10000 + minor*100 + patch. */
 int32_t gls_version(void);

@@ -18,6 +18,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "factor_tc.cuh"
 
 namespace gls {
 namespace {
@@ -378,6 +379,12 @@ cudaError_t potrf_trtri_fp64(double* A, double* Z, int64_t ld, int64_t npad, int
                                                                         flags);
   }
   return cudaGetLastError();
+}
+
+void launch_potrf_diag64(double* A, double* Z, int64_t ld, int64_t k0, int* flags,
+                         cudaStream_t st) {
+  if (set_attrs() != cudaSuccess) return;
+  potrf_diag_kernel<<<1, 256, kTileSmem, st>>>(A, Z, ld, k0, flags);
 }
 
 void launch_whiten(const double* Z, int64_t ldz, int64_t n, int64_t npad, const double* rhs,

@@ -23,8 +23,11 @@ const char* mixed_last_error();
 // tensor-core slices and keeps its FP64 diagonal blocks (only when new_factor),
 // then forms W = Z^T [X~_L | y~] = M^{-1} [X_L | y] in binary64 and splits W^T
 // into the extra row block of the A operand.
+// With w_ready, W has already been written to mixed_w_buffer(ms) by the caller.
 gls_status_t mixed_prepare(MixedState* ms, const double* Z, int64_t ldz, const double* Wt,
-                           int64_t ldw, bool new_factor, cudaStream_t st);
+                           int64_t ldw, bool new_factor, bool w_ready, cudaStream_t st);
+// Device buffer (npad x p, column-major) holding W = M^{-1} [X_L | y].
+double* mixed_w_buffer(MixedState* ms);
 
 // One block, step 1: int8 genotypes -> the 16-bit operand layout read by TMA.
 cudaError_t mixed_convert(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,

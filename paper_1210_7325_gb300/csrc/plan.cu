@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "factor_tc.cuh"
 #include "gls_gb300.h"
 #include "mixed.cuh"
 
@@ -95,6 +96,8 @@ struct gls_plan {
   double* h_b[2]{};
   int32_t* h_s[2]{};
   gls::MixedState* mixed = nullptr;
+  bool tc = false;          // factor on the tensor cores (exact slices)
+  gls::TcFactor* tcf = nullptr;
   // device-time accounting (gls_plan_set_timing / gls_plan_stats)
   struct Slot {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
@@ -155,6 +158,11 @@ size_t partial_doubles(int precision, int64_t npad, int p, int64_t kmax) {
   return (size_t)(npad / 128 + p) * kmax;
 }
 
+bool uses_tc_factor(const gls_plan_desc_t& d) {
+  if (d.precision == GLS_PREC_FP64) return (d.flags & GLS_FLAG_FACTOR_TENSOR) != 0;
+  return (d.flags & GLS_FLAG_FACTOR_NATIVE) == 0;
+}
+
 size_t footprint(const gls_plan_desc_t& d, int64_t* npad_out = nullptr) {
   const int64_t npad = gls::round_up(d.n, 128);
   if (npad_out) *npad_out = npad;
@@ -169,6 +177,7 @@ size_t footprint(const gls_plan_desc_t& d, int64_t* npad_out = nullptr) {
   bytes += 2 * (size_t)kmax * (p * sizeof(double) + sizeof(int32_t));
   bytes += partial_doubles(d.precision, npad, p, kmax) * sizeof(double);  // Gram partials
   if (d.precision != GLS_PREC_FP64) bytes += gls::mixed_footprint(d.n, npad, p, kmax, d.split_terms);
+  if (uses_tc_factor(d)) bytes += gls::tc_factor_bytes(npad);
   return bytes;
 }
 
@@ -198,8 +207,13 @@ gls_status_t validate_desc(const gls_plan_desc_t* d) {
     set_error("split_terms must be 0, 2 or 3");
     return GLS_ERR_INVALID_ARG;
   }
-  if ((d->flags & ~GLS_FLAG_NAIVE_SPLIT) != 0) {
+  const uint32_t known = GLS_FLAG_NAIVE_SPLIT | GLS_FLAG_FACTOR_NATIVE | GLS_FLAG_FACTOR_TENSOR;
+  if ((d->flags & ~known) != 0) {
     set_error("unknown flag bits 0x%x", d->flags);
+    return GLS_ERR_INVALID_ARG;
+  }
+  if ((d->flags & GLS_FLAG_FACTOR_NATIVE) && (d->flags & GLS_FLAG_FACTOR_TENSOR)) {
+    set_error("GLS_FLAG_FACTOR_NATIVE and GLS_FLAG_FACTOR_TENSOR exclude each other");
     return GLS_ERR_INVALID_ARG;
   }
   for (int i = 0; i < 7; ++i)
@@ -216,6 +230,7 @@ void free_plan(gls_plan* pl) {
   if (pl->h2d) cudaStreamSynchronize(pl->h2d);
   if (pl->d2h) cudaStreamSynchronize(pl->d2h);
   if (pl->mixed) gls::mixed_free(pl->mixed);
+  if (pl->tcf) gls::tc_factor_free(pl->tcf);
   cudaFree(pl->A);
   cudaFree(pl->Z);
   cudaFree(pl->Wrhs);
@@ -454,6 +469,13 @@ gls_status_t gls_plan_create(const gls_plan_desc_t* desc, gls_plan_t* out) {
       return fail(st);
     }
   }
+  pl->tc = uses_tc_factor(*desc);
+  if (pl->tc) {
+    if ((st = gls::tc_factor_create(&pl->tcf, npad)) != GLS_OK) {
+      set_error("%s", gls::tc_factor_last_error());
+      return fail(st);
+    }
+  }
   if (cudaStreamSynchronize(pl->stream) != cudaSuccess) {
     set_error("plan setup failed: %s", cudaGetErrorString(cudaGetLastError()));
     return fail(GLS_ERR_CUDA);
@@ -501,13 +523,21 @@ gls_status_t gls_factor(gls_plan_t pl, const double* M, int64_t ldm, const doubl
   GLS_CUDA(cudaMemsetAsync(pl->flags, 0, sizeof(int) * gls::kFlagCount, st));
   if (M) {
     const int64_t N = npad / gls::kT;
-    pl->launches += 2 + N + 4 * (N - 1);
+    pl->launches += 2 + (pl->tc ? gls::tc_potrf_trtri_launches(npad) : N + 4 * (N - 1));
     pl->has_factor = false;
     GLS_CUDA(cudaMemcpy2DAsync(pl->A, npad * sizeof(double), M, ldm * sizeof(double),
                                n * sizeof(double), n, cudaMemcpyDefault, st));
     gls::launch_pad_lower(pl->A, npad, n, npad, st);
     gls::launch_identity(pl->Z, npad, npad, st);
-    GLS_CUDA(gls::potrf_trtri_fp64(pl->A, pl->Z, npad, npad, pl->flags, st));
+    if (pl->tc) {
+      cudaError_t e = gls::tc_potrf_trtri(pl->tcf, pl->A, pl->Z, npad, npad, pl->flags, st);
+      if (e != cudaSuccess) {
+        set_error("tensor-core factor: %s %s", cudaGetErrorString(e), gls::tc_factor_last_error());
+        return GLS_ERR_CUDA;
+      }
+    } else {
+      GLS_CUDA(gls::potrf_trtri_fp64(pl->A, pl->Z, npad, npad, pl->flags, st));
+    }
   }
   if (p > 1 && XL) {
     GLS_CUDA(cudaMemcpy2DAsync(pl->Wrhs, npad * sizeof(double), XL, ldxl * sizeof(double),
@@ -516,7 +546,17 @@ gls_status_t gls_factor(gls_plan_t pl, const double* M, int64_t ldm, const doubl
   }
   GLS_CUDA(cudaMemcpyAsync(pl->Wrhs + (int64_t)(p - 1) * npad, y, n * sizeof(double),
                            cudaMemcpyDefault, st));
-  gls::launch_whiten(pl->Z, npad, n, npad, pl->Wrhs, npad, p, pl->Wt, npad, pl->flags, st);
+  if (pl->tc) {
+    cudaError_t e = gls::tc_lower_times(pl->tcf, pl->Z, npad, npad, pl->Wrhs, npad, p, pl->Wt,
+                                        npad, pl->flags, st);
+    if (e != cudaSuccess) {
+      set_error("tensor-core whitening: %s %s", cudaGetErrorString(e),
+                gls::tc_factor_last_error());
+      return GLS_ERR_CUDA;
+    }
+  } else {
+    gls::launch_whiten(pl->Z, npad, n, npad, pl->Wrhs, npad, p, pl->Wt, npad, pl->flags, st);
+  }
   gls::launch_fixed_gram(pl->Wt, npad, n, p, pl->gram, st);
   if (p > 1) gls::launch_small_chol(pl->gram, p, pl->RTL, pl->zT, pl->flags, st);
   pl->launches += (p > 1) ? 3 : 2;
@@ -535,12 +575,50 @@ gls_status_t gls_factor(gls_plan_t pl, const double* M, int64_t ldm, const doubl
     return GLS_ERR_COVARIATES_SINGULAR;
   }
   if (pl->precision != GLS_PREC_FP64) {
-    GLS_TRY(gls::mixed_prepare(pl->mixed, pl->Z, npad, pl->Wt, npad, M != nullptr, st));
+    double* W = nullptr;  // M^{-1} [X_L | y] = Z^T [X~_L | y~]
+    if (pl->tc) {
+      W = gls::mixed_w_buffer(pl->mixed);
+      cudaError_t e = gls::tc_lower_t_times(pl->tcf, pl->Z, npad, npad, pl->Wt, npad, p, W, npad,
+                                            pl->flags, st);
+      if (e != cudaSuccess) {
+        set_error("tensor-core W: %s %s", cudaGetErrorString(e), gls::tc_factor_last_error());
+        return GLS_ERR_CUDA;
+      }
+    }
+    GLS_TRY(gls::mixed_prepare(pl->mixed, pl->Z, npad, pl->Wt, npad, M != nullptr, W != nullptr,
+                               st));
     pl->launches += (M != nullptr) ? 3 : 2;
   }
   phase.finish();
   if (pl->precision != GLS_PREC_FP64) GLS_TRY(check_flags(pl, hf));
   pl->factored = true;
+  return GLS_OK;
+}
+
+gls_status_t gls_plan_get_factor(gls_plan_t pl, double* L, int64_t ldl, double* Zinv,
+                                 int64_t ldz) {
+  g_last_error.clear();
+  if (!pl) {
+    set_error("plan is NULL");
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (!pl->has_factor) {
+    set_error("no factor yet");
+    return GLS_ERR_STATE;
+  }
+  if ((L && ldl < pl->n) || (Zinv && ldz < pl->n)) {
+    set_error("leading dimension < n");
+    return GLS_ERR_INVALID_ARG;
+  }
+  DeviceGuard guard(pl->device);
+  const int64_t n = pl->n, npad = pl->npad;
+  if (L)
+    GLS_CUDA(cudaMemcpy2DAsync(L, ldl * sizeof(double), pl->A, npad * sizeof(double),
+                               n * sizeof(double), n, cudaMemcpyDefault, pl->stream));
+  if (Zinv)
+    GLS_CUDA(cudaMemcpy2DAsync(Zinv, ldz * sizeof(double), pl->Z, npad * sizeof(double),
+                               n * sizeof(double), n, cudaMemcpyDefault, pl->stream));
+  GLS_CUDA(cudaStreamSynchronize(pl->stream));
   return GLS_OK;
 }
 

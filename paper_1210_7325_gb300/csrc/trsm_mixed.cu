@@ -852,8 +852,10 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   return GLS_OK;
 }
 
+double* mixed_w_buffer(MixedState* ms) { return ms->Wm; }
+
 gls_status_t mixed_prepare(MixedState* ms, const double* Z, int64_t ldz, const double* Wt,
-                           int64_t ldw, bool new_factor, cudaStream_t st) {
+                           int64_t ldw, bool new_factor, bool w_ready, cudaStream_t st) {
   if (new_factor) {
     const unsigned grid = (unsigned)(ms->npad / 32);
     if (ms->bf16)
@@ -863,8 +865,9 @@ gls_status_t mixed_prepare(MixedState* ms, const double* Z, int64_t ldz, const d
       split_kernel<false><<<grid, 256, 0, st>>>(Z, ldz, ms->npad, ms->S, ms->bits, ms->naive,
                                                 ms->slices, ms->rowscale, ms->diagZ);
   }
-  wtrans_kernel<<<(unsigned)(ms->npad / 64), 256, 0, st>>>(Z, ldz, ms->npad, Wt, ldw, ms->p,
-                                                           ms->Wm);
+  if (!w_ready)
+    wtrans_kernel<<<(unsigned)(ms->npad / 64), 256, 0, st>>>(Z, ldz, ms->npad, Wt, ldw, ms->p,
+                                                             ms->Wm);
   if (ms->bf16)
     split_w_kernel<true><<<(unsigned)ms->p, 256, 0, st>>>(ms->Wm, ms->npad, ms->bits, ms->naive,
                                                          ms->slices, ms->rowscale);

@@ -26,6 +26,8 @@ STATUS_NAMES = {
 }
 PRECISIONS = {"fp64": 0, "bf16": 1, "fp16": 2}
 GLS_FLAG_NAIVE_SPLIT = 1
+GLS_FLAG_FACTOR_NATIVE = 2
+GLS_FLAG_FACTOR_TENSOR = 4
 
 
 class GlsError(RuntimeError):
@@ -111,6 +113,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.gls_plan_set_timing.restype = i32
     lib.gls_plan_stats.argtypes = [vp, P(Stats)]
     lib.gls_plan_stats.restype = i32
+    lib.gls_plan_get_factor.argtypes = [vp, vp, i64, vp, i64]
+    lib.gls_plan_get_factor.restype = i32
     _lib = lib
     return lib
 
@@ -138,9 +142,10 @@ def make_desc(n, p, max_block_snps, precision="fp64", device=0, stream=None, spl
     return d
 
 
-def footprint_bytes(n, p, max_block_snps, precision="fp64", split_terms=0) -> int:
+def footprint_bytes(n, p, max_block_snps, precision="fp64", split_terms=0, flags=0) -> int:
     return int(load().gls_plan_footprint_bytes(
-        ctypes.byref(make_desc(n, p, max_block_snps, precision, split_terms=split_terms))))
+        ctypes.byref(make_desc(n, p, max_block_snps, precision, split_terms=split_terms,
+                               flags=flags))))
 
 
 # ------------------------------------------------------------------ marshalling
@@ -240,6 +245,12 @@ class Plan:
             m = XR.shape[1]
         _check(lib.gls_solve_stream(self._h, px, ldx, int(m), pb, ldb, _ptr(status)),
                "gls_solve_stream")
+
+    def get_factor(self, L=None, Zinv=None):
+        """Copies L and L^{-1} (n x n column-major, host or device) of the last factor."""
+        pl, ldl = _colmajor(L, self.n, 8, "L")
+        pz, ldz = _colmajor(Zinv, self.n, 8, "Zinv")
+        _check(load().gls_plan_get_factor(self._h, pl, ldl, pz, ldz), "gls_plan_get_factor")
 
     def set_timing(self, enable: bool = True):
         """Enables per-kernel device timing (and resets the counters)."""
