@@ -55,40 +55,50 @@ __global__ void identity_kernel(double* __restrict__ Z, int64_t ldz, int64_t npa
 // inverse.  One CTA.  The block already carries every update of the earlier
 // block columns.  A pivot <= 0 records its 1-based global index in
 // flags[kFlagPotrf] (first failure wins) and stops.
+//
+// Right-looking over the 64 columns, the Cholesky and the inverse in the same
+// sweep: at column j warp 0 forms L_jj = sqrt(d_j), scales column j of L and
+// row j of W = L^{-1} by 1/L_jj; then all threads apply the rank-1 updates
+// S_il -= L_ij L_lj (j < l <= i) and W_ic -= L_ij W_jc (c <= j, i > j), with
+// 4 threads per row i.  Binary64 throughput per SM is low on this part, so the
+// pivot arithmetic is kept to one square root and one division per column.
 __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ A,
                                                          double* __restrict__ Z, int64_t ld,
                                                          int64_t k0, int* flags) {
   extern __shared__ double sm[];
-  double(*S)[kLd] = reinterpret_cast<double(*)[kLd]>(sm);
-  double(*W)[kLd] = reinterpret_cast<double(*)[kLd]>(sm + kT * kLd);
+  double(*S)[kLd] = reinterpret_cast<double(*)[kLd]>(sm);            // S[i][l], lower
+  double(*W)[kLd] = reinterpret_cast<double(*)[kLd]>(sm + kT * kLd);  // W[i][c], lower
   __shared__ int fail;
   const int tid = threadIdx.x;
   if (*(volatile int*)&flags[kFlagPotrf] != 0) return;
   for (int idx = tid; idx < kT * kT; idx += blockDim.x) {
-    const int j = idx / kT, i = idx % kT;
-    S[i][j] = (i >= j) ? A[(k0 + i) + (k0 + j) * ld] : 0.0;
-    W[i][j] = 0.0;
+    const int i = idx % kT, l = idx / kT;  // unit stride along i (column-major A)
+    S[i][l] = (i >= l) ? A[(k0 + i) + (k0 + l) * ld] : 0.0;
+    W[i][l] = (i == l) ? 1.0 : 0.0;
   }
   if (tid == 0) fail = 0;
   __syncthreads();
+  const int row = tid / 4, tx = tid % 4, lane = tid % 32;
   for (int j = 0; j < kT; ++j) {
-    if (tid == 0) {
+    if (tid < 32) {
       const double d = S[j][j];
-      if (!(d > 0.0)) fail = j + 1;
-      else S[j][j] = sqrt(d);
+      if (!(d > 0.0)) {
+        if (lane == 0) fail = j + 1;
+      } else {
+        const double ajj = sqrt(d);
+        const double r = 1.0 / ajj;
+        for (int i = j + 1 + lane; i < kT; i += 32) S[i][j] *= r;
+        for (int c = lane; c <= j; c += 32) W[j][c] *= r;
+        __syncwarp();  // every lane has read d before it is overwritten
+        if (lane == 0) S[j][j] = ajj;
+      }
     }
     __syncthreads();
     if (fail) break;
-    const double djj = S[j][j];
-    for (int i = j + 1 + tid; i < kT; i += blockDim.x) S[i][j] /= djj;
-    __syncthreads();
-    const int m = kT - 1 - j;
-    for (int idx = tid; idx < m * m; idx += blockDim.x) {
-      const int a = idx / m, b = idx % m;
-      if (b <= a) {
-        const int i = j + 1 + a, l = j + 1 + b;
-        S[i][l] -= S[i][j] * S[l][j];
-      }
+    if (row > j) {
+      const double lij = S[row][j];
+      for (int l = j + 1 + tx; l <= row; l += 4) S[row][l] = fma(-lij, S[l][j], S[row][l]);
+      for (int c = tx; c <= j; c += 4) W[row][c] = fma(-lij, W[j][c], W[row][c]);
     }
     __syncthreads();
   }
@@ -96,21 +106,10 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ A,
     if (tid == 0) atomicCAS(&flags[kFlagPotrf], 0, (int)(k0 + fail));
     return;
   }
-  // W = S^{-1}: thread c forms column c by forward substitution.
-  if (tid < kT) {
-    const int c = tid;
-    W[c][c] = 1.0 / S[c][c];
-    for (int i = c + 1; i < kT; ++i) {
-      double s = 0.0;
-      for (int j = c; j < i; ++j) s = fma(S[i][j], W[j][c], s);
-      W[i][c] = -s / S[i][i];
-    }
-  }
-  __syncthreads();
   for (int idx = tid; idx < kT * kT; idx += blockDim.x) {
-    const int j = idx / kT, i = idx % kT;
-    A[(k0 + i) + (k0 + j) * ld] = (i >= j) ? S[i][j] : 0.0;
-    Z[(k0 + i) + (k0 + j) * ld] = (i >= j) ? W[i][j] : 0.0;
+    const int i = idx % kT, l = idx / kT;
+    A[(k0 + i) + (k0 + l) * ld] = (i >= l) ? S[i][l] : 0.0;
+    Z[(k0 + i) + (k0 + l) * ld] = (i >= l) ? W[i][l] : 0.0;
   }
 }
 
