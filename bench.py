@@ -38,9 +38,15 @@ WORKLOADS = {
                                      block=65536, seed_offset=2),
     "n10000_p20_m1000000_fp16": dict(n=10000, p=20, m=1_000_000, h=0.5, precision="fp16",
                                      block=65536, seed_offset=2),
+    # the headline n with two SNP blocks: profiler captures of the solve kernel (~6 GB)
+    "n10000_p20_m131072_bf16": dict(n=10000, p=20, m=131072, h=0.5, precision="bf16",
+                                    block=65536, seed_offset=2),
     # mid-size case for profiler captures: genotypes 268 MB (> L2), ~2 GB on the device
     "n4096_p20_m65536_bf16": dict(n=4096, p=20, m=65536, h=0.5, precision="bf16",
                                   block=65536, seed_offset=2),
+    # a mid-size scan, the middle of the serving mix
+    "n2000_p12_m131072_bf16": dict(n=2000, p=12, m=131072, h=0.5, precision="bf16",
+                                   block=65536, seed_offset=4),
     "n1000_p4_m4096_fp64": dict(n=1000, p=4, m=4096, h=0.4, precision="fp64", block=4096,
                                 seed_offset=0),
     "n1500_p4_m2500000_fp64": dict(n=1500, p=4, m=2_500_000, h=0.5, precision="fp64",
@@ -227,6 +233,34 @@ def run_gpu(args, wl, rank, world, torch, dist):
         res["e2e_d2h"] = p * m * 8 + 4 * m
     plan.close()
     return res
+
+
+def run_factor_only(args, wl, torch):
+    """gls_factor alone (Cholesky of M, L^{-1}, whitening, fixed Gram), timed
+    with CUDA events on the plan's stream; a profiling and tuning aid."""
+    import numpy as np
+    from paper_1210_7325_gb300 import gls
+    n, p, prec = wl["n"], wl["p"], wl["precision"]
+    M, XL, y, _ = make_inputs(dict(wl, m=1), 0, torch)
+    Md = torch.from_numpy(np.ascontiguousarray(M.T)).cuda().t()
+    XLd = torch.from_numpy(np.ascontiguousarray(XL.T)).cuda().t()
+    yd = torch.from_numpy(y).cuda()
+    flags = gls.GLS_FLAG_FACTOR_NATIVE if (args.factor_native and prec != "fp64") else 0
+    plan = gls.Plan(n, p, 1024, precision=prec, flags=flags)
+    for _ in range(args.warmup):
+        plan.factor(Md, XLd, yd)
+    plan.synchronize()
+    plan.set_timing(True)
+    for _ in range(args.steps):
+        plan.factor(Md, XLd, yd)
+    s = plan.stats()
+    plan.close()
+    return {"metric": "gls_factor time", "value": s["factor_ms"] / args.steps, "unit": "ms",
+            "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": args.workload, "n": n, "p": p, "precision": prec,
+                       "factor": "binary64 CUDA cores" if flags else
+                       ("tensor-core exact slices" if prec != "fp64" else "binary64 CUDA cores")},
+            "gpu_launches_per_call": s["launches"] / args.steps}
 
 
 def fp64_sample(wl, torch, m_sample=16384):
@@ -574,6 +608,10 @@ def main():
                     default=DEFAULT_WORKLOAD)
     ap.add_argument("--requests", type=int, default=0, help="serving: number of requests")
     ap.add_argument("--time-cap", type=float, default=0.0, help="serving: wall-time cap (s)")
+    ap.add_argument("--factor-only", action="store_true",
+                    help="time gls_factor alone on the workload's M (setup phase, Alg. 5 lines 1-6)")
+    ap.add_argument("--factor-native", action="store_true",
+                    help="with --factor-only on a mixed workload: the binary64 CUDA-core factor")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
@@ -596,6 +634,12 @@ def main():
         return
     wl = WORKLOADS[args.workload]
     args.warmup = max(args.warmup, 3) if args.impl == "gb300" else args.warmup
+    if args.factor_only:
+        import torch
+        from paper_1210_7325_gb300 import build as gbuild
+        gbuild.build()
+        print(json.dumps(run_factor_only(args, wl, torch)), flush=True)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

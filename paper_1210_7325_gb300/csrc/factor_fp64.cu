@@ -59,9 +59,10 @@ __global__ void identity_kernel(double* __restrict__ Z, int64_t ldz, int64_t npa
 // Right-looking over the 64 columns, the Cholesky and the inverse in the same
 // sweep: at column j warp 0 forms L_jj = sqrt(d_j), scales column j of L and
 // row j of W = L^{-1} by 1/L_jj; then all threads apply the rank-1 updates
-// S_il -= L_ij L_lj (j < l <= i) and W_ic -= L_ij W_jc (c <= j, i > j), with
-// 4 threads per row i.  Binary64 throughput per SM is low on this part, so the
-// pivot arithmetic is kept to one square root and one division per column.
+// S_il -= L_ij L_lj (j < l <= i) and W_ic -= L_ij W_jc (c <= j, i > j),
+// numbered densely over the threads.  Binary64 throughput per SM is low on this
+// part, so the pivot is one reciprocal square root (FP32 estimate, two Newton
+// steps) and no binary64 instruction runs with idle lanes.
 __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ A,
                                                          double* __restrict__ Z, int64_t ld,
                                                          int64_t k0, int* flags) {
@@ -78,15 +79,25 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ A,
   }
   if (tid == 0) fail = 0;
   __syncthreads();
-  const int row = tid / 4, tx = tid % 4, lane = tid % 32;
+  const int lane = tid % 32;
   for (int j = 0; j < kT; ++j) {
     if (tid < 32) {
       const double d = S[j][j];
       if (!(d > 0.0)) {
         if (lane == 0) fail = j + 1;
       } else {
-        const double ajj = sqrt(d);
-        const double r = 1.0 / ajj;
+        // r = 1/sqrt(d): the FP32 estimate refined by two binary64 Newton steps
+        // (a short dependent chain; binary64 latency on this part is long)
+        double r;
+        if (d > 1e-30 && d < 1e30) {
+          const double h = 0.5 * d;
+          r = (double)rsqrtf((float)d);
+          r = r * fma(-h * r, r, 1.5);
+          r = r * fma(-h * r, r, 1.5);
+        } else {
+          r = 1.0 / sqrt(d);
+        }
+        const double ajj = d * r;
         for (int i = j + 1 + lane; i < kT; i += 32) S[i][j] *= r;
         for (int c = lane; c <= j; c += 32) W[j][c] *= r;
         __syncwarp();  // every lane has read d before it is overwritten
@@ -95,10 +106,43 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ A,
     }
     __syncthreads();
     if (fail) break;
-    if (row > j) {
-      const double lij = S[row][j];
-      for (int l = j + 1 + tx; l <= row; l += 4) S[row][l] = fma(-lij, S[l][j], S[row][l]);
-      for (int c = tx; c <= j; c += 4) W[row][c] = fma(-lij, W[j][c], W[row][c]);
+    {
+      // The column's updates, S_il (j < l <= i) then W_ic (c <= j < i), are
+      // numbered densely over all threads so that every lane of every binary64
+      // instruction does useful work; four per thread are loaded before any
+      // store so their FMAs overlap.
+      const int m = kT - 1 - j, ns = m * (m + 1) / 2, total = ns + m * (j + 1);
+      for (int q0 = tid; q0 < total; q0 += 4 * 256) {
+        double av[4], bv[4], lv[4];
+        double* dst[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = q0 + u * 256;
+          dst[u] = nullptr;
+          if (q < total) {
+            int i;
+            if (q < ns) {
+              int ip = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
+              while ((ip + 1) * (ip + 2) / 2 <= q) ++ip;
+              while (ip * (ip + 1) / 2 > q) --ip;
+              const int l = j + 1 + (q - ip * (ip + 1) / 2);
+              i = j + 1 + ip;
+              dst[u] = &S[i][l];
+              bv[u] = S[l][j];
+            } else {
+              const int r = q - ns, ip = r / (j + 1), c = r - ip * (j + 1);
+              i = j + 1 + ip;
+              dst[u] = &W[i][c];
+              bv[u] = W[j][c];
+            }
+            lv[u] = S[i][j];
+            av[u] = *dst[u];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (dst[u]) *dst[u] = fma(-lv[u], bv[u], av[u]);
+      }
     }
     __syncthreads();
   }

@@ -41,18 +41,24 @@
 // Every product has a long inner dimension, so the binary64 epilogue runs once
 // per output element of each product rather than once per 64-deep update.
 //
-// Tensor-core kernel.  One persistent CTA per SM, 320 threads:
-//   warp 0     TMA producer: per 32-deep stage, the 7 slices of a 128-row A tile
-//              and of a 64-row B tile (64-byte swizzle), one mbarrier per stage
+// Tensor-core kernel.  One persistent CTA per SM, 320 threads, output tiles of
+// 128 x BN (BN = 64; BN = 16 for products with few tiles, so that more SMs
+// share their binary64 epilogue):
+//   warp 0     TMA producer: per 16-deep stage, the 7 slices of a 128-row A tile
+//              and of a BN-row B tile (32-byte swizzle), 5-6 stages in flight
 //   warp 1     TMEM allocator and the thread issuing tcgen05.mma (M = 128,
-//              N = 64, K = 16, BF16 in, FP32 accumulate): 28 pairs x 2 per stage
+//              N = BN, K = 16, BF16 in, FP32 accumulate): 28 pairs per stage
 //              into five accumulators; each accumulator has its own full/empty
 //              barrier pair, so the epilogue drains level L of one 128-deep
 //              chunk while the tensor core works on the later levels and the
 //              next chunk
-//   warps 2-9  epilogue: two warps per TMEM lane quarter, 32 columns each;
+//   warps 2-9  epilogue: two warps per TMEM lane quarter, BN/2 columns each;
 //              per chunk tcgen05.ld of the five accumulators into the int64 and
-//              FP32 sums, per tile the binary64 result written to C
+//              FP32 sums, per tile the binary64 result written to C (three
+//              binary64 operations per element; the power-of-two scale is an
+//              exponent-field add)
+// The slices are formed by one launch per product (both operands): row
+// maxima, then integer digit extraction, 8 consecutive k per 16-byte store.
 // Every mbarrier wait is bounded (1 s of %globaltimer); a timeout sets an error
 // flag, drains what is in flight, frees tensor memory and returns.
 #include <cuda.h>
@@ -76,21 +82,28 @@ namespace {
 
 constexpr int kS = 7;                  // slices per binary64 operand
 constexpr int OBM = 128;               // output rows per tile (TMEM lanes)
-constexpr int OBN = 64;                // output columns per tile
-constexpr int OBK = 32;                // K per stage: 32 x 16-bit = one 64-byte swizzle row
-constexpr int kChunkStages = 4;        // exact chunks of 128
-constexpr int kStages = 2;
+constexpr int OBK = 16;                // K per stage: 16 x 16-bit = one 32-byte swizzle row
+constexpr int kChunkStages = 8;        // exact chunks of 128
+constexpr int kKAlign = 32;            // operand rows are stored padded to a multiple of 32
 constexpr int kAcc = 5;                // levels 0, 1, 2, 3 (exact) and the tail 4..6
-constexpr uint32_t kTmemCols = 512;    // 5 accumulators x 64 columns (power-of-two allocation)
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr int kABytes = kS * OBM * OBK * 2;     // 57344
-constexpr int kBBytes = kS * OBN * OBK * 2;     // 28672
-constexpr int kStageBytes = kABytes + kBBytes;  // 86016 = 84 KiB
-constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
 constexpr uint64_t kWaitLimitNs = 1000000000ull;
 constexpr uint64_t kDrainLimitNs = 100000000ull;
 constexpr int kExpNonFinite = 4096;    // row exponent marking a row with Inf/NaN
+
+// Tile shapes: BN = 64 output columns for large products, BN = 16 for small
+// ones (more CTAs share the binary64 epilogue of a few output tiles).
+template <int BN>
+struct Shape {
+  static constexpr int kABytes = kS * OBM * OBK * 2;       // 28672
+  static constexpr int kBBytes = kS * BN * OBK * 2;        // 14336 or 3584
+  static constexpr int kStageBytes = kABytes + kBBytes;    // multiples of 512
+  static constexpr int kStages = BN == 64 ? 5 : 6;
+  static constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
+  static constexpr uint32_t kTmemCols = BN == 64 ? 512 : 128;  // 5 accumulators x BN
+  static constexpr int kCols = BN / 2;                     // columns per epilogue warp
+};
 
 enum KMode : int { kKFull = 0, kKLeJ = 1, kKGeJ = 2, kKLeI = 3, kKGeI = 4 };
 
@@ -102,20 +115,21 @@ struct OzParams {
   const int* eA;     // row exponents of the A operand
   const int* eB;     // row exponents of the B operand
   int64_t diag_off;  // lower: store only where row + diag_off >= col
-  double alpha;
   int M, N, tilesI, tilesJ;
   int Kend, kmode, koff;
-  int beta, lower;
+  int neg, beta, lower;  // C = (neg ? -1 : 1) A B^T + (beta ? C : 0)
   int* flags;        // plan status words: kFlagPotrf read, kFlagKernel / kFlagWhere written
 };
 
-__device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t smem_addr) {
+// K-major operand tile written by TMA with 32-byte swizzling: rows of 32
+// bytes (16 BF16), 8-row groups 256 bytes apart.
+__device__ __forceinline__ uint64_t umma_desc_sw32(uint32_t smem_addr) {
   uint64_t d = 0;
   d |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
   d |= (uint64_t)(16u >> 4) << 16;   // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(512u >> 4) << 32;  // stride byte offset: 8 rows x 64 bytes
+  d |= (uint64_t)(256u >> 4) << 32;  // stride byte offset: 8 rows x 32 bytes
   d |= (uint64_t)1 << 46;            // descriptor version
-  d |= (uint64_t)4 << 61;            // 64-byte swizzle
+  d |= (uint64_t)6 << 61;            // 32-byte swizzle
   return d;
 }
 
@@ -124,20 +138,30 @@ __device__ __forceinline__ double pow2i(int e) {
   return ldexp(1.0, e);
 }
 
+// d * 2^e: an exponent-field add while the result stays a normal number.
+__device__ __forceinline__ double scale2(double d, int e) {
+  const long long b = __double_as_longlong(d);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex != 0 && ex != 0x7FF && ex + e >= 1 && ex + e <= 2046)
+    return __longlong_as_double(b + ((long long)e << 52));
+  return d * pow2i(e);
+}
+
 struct TileWork {
   int I, J, k0, k1;
   bool valid;
 };
 
+template <int BN>
 __device__ __forceinline__ TileWork tile_work(const OzParams& q, int t) {
   TileWork w;
   w.I = t / q.tilesJ;
   w.J = t - w.I * q.tilesJ;
-  w.valid = !q.lower || ((int64_t)w.I * OBM + OBM - 1 + q.diag_off >= (int64_t)w.J * OBN);
+  w.valid = !q.lower || ((int64_t)w.I * OBM + OBM - 1 + q.diag_off >= (int64_t)w.J * BN);
   int k0 = 0, k1 = q.Kend;
   switch (q.kmode) {
-    case kKLeJ: k1 = min(k1, (w.J + 1) * OBN + q.koff); break;
-    case kKGeJ: k0 = w.J * OBN + q.koff; break;
+    case kKLeJ: k1 = min(k1, (w.J + 1) * BN + q.koff); break;
+    case kKGeJ: k0 = w.J * BN + q.koff; break;
     case kKLeI: k1 = min(k1, (w.I + 1) * OBM + q.koff); break;
     case kKGeI: k0 = w.I * OBM + q.koff; break;
     default: break;
@@ -174,24 +198,37 @@ __device__ __forceinline__ bool wait_drain(uint64_t* bar, uint32_t parity) {
 
 __device__ __forceinline__ float f32(uint32_t v) { return __uint_as_float(v); }
 
+// One accumulator's columns of this warp (32 or 8), waited for.
+__device__ __forceinline__ void ld_cols(uint32_t taddr, uint32_t (&r)[32]) {
+  tmem_ld32(taddr, r);
+  tmem_ld_wait(r);
+}
+__device__ __forceinline__ void ld_cols(uint32_t taddr, uint32_t (&r)[8]) {
+  tmem_ld8(taddr, r);
+  tmem_ld_wait8(r);
+}
+
+template <int BN>
 __global__ void __launch_bounds__(kThreads, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ OzParams q) {
+  using Sh = Shape<BN>;
+  constexpr int CW = Sh::kCols;
   if (*(volatile const int*)&q.flags[kFlagPotrf] != 0) return;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-  uint64_t* full = reinterpret_cast<uint64_t*>(base + kStages * kStageBytes);
-  uint64_t* empty = full + kStages;
-  uint64_t* afull = empty + kStages;   // per accumulator: chunk's products complete
-  uint64_t* aempty = afull + kAcc;     // per accumulator: drained by the epilogue
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + Sh::kStages * Sh::kStageBytes);
+  uint64_t* empty = full + Sh::kStages;
+  uint64_t* afull = empty + Sh::kStages;  // per accumulator: chunk's products complete
+  uint64_t* aempty = afull + kAcc;        // per accumulator: drained by the epilogue
   uint64_t* drain = aempty + kAcc;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < Sh::kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -204,7 +241,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     fence_barrier_init();
   }
   if (warp == 1) {
-    tmem_alloc(tmem_slot, kTmemCols);
+    tmem_alloc(tmem_slot, Sh::kTmemCols);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -221,78 +258,72 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t g = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const TileWork w = tile_work(q, t);
+        const TileWork w = tile_work<BN>(q, t);
         if (!w.valid) continue;
         for (int k = w.k0; k < w.k1; k += OBK, ++g) {
-          const int st = (int)(g % kStages);
-          const uint32_t ph = g / kStages;
+          const int st = (int)(g % Sh::kStages);
+          const uint32_t ph = g / Sh::kStages;
           if (!mbar_wait_bounded(&empty[st], (ph & 1) ^ 1, abort_flag, kWaitLimitNs)) {
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(&full[st], (uint32_t)kStageBytes);
-          uint8_t* sb = base + (size_t)st * kStageBytes;
+          mbar_arrive_expect_tx(&full[st], (uint32_t)Sh::kStageBytes);
+          uint8_t* sb = base + (size_t)st * Sh::kStageBytes;
           tma_load_3d(sb, &tmA, &full[st], k, w.I * OBM, 0);
-          tma_load_3d(sb + kABytes, &tmB, &full[st], k, w.J * OBN, 0);
+          tma_load_3d(sb + Sh::kABytes, &tmB, &full[st], k, w.J * BN, 0);
         }
       }
       if (!ok) {
         raise_error(q.flags, 1);
-        const uint32_t first = g > (uint32_t)kStages ? g - kStages : 0;
+        const uint32_t first = g > (uint32_t)Sh::kStages ? g - Sh::kStages : 0;
         for (uint32_t g2 = first; g2 < g; ++g2)
-          wait_drain(&full[g2 % kStages], (g2 / kStages) & 1);
+          wait_drain(&full[g2 % Sh::kStages], (g2 / Sh::kStages) & 1);
       }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = umma_idesc_f16(OBM, OBN, true);
+      const uint32_t idesc = umma_idesc_f16(OBM, BN, true);
       uint32_t g = 0, cg = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const TileWork w = tile_work(q, t);
+        const TileWork w = tile_work<BN>(q, t);
         if (!w.valid) continue;
         const int nk = (w.k1 - w.k0) / OBK;
         for (int s0 = 0; s0 < nk && ok; s0 += kChunkStages, ++cg) {
           const uint32_t par = cg & 1;
           const int ns = min(kChunkStages, nk - s0);
           for (int s = 0; s < ns && ok; ++s, ++g) {
-            const int st = (int)(g % kStages);
-            const uint32_t ph = g / kStages;
+            const int st = (int)(g % Sh::kStages);
+            const uint32_t ph = g / Sh::kStages;
             if (!mbar_wait_bounded(&full[st], ph & 1, abort_flag, kWaitLimitNs)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint32_t sa = smem_u32(base + (size_t)st * kStageBytes);
-            const uint32_t sbb = sa + kABytes;
+            const uint32_t sa = smem_u32(base + (size_t)st * Sh::kStageBytes);
+            const uint32_t sbb = sa + Sh::kABytes;
+            const bool chunk_first = s == 0;
+            const bool chunk_last = s == ns - 1;
 #pragma unroll
-            for (int kk = 0; kk < OBK / 16; ++kk) {
-              const bool chunk_first = (s == 0) && (kk == 0);
-              const bool chunk_last = (s == ns - 1) && (kk == OBK / 16 - 1);
-#pragma unroll
-              for (int lam = 0; lam < kS; ++lam) {
-                const int acc = lam < kAcc - 1 ? lam : kAcc - 1;
-                if (chunk_first && lam < kAcc) {
-                  // the previous chunk's value of this accumulator has been read
-                  if (!mbar_wait_bounded(&aempty[acc], par ^ 1, abort_flag, kWaitLimitNs)) {
-                    ok = false;
-                    break;
-                  }
-                  tc_fence_after();
+            for (int lam = 0; lam < kS; ++lam) {
+              const int acc = lam < kAcc - 1 ? lam : kAcc - 1;
+              if (chunk_first && lam < kAcc) {
+                // the previous chunk's value of this accumulator has been read
+                if (!mbar_wait_bounded(&aempty[acc], par ^ 1, abort_flag, kWaitLimitNs)) {
+                  ok = false;
+                  break;
                 }
-#pragma unroll
-                for (int ta = 0; ta <= lam; ++ta) {
-                  const int tb = lam - ta;
-                  const bool fresh = chunk_first && ta == 0 && lam < kAcc;
-                  umma_f16(tmem + (uint32_t)acc * OBN,
-                           umma_desc_sw64(sa + ta * (OBM * OBK * 2) + kk * 32),
-                           umma_desc_sw64(sbb + tb * (OBN * OBK * 2) + kk * 32), idesc,
-                           fresh ? 0u : 1u);
-                }
-                if (chunk_last && (lam < kAcc - 1 || lam == kS - 1)) umma_commit(&afull[acc]);
+                tc_fence_after();
               }
-              if (!ok) break;
+#pragma unroll
+              for (int ta = 0; ta <= lam; ++ta) {
+                const int tb = lam - ta;
+                const bool fresh = chunk_first && ta == 0 && lam < kAcc;
+                umma_f16(tmem + (uint32_t)(acc * BN), umma_desc_sw32(sa + ta * (OBM * OBK * 2)),
+                         umma_desc_sw32(sbb + tb * (BN * OBK * 2)), idesc, fresh ? 0u : 1u);
+              }
+              if (chunk_last && (lam < kAcc - 1 || lam == kS - 1)) umma_commit(&afull[acc]);
             }
             umma_commit(&empty[st]);
           }
@@ -307,17 +338,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int quarter = warp & 3;
     const int half = (warp - 2) >> 2;
     const int rl = quarter * 32 + lane;
-    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)half * 32;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * CW);
     uint32_t cg = 0;
     bool alive = true;
     for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
-      const TileWork w = tile_work(q, t);
+      const TileWork w = tile_work<BN>(q, t);
       if (!w.valid) continue;
       const int nk = (w.k1 - w.k0) / OBK;
-      long long V[32];
-      float tl[32];
+      long long V[CW];  // exact levels 0..3, in units of 2^-24 of level 0
+      float tl[CW];     // levels 4..6
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
+      for (int j = 0; j < CW; ++j) {
         V[j] = 0;
         tl[j] = 0.f;
       }
@@ -332,21 +363,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc_fence_after();
-          uint32_t r[32];
-          tmem_ld32(lane_base + (uint32_t)a * OBN, r);
-          tmem_ld_wait(r);
+          uint32_t r[CW];
+          ld_cols(lane_base + (uint32_t)(a * BN), r);
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&aempty[a]);
           if (a < kAcc - 1) {
-            // level a: an integer multiple of 2^(-8a); V counts units of 2^-24
+            // level a: an integer multiple of 2^(-8a)
             const float up = (float)(1u << (8 * a));
-            const long long w = 1ll << (24 - 8 * a);
+            const long long wgt = 1ll << (24 - 8 * a);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) V[j] += (long long)__float2int_rn(f32(r[j]) * up) * w;
+            for (int j = 0; j < CW; ++j) V[j] += (long long)__float2int_rn(f32(r[j]) * up) * wgt;
           } else {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) tl[j] += f32(r[j]);
+            for (int j = 0; j < CW; ++j) tl[j] += f32(r[j]);
           }
         }
       }
@@ -354,9 +384,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t row = (int64_t)w.I * OBM + rl;
       if (row < q.M) {
         const int ea = q.eA[row];
-        const int64_t col0 = (int64_t)w.J * OBN + half * 32;
+        const int64_t col0 = (int64_t)w.J * BN + half * CW;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
+        for (int j = 0; j < CW; ++j) {
           const int64_t col = col0 + j;
           if (col < q.N && (!q.lower || row + q.diag_off >= col)) {
             const int eb = q.eB[col];
@@ -364,11 +394,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (ea == kExpNonFinite || eb == kExpNonFinite) {
               d = __longlong_as_double(0x7ff8000000000000ll);
             } else {
-              const int e = ea + eb - 16;
-              d = fma((double)V[j], pow2i(e - 24), (double)tl[j] * pow2i(e));
+              // 2^(ea + eb - 16) (V 2^-24 + tl), with tl 2^24 exact in FP32
+              d = scale2((double)V[j] + (double)(tl[j] * 16777216.f), ea + eb - 40);
             }
+            if (q.neg) d = -d;
             double* cp = q.C + row + col * q.ldc;
-            *cp = q.beta ? fma(q.alpha, d, *cp) : q.alpha * d;
+            *cp = q.beta ? *cp + d : d;
           }
         }
       }
@@ -377,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) tmem_dealloc(tmem, kTmemCols);
+  if (warp == 1) tmem_dealloc(tmem, Sh::kTmemCols);
 }
 
 // ---------------------------------------------------------------- slicing
@@ -414,102 +445,176 @@ __device__ __forceinline__ void slice_value(double x, int E, uint16_t (&s)[kS]) 
   s[kS - 1] = __bfloat16_as_ushort(__float2bfloat16_rn(ldexpf((float)r, -8 * (kS - 1))));
 }
 
-// Operand row i = source row i, k = source column k: x(i, k) = src[i + k ld],
-// i < R, k < K; out[t][i][k] with row length kld (zeros for K <= k < kld).
-// One CTA per 32 rows; lanes walk rows (coalesced reads), warps walk k, and
-// the K-major slices are written through a shared-memory transpose.
-__global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ src,
-                                                         int64_t ld, int64_t R, int64_t K,
-                                                         int64_t kld, uint16_t* __restrict__ out,
-                                                         int* __restrict__ expo,
-                                                         const int* flags) {
-  if (*(volatile const int*)&flags[kFlagPotrf] != 0) return;
-  __shared__ double red[8][33];
-  __shared__ int bad[8][33];
-  __shared__ int Es[32];
-  __shared__ __align__(16) uint16_t sh[kS][32][OBK + 8];
-  const int l = threadIdx.x % 32, w = threadIdx.x / 32;
-  const int64_t i = (int64_t)blockIdx.x * 32 + l;
-  const bool iv = i < R;
-  double m = 0.0;
-  int nf = 0;
-  if (iv)
-    for (int64_t k = w; k < K; k += 8) {
-      const double v = src[i + k * ld];
-      nf |= !isfinite(v);
-      m = fmax(m, fabs(v));
-    }
-  red[w][l] = m;
-  bad[w][l] = nf;
-  __syncthreads();
-  if (w == 0) {
-    for (int v = 1; v < 8; ++v) {
-      m = fmax(m, red[v][l]);
-      nf |= bad[v][l];
-    }
-    const int E = row_exponent(m, nf != 0);
-    Es[l] = E;
-    if (iv) expo[i] = E;
+// One operand to slice: x(i, k) = src[i + k ld] (rows mode, operand rows are
+// source rows) or src[k + i ld] (columns mode), i < R, k < K; written as
+// out[t][i][k], t < kS, row length kld (zeros for K <= k < kld), plus the row
+// exponents expo[i].  nblocks CTAs: 32 rows each (rows mode) or 16 (columns).
+struct SliceJob {
+  const double* src;
+  int64_t ld, R, K, kld;
+  uint16_t* out;
+  int* expo;
+  // Null: every CTA forms its rows' maxima over the whole k range itself.
+  // Otherwise the row maxima of |x| as bit patterns, written by rowmax_kernel.
+  unsigned long long* maxbits;
+  int rows_mode;
+  int kspan;    // k per CTA (a multiple of 256), kld when maxbits is null
+  int kblocks;  // CTAs per row band along k
+  int nblocks;  // bands x kblocks
+};
+
+__device__ __forceinline__ void pack8(const uint16_t (&v)[8][kS], int t, uint4& o) {
+  o.x = (uint32_t)v[0][t] | ((uint32_t)v[1][t] << 16);
+  o.y = (uint32_t)v[2][t] | ((uint32_t)v[3][t] << 16);
+  o.z = (uint32_t)v[4][t] | ((uint32_t)v[5][t] << 16);
+  o.w = (uint32_t)v[6][t] | ((uint32_t)v[7][t] << 16);
+}
+
+constexpr int kSliceWarps = 16;
+constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
+
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(fabs(v));  // Inf / NaN sort above finite
+}
+
+__device__ __forceinline__ int exponent_of_bits(unsigned long long mb) {
+  return row_exponent(__longlong_as_double((long long)(mb & ~(1ull << 63))), mb >= kInfBits);
+}
+
+// 8 consecutive k (k0 .. k0+7) of one operand row: x(k) = base[k * stride],
+// sliced and stored as one 16-byte vector per slice.
+__device__ __forceinline__ void slice_store8(const double* base, int64_t stride, int64_t K,
+                                             int64_t k0, int E, uint16_t* dst, size_t plane) {
+  uint16_t v[8][kS];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int64_t k = k0 + e;
+    slice_value(k < K ? base[k * stride] : 0.0, E, v[e]);
   }
-  __syncthreads();
-  const int E = Es[l];
-  const size_t plane = (size_t)R * kld;
-  for (int64_t k0 = 0; k0 < kld; k0 += OBK) {
 #pragma unroll
-    for (int e = 0; e < OBK / 8; ++e) {
-      const int kk = w + 8 * e;
-      const int64_t k = k0 + kk;
-      uint16_t s[kS];
-      slice_value((iv && k < K) ? src[i + k * ld] : 0.0, E, s);
-#pragma unroll
-      for (int t = 0; t < kS; ++t) sh[t][l][kk] = s[t];
-    }
-    __syncthreads();
-    // kS slices x 32 rows x 4 uint4 (64 bytes per row)
-    for (int idx = threadIdx.x; idx < kS * 32 * 4; idx += 256) {
-      const int t = idx / 128, rr = (idx / 4) % 32, c4 = idx % 4;
-      const int64_t ii = (int64_t)blockIdx.x * 32 + rr;
-      if (ii < R) {
-        const uint4 v = *reinterpret_cast<const uint4*>(&sh[t][rr][c4 * 8]);
-        *reinterpret_cast<uint4*>(out + t * plane + ii * kld + k0 + c4 * 8) = v;
-      }
-    }
-    __syncthreads();
+  for (int t = 0; t < kS; ++t) {
+    uint4 o;
+    pack8(v, t, o);
+    *reinterpret_cast<uint4*>(dst + t * plane + k0) = o;
   }
 }
 
-// Operand row i = source column i, k = source row k: x(i, k) = src[k + i ld].
-// One warp per operand row.
-__global__ void __launch_bounds__(256) slice_cols_kernel(const double* __restrict__ src,
-                                                         int64_t ld, int64_t R, int64_t K,
-                                                         int64_t kld, uint16_t* __restrict__ out,
-                                                         int* __restrict__ expo,
-                                                         const int* flags) {
-  if (*(volatile const int*)&flags[kFlagPotrf] != 0) return;
+// Rows mode tile: 32 rows (lane = row, reads coalesced along the column-major
+// source) x one k span; warps split the span.
+__device__ void slice_rows_tile(const SliceJob& j, int band, int kb) {
+  __shared__ unsigned long long red[kSliceWarps][33];
+  __shared__ int Es[32];
   const int l = threadIdx.x % 32, w = threadIdx.x / 32;
-  const int64_t i = (int64_t)blockIdx.x * 8 + w;
-  if (i >= R) return;
-  const double* col = src + i * ld;
-  double m = 0.0;
-  int nf = 0;
-  for (int64_t k = l; k < K; k += 32) {
-    const double v = col[k];
-    nf |= !isfinite(v);
-    m = fmax(m, fabs(v));
+  const int64_t i = (int64_t)band * 32 + l;
+  const bool iv = i < j.R;
+  const double* row = j.src + (iv ? i : 0);
+  if (!j.maxbits) {
+    unsigned long long m = 0;
+    if (iv) {
+#pragma unroll 8
+      for (int64_t k = w; k < j.K; k += kSliceWarps) m = max(m, abs_bits(row[k * j.ld]));
+    }
+    red[w][l] = m;
+    __syncthreads();
+    if (w == 0) {
+      for (int v = 1; v < kSliceWarps; ++v) m = max(m, red[v][l]);
+      const int E = exponent_of_bits(m);
+      Es[l] = E;
+      if (iv) j.expo[i] = E;
+    }
+    __syncthreads();
+  } else if (w == 0) {
+    const int E = iv ? exponent_of_bits(j.maxbits[i]) : 0;
+    Es[l] = E;
+    if (iv && kb == 0) j.expo[i] = E;
   }
+  if (j.maxbits) __syncthreads();
+  if (!iv) return;
+  const int E = Es[l];
+  const size_t plane = (size_t)j.R * j.kld;
+  uint16_t* dst = j.out + i * j.kld;
+  const int64_t kend = min(j.kld, (int64_t)(kb + 1) * j.kspan);
+  for (int64_t k0 = (int64_t)kb * j.kspan + w * 8; k0 < kend; k0 += 8 * kSliceWarps)
+    slice_store8(row, j.ld, j.K, k0, E, dst, plane);
+}
+
+// Columns mode tile: 16 operand rows (one warp each, a contiguous source
+// column) x one k span.
+__device__ void slice_cols_tile(const SliceJob& j, int band, int kb) {
+  const int l = threadIdx.x % 32, w = threadIdx.x / 32;
+  const int64_t i = (int64_t)band * kSliceWarps + w;
+  if (i >= j.R) return;
+  const double* col = j.src + i * j.ld;
+  int E;
+  if (!j.maxbits) {
+    unsigned long long m = 0;
+#pragma unroll 4
+    for (int64_t k = l; k < j.K; k += 32) m = max(m, abs_bits(col[k]));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    nf |= __shfl_xor_sync(0xffffffffu, nf, o);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    E = exponent_of_bits(m);
+  } else {
+    E = exponent_of_bits(j.maxbits[i]);
   }
-  const int E = row_exponent(m, nf != 0);
-  if (l == 0) expo[i] = E;
-  const size_t plane = (size_t)R * kld;
-  for (int64_t k = l; k < kld; k += 32) {
-    uint16_t s[kS];
-    slice_value(k < K ? col[k] : 0.0, E, s);
+  if (l == 0 && kb == 0) j.expo[i] = E;
+  const size_t plane = (size_t)j.R * j.kld;
+  uint16_t* dst = j.out + i * j.kld;
+  const int64_t kend = min(j.kld, (int64_t)(kb + 1) * j.kspan);
+  for (int64_t k0 = (int64_t)kb * j.kspan + l * 8; k0 < kend; k0 += 256)
+    slice_store8(col, 1, j.K, k0, E, dst, plane);
+}
+
+// Up to two operands in one launch: blocks [0, a.nblocks) slice a, the rest b.
+__global__ void __launch_bounds__(32 * kSliceWarps) slice_kernel(const SliceJob a,
+                                                                 const SliceJob b,
+                                                                 const int* flags) {
+  if (*(volatile const int*)&flags[kFlagPotrf] != 0) return;
+  const bool first = (int)blockIdx.x < a.nblocks;
+  const SliceJob& j = first ? a : b;
+  const int bid = first ? (int)blockIdx.x : (int)blockIdx.x - a.nblocks;
+  const int band = bid / j.kblocks, kb = bid - band * j.kblocks;
+  if (j.rows_mode) slice_rows_tile(j, band, kb);
+  else slice_cols_tile(j, band, kb);
+}
+
+// Row maxima of |x| (bit patterns, atomicMax into maxbits zeroed beforehand)
+// over the same tiles as slice_kernel, for operands split along k.
+__global__ void __launch_bounds__(32 * kSliceWarps) rowmax_kernel(const SliceJob a,
+                                                                  const SliceJob b,
+                                                                  const int* flags) {
+  if (*(volatile const int*)&flags[kFlagPotrf] != 0) return;
+  __shared__ unsigned long long red[kSliceWarps][33];
+  const bool first = (int)blockIdx.x < a.nblocks;
+  const SliceJob& j = first ? a : b;
+  if (!j.maxbits) return;
+  const int bid = first ? (int)blockIdx.x : (int)blockIdx.x - a.nblocks;
+  const int band = bid / j.kblocks, kb = bid - band * j.kblocks;
+  const int l = threadIdx.x % 32, w = threadIdx.x / 32;
+  const int64_t k_lo = (int64_t)kb * j.kspan, k_hi = min(j.K, k_lo + j.kspan);
+  if (j.rows_mode) {
+    const int64_t i = (int64_t)band * 32 + l;
+    unsigned long long m = 0;
+    if (i < j.R) {
+      const double* row = j.src + i;
+#pragma unroll 8
+      for (int64_t k = k_lo + w; k < k_hi; k += kSliceWarps) m = max(m, abs_bits(row[k * j.ld]));
+    }
+    red[w][l] = m;
+    __syncthreads();
+    if (w == 0 && i < j.R) {
+      for (int v = 1; v < kSliceWarps; ++v) m = max(m, red[v][l]);
+      atomicMax(&j.maxbits[i], m);
+    }
+  } else {
+    const int64_t i = (int64_t)band * kSliceWarps + w;
+    if (i >= j.R) return;
+    const double* col = j.src + i * j.ld;
+    unsigned long long m = 0;
+#pragma unroll 4
+    for (int64_t k = k_lo + l; k < k_hi; k += 32) m = max(m, abs_bits(col[k]));
 #pragma unroll
-    for (int t = 0; t < kS; ++t) out[t * plane + i * kld + k] = s[t];
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (l == 0) atomicMax(&j.maxbits[i], m);
   }
 }
 
@@ -538,8 +643,11 @@ struct TcFactor {
   uint16_t* SB = nullptr;     // kS x cap
   int* eA = nullptr;          // npad
   int* eB = nullptr;          // npad
+  unsigned long long* maxA = nullptr;  // npad: row maxima of split operands
+  unsigned long long* maxB = nullptr;
   double* T = nullptr;        // half x half
   int num_sms = 1;
+  int64_t launches = 0;       // kernels enqueued so far
 };
 
 namespace {
@@ -550,10 +658,8 @@ int64_t half_of(int64_t npad) { return 64 * ceil_div(npad / 64, 2); }
 // and at least one 128-row panel of the whitening products (128 x npad).
 size_t plane_cap(int64_t npad) {
   const int64_t h = half_of(npad);
-  return std::max((size_t)h * (size_t)round_up(h, OBK), (size_t)OBM * (size_t)npad);
+  return std::max((size_t)h * (size_t)round_up(h, kKAlign), (size_t)OBM * (size_t)npad);
 }
-
-bool g_smem_attr = false;
 
 struct Operand {
   const uint16_t* slices;
@@ -574,41 +680,73 @@ cudaError_t encode(CUtensorMap* map, const Operand& o, int box_rows) {
   cuuint32_t box[3] = {OBK, (cuuint32_t)box_rows, kS};
   cuuint32_t es[3] = {1, 1, 1};
   if (enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(o.slices), dims,
-          strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+          strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return enc_err("slices");
   return cudaSuccess;
 }
 
-// x(i, k) = src[i + k ld] (rows = true) or src[k + i ld] (rows = false).
-cudaError_t slice(const double* src, int64_t ld, int64_t R, int64_t K, bool rows, uint16_t* out,
-                  int* expo, const int* flags, cudaStream_t st) {
-  const int64_t kld = round_up(K, OBK);
-  if (rows)
-    slice_rows_kernel<<<(unsigned)ceil_div(R, 32), 256, 0, st>>>(src, ld, R, K, kld, out, expo,
-                                                                 flags);
-  else
-    slice_cols_kernel<<<(unsigned)ceil_div(R, 8), 256, 0, st>>>(src, ld, R, K, kld, out, expo,
-                                                                flags);
+// Operands of at least this many elements are split along k as well as rows:
+// a row-maxima pass, then the slicing pass, each over (rows x 1024 k) tiles.
+constexpr int64_t kSplitElems = (int64_t)1 << 21;
+constexpr int kSplitSpan = 1024;
+
+SliceJob job(const double* src, int64_t ld, int64_t R, int64_t K, bool rows, uint16_t* out,
+             int* expo, unsigned long long* maxbuf) {
+  SliceJob j;
+  j.src = src;
+  j.ld = ld;
+  j.R = R;
+  j.K = K;
+  j.kld = round_up(K, kKAlign);
+  j.out = out;
+  j.expo = expo;
+  j.rows_mode = rows ? 1 : 0;
+  const bool split = R * j.kld >= kSplitElems;
+  j.maxbits = split ? maxbuf : nullptr;
+  j.kspan = split ? kSplitSpan : (int)j.kld;
+  j.kblocks = split ? (int)ceil_div(j.kld, kSplitSpan) : 1;
+  const int64_t bands = rows ? ceil_div(R, 32) : ceil_div(R, kSliceWarps);
+  j.nblocks = R <= 0 ? 0 : (int)(bands * j.kblocks);
+  return j;
+}
+
+// Slices one or two operands in one launch (b.nblocks may be 0).
+cudaError_t slice2(TcFactor* w, const SliceJob& a, const SliceJob& b, const int* flags,
+                   cudaStream_t st) {
+  const int grid = a.nblocks + b.nblocks;
+  if (grid == 0) return cudaSuccess;
+  if ((a.nblocks && a.maxbits) || (b.nblocks && b.maxbits)) {
+    for (const SliceJob* j : {&a, &b})
+      if (j->nblocks && j->maxbits) {
+        cudaError_t e = cudaMemsetAsync(j->maxbits, 0, (size_t)j->R * 8, st);
+        if (e != cudaSuccess) return e;
+      }
+    rowmax_kernel<<<grid, 32 * kSliceWarps, 0, st>>>(a, b, flags);
+    ++w->launches;
+  }
+  slice_kernel<<<grid, 32 * kSliceWarps, 0, st>>>(a, b, flags);
+  ++w->launches;
   return cudaGetLastError();
 }
 
-// C (M x N, ldc) = alpha * A B^T + beta * C, A = M x K and B = N x K operands
-// already sliced; kmode restricts each tile's K range to the structural nonzeros.
+cudaError_t slice1(TcFactor* w, const SliceJob& a, const int* flags, cudaStream_t st) {
+  SliceJob none = a;
+  none.nblocks = 0;
+  return slice2(w, a, none, flags, st);
+}
+
+template <int BN>
+cudaError_t launch_gemm(TcFactor* w, const Operand& A, const Operand& B, OzParams q,
+                        cudaStream_t st);
+
+// C (M x N, ldc) = (neg ? -1 : 1) A B^T + (beta ? C : 0), A = M x K and B = N x K
+// operands already sliced; kmode restricts each tile's K range to the
+// structural nonzeros.  Products with few 128 x 64 tiles use 128 x 16 tiles.
 cudaError_t gemm(TcFactor* w, const Operand& A, const Operand& B, double* C, int64_t ldc, int M,
-                 int N, int K, int kmode, int koff, double alpha, int beta, bool lower,
+                 int N, int K, int kmode, int koff, bool neg, int beta, bool lower,
                  int64_t diag_off, int* flags, cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  if (!g_smem_attr) {
-    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    if (e != cudaSuccess) return e;
-    g_smem_attr = true;
-  }
-  CUtensorMap ta, tb;
-  cudaError_t e;
-  if ((e = encode(&ta, A, OBM)) != cudaSuccess) return e;
-  if ((e = encode(&tb, B, OBN)) != cudaSuccess) return e;
   OzParams q;
   memset(&q, 0, sizeof(q));
   q.C = C;
@@ -616,20 +754,47 @@ cudaError_t gemm(TcFactor* w, const Operand& A, const Operand& B, double* C, int
   q.eA = A.expo;
   q.eB = B.expo;
   q.diag_off = diag_off;
-  q.alpha = alpha;
   q.M = M;
   q.N = N;
   q.tilesI = (int)ceil_div(M, OBM);
-  q.tilesJ = (int)ceil_div(N, OBN);
   q.Kend = K;
   q.kmode = kmode;
   q.koff = koff;
+  q.neg = neg ? 1 : 0;
   q.beta = beta;
   q.lower = lower ? 1 : 0;
   q.flags = flags;
+  const int64_t tiles64 = (int64_t)q.tilesI * ceil_div(N, 64);
+  if (tiles64 * 4 <= w->num_sms) {
+    q.tilesJ = (int)ceil_div(N, 16);
+    return launch_gemm<16>(w, A, B, q, st);
+  }
+  q.tilesJ = (int)ceil_div(N, 64);
+  return launch_gemm<64>(w, A, B, q, st);
+}
+
+template <int BN>
+cudaError_t launch_gemm(TcFactor* w, const Operand& A, const Operand& B, OzParams q,
+                        cudaStream_t st) {
+  using Sh = Shape<BN>;
+  static bool attr_done[64] = {};  // per instantiation and device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel<BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Sh::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) attr_done[dev] = true;
+  }
+  CUtensorMap ta, tb;
+  cudaError_t e;
+  if ((e = encode(&ta, A, OBM)) != cudaSuccess) return e;
+  if ((e = encode(&tb, B, BN)) != cudaSuccess) return e;
   const int tiles = q.tilesI * q.tilesJ;
   const int grid = std::max(1, std::min(w->num_sms, tiles));
-  oz_gemm_kernel<<<grid, kThreads, kSmemBytes, st>>>(ta, tb, q);
+  oz_gemm_kernel<BN><<<grid, kThreads, Sh::kSmemBytes, st>>>(ta, tb, q);
+  ++w->launches;
   return cudaGetLastError();
 }
 
@@ -643,6 +808,7 @@ cudaError_t rec(TcFactor* w, double* A, double* Z, int64_t ld, int64_t r0, int64
                 cudaStream_t st) {
   if (n == 64) {
     launch_potrf_diag64(A, Z, ld, r0, flags, st);
+    ++w->launches;
     return cudaGetLastError();
   }
   const int64_t n1 = 64 * ((n / 64) / 2), n2 = n - n1;
@@ -652,43 +818,36 @@ cudaError_t rec(TcFactor* w, double* A, double* Z, int64_t ld, int64_t r0, int64
   double* Z11 = Z + r0 + r0 * ld;
   double* Z21 = Z + (r0 + n1) + r0 * ld;
   double* Z22 = Z + (r0 + n1) + (r0 + n1) * ld;
-  const Operand SA1{w->SA, w->eA, n2, round_up(n1, OBK)};
-  const Operand SB1{w->SB, w->eB, n1, round_up(n1, OBK)};
-  // L21 = A21 Z11^T (Z11 lower: column block J needs k < (J+1) 64)
-  TC_TRY(slice(A21, ld, n2, n1, true, w->SA, w->eA, flags, st));
-  TC_TRY(slice(Z11, ld, n1, n1, true, w->SB, w->eB, flags, st));
-  TC_TRY(gemm(w, SA1, SB1, A21, ld, (int)n2, (int)n1, (int)n1, kKLeJ, 0, 1.0, 0, false, 0, flags,
-              st));
-  // A22 -= L21 L21^T (lower triangle)
-  TC_TRY(slice(A21, ld, n2, n1, true, w->SA, w->eA, flags, st));
-  const Operand SA1b{w->SA, w->eA, n2, round_up(n1, OBK)};
-  TC_TRY(gemm(w, SA1, SA1b, A22, ld, (int)n2, (int)n2, (int)n1, kKFull, 0, -1.0, 1, true, 0,
+  const Operand SA1{w->SA, w->eA, n2, round_up(n1, kKAlign)};
+  const Operand SB1{w->SB, w->eB, n1, round_up(n1, kKAlign)};
+  // L21 = A21 Z11^T (Z11 lower: column block J needs k < (J+1) BN)
+  TC_TRY(slice2(w, job(A21, ld, n2, n1, true, w->SA, w->eA, w->maxA),
+                job(Z11, ld, n1, n1, true, w->SB, w->eB, w->maxB), flags, st));
+  TC_TRY(gemm(w, SA1, SB1, A21, ld, (int)n2, (int)n1, (int)n1, kKLeJ, 0, false, 0, false, 0,
               flags, st));
+  // A22 -= L21 L21^T (lower triangle)
+  TC_TRY(slice1(w, job(A21, ld, n2, n1, true, w->SA, w->eA, w->maxA), flags, st));
+  TC_TRY(gemm(w, SA1, SA1, A22, ld, (int)n2, (int)n2, (int)n1, kKFull, 0, true, 1, true, 0, flags,
+              st));
   TC_TRY(rec(w, A, Z, ld, r0 + n1, n2, flags, st));
   // T = L21 Z11 (Z11 lower: column j needs k >= j)
-  TC_TRY(slice(A21, ld, n2, n1, true, w->SA, w->eA, flags, st));
-  TC_TRY(slice(Z11, ld, n1, n1, false, w->SB, w->eB, flags, st));
-  TC_TRY(gemm(w, SA1, SB1, w->T, n2, (int)n2, (int)n1, (int)n1, kKGeJ, 0, 1.0, 0, false, 0, flags,
-              st));
+  TC_TRY(slice2(w, job(A21, ld, n2, n1, true, w->SA, w->eA, w->maxA),
+                job(Z11, ld, n1, n1, false, w->SB, w->eB, w->maxB), flags, st));
+  TC_TRY(gemm(w, SA1, SB1, w->T, n2, (int)n2, (int)n1, (int)n1, kKGeJ, 0, false, 0, false, 0,
+              flags, st));
   // Z21 = -Z22 T (Z22 lower: row block I needs k < (I+1) 128)
-  const Operand SA2{w->SA, w->eA, n2, round_up(n2, OBK)};
-  const Operand SB2{w->SB, w->eB, n1, round_up(n2, OBK)};
-  TC_TRY(slice(Z22, ld, n2, n2, true, w->SA, w->eA, flags, st));
-  TC_TRY(slice(w->T, n2, n1, n2, false, w->SB, w->eB, flags, st));
-  TC_TRY(gemm(w, SA2, SB2, Z21, ld, (int)n2, (int)n1, (int)n2, kKLeI, 0, -1.0, 0, false, 0, flags,
+  const Operand SA2{w->SA, w->eA, n2, round_up(n2, kKAlign)};
+  const Operand SB2{w->SB, w->eB, n1, round_up(n2, kKAlign)};
+  TC_TRY(slice2(w, job(Z22, ld, n2, n2, true, w->SA, w->eA, w->maxA),
+                job(w->T, n2, n1, n2, false, w->SB, w->eB, w->maxB), flags, st));
+  TC_TRY(gemm(w, SA2, SB2, Z21, ld, (int)n2, (int)n1, (int)n2, kKLeI, 0, true, 0, false, 0, flags,
               st));
   return cudaSuccess;
 }
 
-int64_t rec_launches(int64_t n) {
-  if (n == 64) return 1;
-  const int64_t n1 = 64 * ((n / 64) / 2), n2 = n - n1;
-  return rec_launches(n1) + rec_launches(n2) + 11;
-}
-
 // Rows per panel so that rows x K fits one slice plane.
 int64_t panel_rows(const TcFactor* w, int64_t K) {
-  int64_t P = (int64_t)(w->cap / (size_t)round_up(K, OBK));
+  int64_t P = (int64_t)(w->cap / (size_t)round_up(K, kKAlign));
   P = (P / OBM) * OBM;
   return std::max<int64_t>(P, OBM);
 }
@@ -697,7 +856,7 @@ int64_t panel_rows(const TcFactor* w, int64_t K) {
 
 size_t tc_factor_bytes(int64_t npad) {
   const int64_t h = half_of(npad);
-  return 2 * (size_t)kS * plane_cap(npad) * 2 + 2 * (size_t)npad * 4 + (size_t)h * h * 8;
+  return 2 * (size_t)kS * plane_cap(npad) * 2 + 2 * (size_t)npad * (4 + 8) + (size_t)h * h * 8;
 }
 
 const char* tc_factor_last_error() { return g_err.c_str(); }
@@ -708,6 +867,8 @@ void tc_factor_free(TcFactor* w) {
   cudaFree(w->SB);
   cudaFree(w->eA);
   cudaFree(w->eB);
+  cudaFree(w->maxA);
+  cudaFree(w->maxB);
   cudaFree(w->T);
   delete w;
 }
@@ -729,6 +890,8 @@ gls_status_t tc_factor_create(TcFactor** out, int64_t npad) {
       cudaMalloc(&w->SB, (size_t)kS * w->cap * 2) != cudaSuccess ||
       cudaMalloc(&w->eA, (size_t)npad * 4) != cudaSuccess ||
       cudaMalloc(&w->eB, (size_t)npad * 4) != cudaSuccess ||
+      cudaMalloc(&w->maxA, (size_t)npad * 8) != cudaSuccess ||
+      cudaMalloc(&w->maxB, (size_t)npad * 8) != cudaSuccess ||
       cudaMalloc(&w->T, (size_t)w->half * w->half * 8) != cudaSuccess) {
     cudaGetLastError();
     tc_factor_free(w);
@@ -739,7 +902,7 @@ gls_status_t tc_factor_create(TcFactor** out, int64_t npad) {
   return GLS_OK;
 }
 
-int64_t tc_potrf_trtri_launches(int64_t npad) { return rec_launches(npad); }
+int64_t tc_launches(const TcFactor* w) { return w->launches; }
 
 cudaError_t tc_potrf_trtri(TcFactor* w, double* A, double* Z, int64_t ld, int64_t npad, int* flags,
                            cudaStream_t st) {
@@ -758,11 +921,11 @@ cudaError_t tc_lower_times(TcFactor* w, const double* Z, int64_t ldz, int64_t np
   const int64_t P = panel_rows(w, npad);
   for (int64_t i0 = 0; i0 < npad; i0 += P) {
     const int64_t rows = std::min(P, npad - i0), K = i0 + rows;
-    TC_TRY(slice(Z + i0, ldz, rows, K, true, w->SA, w->eA, flags, st));
-    TC_TRY(slice(rhs, ldr, ncols, K, false, w->SB, w->eB, flags, st));
-    const Operand a{w->SA, w->eA, rows, round_up(K, OBK)};
-    const Operand b{w->SB, w->eB, ncols, round_up(K, OBK)};
-    TC_TRY(gemm(w, a, b, out + i0, ldo, (int)rows, ncols, (int)K, kKLeI, (int)i0, 1.0, 0, false,
+    TC_TRY(slice2(w, job(Z + i0, ldz, rows, K, true, w->SA, w->eA, w->maxA),
+                  job(rhs, ldr, ncols, K, false, w->SB, w->eB, w->maxB), flags, st));
+    const Operand a{w->SA, w->eA, rows, round_up(K, kKAlign)};
+    const Operand b{w->SB, w->eB, ncols, round_up(K, kKAlign)};
+    TC_TRY(gemm(w, a, b, out + i0, ldo, (int)rows, ncols, (int)K, kKLeI, (int)i0, false, 0, false,
                 0, flags, st));
   }
   return cudaSuccess;
@@ -775,11 +938,11 @@ cudaError_t tc_lower_t_times(TcFactor* w, const double* Z, int64_t ldz, int64_t 
   const int64_t P = panel_rows(w, npad);
   for (int64_t c0 = 0; c0 < npad; c0 += P) {
     const int64_t rows = std::min(P, npad - c0), K = npad - c0;
-    TC_TRY(slice(Z + c0 + c0 * ldz, ldz, rows, K, false, w->SA, w->eA, flags, st));
-    TC_TRY(slice(rhs + c0, ldr, ncols, K, false, w->SB, w->eB, flags, st));
-    const Operand a{w->SA, w->eA, rows, round_up(K, OBK)};
-    const Operand b{w->SB, w->eB, ncols, round_up(K, OBK)};
-    TC_TRY(gemm(w, a, b, out + c0, ldo, (int)rows, ncols, (int)K, kKGeI, 0, 1.0, 0, false, 0,
+    TC_TRY(slice2(w, job(Z + c0 + c0 * ldz, ldz, rows, K, false, w->SA, w->eA, w->maxA),
+                  job(rhs + c0, ldr, ncols, K, false, w->SB, w->eB, w->maxB), flags, st));
+    const Operand a{w->SA, w->eA, rows, round_up(K, kKAlign)};
+    const Operand b{w->SB, w->eB, ncols, round_up(K, kKAlign)};
+    TC_TRY(gemm(w, a, b, out + c0, ldo, (int)rows, ncols, (int)K, kKGeI, 0, false, 0, false, 0,
                 flags, st));
   }
   return cudaSuccess;

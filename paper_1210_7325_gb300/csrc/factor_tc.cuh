@@ -35,8 +35,8 @@ cudaError_t tc_lower_t_times(TcFactor* w, const double* Z, int64_t ldz, int64_t 
                              const double* rhs, int64_t ldr, int ncols, double* out, int64_t ldo,
                              int* flags, cudaStream_t st);
 
-// Kernel launches one tc_potrf_trtri call enqueues (for the plan's launch count).
-int64_t tc_potrf_trtri_launches(int64_t npad);
+// Kernels enqueued through this workspace so far (for the plan's launch count).
+int64_t tc_launches(const TcFactor* w);
 
 // Launcher of the binary64 64 x 64 diagonal-block Cholesky + inverse (factor_fp64.cu).
 void launch_potrf_diag64(double* A, double* Z, int64_t ld, int64_t k0, int* flags,

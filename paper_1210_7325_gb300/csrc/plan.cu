@@ -520,10 +520,11 @@ gls_status_t gls_factor(gls_plan_t pl, const double* M, int64_t ldm, const doubl
   const int p = pl->p;
   cudaStream_t st = pl->stream;
   Timed phase(pl, &pl->t_factor);
+  const int64_t tc_before = pl->tc ? gls::tc_launches(pl->tcf) : 0;
   GLS_CUDA(cudaMemsetAsync(pl->flags, 0, sizeof(int) * gls::kFlagCount, st));
   if (M) {
     const int64_t N = npad / gls::kT;
-    pl->launches += 2 + (pl->tc ? gls::tc_potrf_trtri_launches(npad) : N + 4 * (N - 1));
+    pl->launches += 2 + (pl->tc ? 0 : N + 4 * (N - 1));
     pl->has_factor = false;
     GLS_CUDA(cudaMemcpy2DAsync(pl->A, npad * sizeof(double), M, ldm * sizeof(double),
                                n * sizeof(double), n, cudaMemcpyDefault, st));
@@ -587,9 +588,10 @@ gls_status_t gls_factor(gls_plan_t pl, const double* M, int64_t ldm, const doubl
     }
     GLS_TRY(gls::mixed_prepare(pl->mixed, pl->Z, npad, pl->Wt, npad, M != nullptr, W != nullptr,
                                st));
-    pl->launches += (M != nullptr) ? 3 : 2;
+    pl->launches += (M != nullptr ? 1 : 0) + (W != nullptr ? 0 : 1) + 1;
   }
   phase.finish();
+  if (pl->tc) pl->launches += gls::tc_launches(pl->tcf) - tc_before;
   if (pl->precision != GLS_PREC_FP64) GLS_TRY(check_flags(pl, hf));
   pl->factored = true;
   return GLS_OK;
