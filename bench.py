@@ -54,6 +54,11 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "n10000_p20_m1000000_bf16"
 
+# DRAM bytes (read + write) of one launch of the mixed blocked-solve kernel, from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the current
+# kernel at that launch size: (precision, n, SNPs per launch) -> bytes.
+TRSM_TRAFFIC = {("bf16", 10000, 65536): 57.37e9 + 0.586e9}
+
 # Batched uneven scans: each scan its own kinship, h ~ U(0.1, 0.9); one persistent
 # launch per round serves one block of every scan.
 BATCH_WORKLOADS = {
@@ -713,7 +718,8 @@ def main():
         achieved = flops / trsm_avg_s / 1e12
         peak = peaks["bf16_tflops_sustained"]
         line["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak,
-                            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                            "unit": "TFLOP/s", "frac": achieved / peak,
+                            "traffic": TRSM_TRAFFIC.get((wl["precision"], n, wl["block"])),
                             "peak_source": f"{peak_src} bf16_tflops_sustained",
                             "flops_per_launch": flops,
                             "per_unit": f"{S} slices x n^2 tensor flops per SNP"}

@@ -51,18 +51,32 @@ __global__ void identity_kernel(double* __restrict__ Z, int64_t ldz, int64_t npa
   }
 }
 
+// 1/sqrt(d): the FP32 estimate refined by two binary64 Newton steps.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (d > 1e-30 && d < 1e30) {
+    const double h = 0.5 * d;
+    double r = (double)rsqrtf((float)d);
+    r = r * fma(-h * r, r, 1.5);
+    r = r * fma(-h * r, r, 1.5);
+    return r;
+  }
+  return 1.0 / sqrt(d);
+}
+
 // Cholesky of the 64 x 64 diagonal block at (k0, k0) and its triangular
 // inverse.  One CTA.  The block already carries every update of the earlier
 // block columns.  A pivot <= 0 records its 1-based global index in
 // flags[kFlagPotrf] (first failure wins) and stops.
 //
 // Right-looking over the 64 columns, the Cholesky and the inverse in the same
-// sweep: at column j warp 0 forms L_jj = sqrt(d_j), scales column j of L and
-// row j of W = L^{-1} by 1/L_jj; then all threads apply the rank-1 updates
-// S_il -= L_ij L_lj (j < l <= i) and W_ic -= L_ij W_jc (c <= j, i > j),
-// numbered densely over the threads.  Binary64 throughput per SM is low on this
-// part, so the pivot is one reciprocal square root (FP32 estimate, two Newton
-// steps) and no binary64 instruction runs with idle lanes.
+// sweep.  At column j warp 0 scales column j of L and row j of W = L^{-1} by
+// r_j = 1/L_jj; then warps 1-7 apply the rank-1 updates S_il -= L_ij L_lj
+// (j < l <= i) and W_ic -= L_ij W_jc (c <= j < i), numbered densely so that
+// every lane of every binary64 instruction does useful work, while thread 0
+// already forms the next pivot d_{j+1} = S_{j+1,j+1} - L_{j+1,j}^2 and r_{j+1}.
+// Dependent binary64 operations take about 64 cycles each on this part, so the
+// pivot's chain (about 700 cycles) runs beside the column's update instead of
+// before it.
 __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ A,
                                                          double* __restrict__ Z, int64_t ld,
                                                          int64_t k0, int* flags) {
@@ -70,6 +84,7 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ A,
   double(*S)[kLd] = reinterpret_cast<double(*)[kLd]>(sm);            // S[i][l], lower
   double(*W)[kLd] = reinterpret_cast<double(*)[kLd]>(sm + kT * kLd);  // W[i][c], lower
   __shared__ int fail;
+  __shared__ double piv_d, piv_r;  // d_j and 1/sqrt(d_j) of the column to scale next
   const int tid = threadIdx.x;
   if (*(volatile int*)&flags[kFlagPotrf] != 0) return;
   for (int idx = tid; idx < kT * kT; idx += blockDim.x) {
@@ -79,45 +94,50 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ A,
   }
   if (tid == 0) fail = 0;
   __syncthreads();
+  if (tid == 0) {
+    const double d = S[0][0];
+    if (!(d > 0.0)) {
+      fail = 1;
+    } else {
+      piv_d = d;
+      piv_r = rsqrt_newton(d);
+    }
+  }
+  __syncthreads();
   const int lane = tid % 32;
+  constexpr int kUpd = 256 - 32;  // threads of warps 1-7
   for (int j = 0; j < kT; ++j) {
+    if (fail) break;
+    double dd = 0.0;  // thread 0: S_{j+1,j+1} before column j's update
     if (tid < 32) {
-      const double d = S[j][j];
-      if (!(d > 0.0)) {
-        if (lane == 0) fail = j + 1;
-      } else {
-        // r = 1/sqrt(d): the FP32 estimate refined by two binary64 Newton steps
-        // (a short dependent chain; binary64 latency on this part is long)
-        double r;
-        if (d > 1e-30 && d < 1e30) {
-          const double h = 0.5 * d;
-          r = (double)rsqrtf((float)d);
-          r = r * fma(-h * r, r, 1.5);
-          r = r * fma(-h * r, r, 1.5);
-        } else {
-          r = 1.0 / sqrt(d);
-        }
-        const double ajj = d * r;
-        for (int i = j + 1 + lane; i < kT; i += 32) S[i][j] *= r;
-        for (int c = lane; c <= j; c += 32) W[j][c] *= r;
-        __syncwarp();  // every lane has read d before it is overwritten
-        if (lane == 0) S[j][j] = ajj;
+      const double r = piv_r;
+      for (int i = j + 1 + lane; i < kT; i += 32) S[i][j] *= r;
+      for (int c = lane; c <= j; c += 32) W[j][c] *= r;
+      if (lane == 0) {
+        S[j][j] = piv_d * r;
+        if (j + 1 < kT) dd = S[j + 1][j + 1];
       }
     }
     __syncthreads();
-    if (fail) break;
-    {
-      // The column's updates, S_il (j < l <= i) then W_ic (c <= j < i), are
-      // numbered densely over all threads so that every lane of every binary64
-      // instruction does useful work; four per thread are loaded before any
-      // store so their FMAs overlap.
+    if (tid == 0) {
+      if (j + 1 < kT) {
+        const double l = S[j + 1][j];
+        const double d = fma(-l, l, dd);
+        if (!(d > 0.0)) {
+          fail = j + 2;
+        } else {
+          piv_d = d;
+          piv_r = rsqrt_newton(d);
+        }
+      }
+    } else if (tid >= 32) {
       const int m = kT - 1 - j, ns = m * (m + 1) / 2, total = ns + m * (j + 1);
-      for (int q0 = tid; q0 < total; q0 += 4 * 256) {
+      for (int q0 = tid - 32; q0 < total; q0 += 4 * kUpd) {
         double av[4], bv[4], lv[4];
         double* dst[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int q = q0 + u * 256;
+          const int q = q0 + u * kUpd;
           dst[u] = nullptr;
           if (q < total) {
             int i;
