@@ -234,6 +234,18 @@ def run_gpu(args, wl, rank, world, torch, dist):
             e2e_step()
         te = time.perf_counter() - t0
         res["e2e_time"] = te
+        # context for the end-to-end figure: this box's pinned host -> device copy rate
+        probe = torch.empty((min(m, kmax), n), dtype=torch.int8, device=dev)
+        best = float("inf")
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            probe.copy_(XRh[:probe.shape[0]], non_blocking=True)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        res["h2d_gbps"] = probe.numel() / best / 1e9
+        del probe
         res["e2e_h2d"] = n * n * 8 + n * (p - 1) * 8 + n * 8 + n * m
         res["e2e_d2h"] = p * m * 8 + 4 * m
     plan.close()
@@ -725,7 +737,8 @@ def main():
                             "per_unit": f"{S} slices x n^2 tensor flops per SNP"}
     if e2e_max:
         line["e2e"] = {"value": world * m * K / e2e_max, "unit": UNIT,
-                       "h2d_bytes_per_step": res["e2e_h2d"], "d2h_bytes_per_step": res["e2e_d2h"]}
+                       "h2d_bytes_per_step": res["e2e_h2d"], "d2h_bytes_per_step": res["e2e_d2h"],
+                       "h2d_gbps_measured": res.get("h2d_gbps")}
     if not args.skip_fp64 and wl["precision"] != "fp64":
         try:
             line["fp64"] = fp64_sample(wl, torch)

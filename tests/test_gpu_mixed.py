@@ -126,33 +126,38 @@ def test_stream_mixed():
 
 
 def test_full_size_sampled():
-    """n = 10^4, p = 20, one block of 16384 SNPs, BF16 and FP16 splits, 48
-    sampled SNPs checked against the oracle; plus a planted exact solution on
-    one SNP."""
+    """n = 10^4, p = 20 in the bench's launch configuration: blocks of 65536 SNPs
+    plus the ragged last block of the m = 10^6 workload (16960 SNPs); BF16 and
+    FP16 splits; 48 sampled SNPs checked against the oracle; plus a planted
+    exact solution on one SNP."""
     import torch
-    n, p, k = 10000, 20, 16384
+    n, p, kmax, tail = 10000, 20, 65536, 1_000_000 - 15 * 65536
+    k = kmax + tail
     seed = synth.BASE_SEED + 2
     M = synth.kinship_M(n, 0.5, seed, device="cuda:0")
     XL = synth.covariates(n, p, seed)
     y = synth.phenotype(n, seed)
     XRt = synth.genotypes_torch(n, k, seed, device="cuda:0")  # (k, n)
     beta = np.linspace(-1.0, 1.0, p)
-    planted = 12345
+    planted = kmax + 12345  # in the ragged block
     y_pl = XL @ beta[:-1] + XRt[planted].double().cpu().numpy() * beta[-1]
     dev = "cuda:0"
     Md = torch.from_numpy(np.ascontiguousarray(M.T)).to(dev).t()
     XLd = torch.from_numpy(np.ascontiguousarray(XL.T)).to(dev).t()
     out = {}
     for tag, yy in (("y", y), ("planted", y_pl), ("fp16", y)):
-        with gls.Plan(n, p, k, precision="fp16" if tag == "fp16" else "bf16") as plan:
+        with gls.Plan(n, p, kmax, precision="fp16" if tag == "fp16" else "bf16") as plan:
             plan.factor(Md, XLd, torch.from_numpy(yy).to(dev))
             B = torch.empty((k, p), dtype=torch.float64, device=dev)
             st = torch.empty(k, dtype=torch.int32, device=dev)
-            plan.solve_block(XRt.t(), B.t(), st, k=k)
+            for s0 in (0, kmax):
+                kb = min(kmax, k - s0)
+                plan.solve_block(XRt[s0:s0 + kb].t(), B[s0:s0 + kb].t(), st[s0:s0 + kb], k=kb)
             plan.synchronize()
             out[tag] = (B.cpu().numpy().T, st.cpu().numpy())
     assert np.abs(out["planted"][0][:, planted] - beta).max() <= 1e-6
-    idx = np.unique(np.concatenate([np.arange(16), np.linspace(16, k - 1, 32).astype(np.int64)]))
+    idx = np.unique(np.concatenate([np.arange(16), np.linspace(16, k - 1, 32).astype(np.int64),
+                                    [kmax - 1, kmax, k - 1]]))
     XR_host = np.asfortranarray(XRt.cpu().numpy().T)
     Bref, sref, info = oracle.gls_sampled(M, XL, y, XR_host, idx, tau=oracle.TAU_MIXED,
                                           nthreads=oracle.default_threads())
