@@ -98,6 +98,10 @@ class Server:
         self.rejected: List[tuple] = []   # (rid, reason): larger than the whole budget
         self.peak_used = 0.0
         self._lock = threading.Lock()
+        # wall-time breakdown of the serving loop (seconds) and factor wall time
+        self.breakdown = {"admit_s": 0.0, "rounds_s": 0.0, "idle_s": 0.0, "rounds": 0,
+                          "round_requests": 0, "factor_s": 0.0, "factors": 0,
+                          "plan_create_s": 0.0, "evict_s": 0.0, "inputs_s": 0.0}
 
     # ------------------------------------------------------------ memory
     def _plan_bytes(self, n, p):
@@ -111,8 +115,10 @@ class Server:
         for s in idle:
             if self.used + need <= self.budget:
                 break
+            t = time.perf_counter()
             self._drop_batches_with(s.plan)
             s.plan.close()
+            self.breakdown["evict_s"] += time.perf_counter() - t
             self.used -= s.nbytes
             del self.slots[s.key]
 
@@ -138,12 +144,16 @@ class Server:
             if self.used + need > self.budget:
                 return None
         reuse = slot is not None
+        t = time.perf_counter()
         inputs = self.make_inputs(req, self.torch, reuse)
         # the plan's stream reads these tensors: let their producers finish first
         if str(self.device).startswith("cuda"):
             self.torch.cuda.current_stream().synchronize()
+        self.breakdown["inputs_s"] += time.perf_counter() - t
         if not reuse:
+            t = time.perf_counter()
             plan = gls.Plan(req.n, req.p, self.block, precision=self.precision)
+            self.breakdown["plan_create_s"] += time.perf_counter() - t
             slot = _Slot(plan, req.mkey, req.n, req.p, self._plan_bytes(req.n, req.p))
             self.slots[req.mkey] = slot
             self.used += slot.nbytes
@@ -155,10 +165,18 @@ class Server:
         st = torch.empty(req.m, dtype=torch.int32, device=self.device)
         act = _Active(req, slot, inputs, B, st, now)
         if reuse:
-            act.factored = self.pool.submit(slot.plan.factor, None, None, inputs.y)
+            act.factored = self.pool.submit(self._timed_factor, slot.plan, None, None, inputs.y)
         else:
-            act.factored = self.pool.submit(slot.plan.factor, inputs.M, inputs.XL, inputs.y)
+            act.factored = self.pool.submit(self._timed_factor, slot.plan, inputs.M, inputs.XL,
+                                            inputs.y)
         return act
+
+    def _timed_factor(self, plan, M, XL, y):
+        t = time.perf_counter()
+        plan.factor(M, XL, y)
+        with self._lock:
+            self.breakdown["factor_s"] += time.perf_counter() - t
+            self.breakdown["factors"] += 1
 
     # ------------------------------------------------------------ solving
     def _batch_for(self, acts):
@@ -219,6 +237,7 @@ class Server:
                 waiting.append(pending.popleft())
             # admission in arrival order; a blocked request does not block others
             still = collections.deque()
+            t_adm = time.perf_counter()
             while waiting:
                 req = waiting.popleft()
                 if len(active) >= MAX_BATCH:
@@ -234,17 +253,24 @@ class Server:
                 else:
                     active.append(act)
             waiting = still
+            self.breakdown["admit_s"] += time.perf_counter() - t_adm
             self.queue_depth.append((now, len(waiting), len(active)))
             ready = [a for a in active if a.factored.done()]
             for a in ready:
                 a.factored.result()  # re-raises a factor error
             ready = [a for a in ready if a.next < a.req.m]
             if ready:
+                t_r = time.perf_counter()
                 self._round(ready[:MAX_BATCH])
+                self.breakdown["rounds_s"] += time.perf_counter() - t_r
+                self.breakdown["rounds"] += 1
+                self.breakdown["round_requests"] += min(len(ready), MAX_BATCH)
             else:
                 # nothing to solve yet: wait for a factor or the next arrival
                 nxt = pending[0].arrival if pending else now + 0.01
+                t_i = time.perf_counter()
                 time.sleep(max(0.0, min(0.002, nxt - now)))
+                self.breakdown["idle_s"] += time.perf_counter() - t_i
             done_now = time.perf_counter() - t0
             for a in [a for a in active if a.factored.done() and a.next >= a.req.m]:
                 self._finish(a, done_now)
@@ -255,13 +281,15 @@ class Server:
         return self.results
 
     def close(self):
+        # a run cut off by its time cap can leave factors running on the
+        # workers: they finish before any plan is destroyed
+        self.pool.shutdown(wait=True)
         for b in self.batches.values():
             b.close()
         self.batches.clear()
         for s in self.slots.values():
             s.plan.close()
         self.slots.clear()
-        self.pool.shutdown(wait=True)
 
 
 def poisson_requests(count, rate, seed, n_range, p_range, m_range, reuse_frac=0.3, h=0.5):

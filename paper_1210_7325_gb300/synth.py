@@ -91,9 +91,9 @@ def kinship_M_torch(n: int, h: float, seed: int, n_markers: int = 5000, device="
     f = torch.rand(n_markers, generator=gen, device=dev) * 0.45 + 0.05
 
     def draw(fcols):
-        a = torch.rand((n, fcols.numel()), generator=gen, device=dev) < fcols
-        b = torch.rand((n, fcols.numel()), generator=gen, device=dev) < fcols
-        return a.float() + b.float()
+        # Binomial(2, f) from one uniform: [u >= (1-f)^2] + [u >= 1 - f^2]
+        u = torch.rand((n, fcols.numel()), generator=gen, device=dev)
+        return (u >= (1.0 - fcols) * (1.0 - fcols)).float() + (u >= 1.0 - fcols * fcols).float()
 
     G = draw(f)
     for _ in range(10000):
@@ -148,7 +148,9 @@ def genotypes_np(n: int, m: int, seed: int) -> np.ndarray:
 def genotypes_torch(n: int, m: int, seed: int, device="cpu", chunk: int = 8192, out=None):
     """X_R as a torch int8 tensor of shape (m, n) (row i = SNP i, i.e. the
     column-major n x m matrix), drawn on ``device`` in chunks of SNPs.
-    Binomial(2, f) is drawn as the sum of two Bernoulli(f) draws."""
+    Binomial(2, f) is drawn from one uniform u per genotype by its inverse
+    distribution function: x = [u >= (1-f)^2] + [u >= 1 - f^2], so that
+    P(0) = (1-f)^2, P(1) = 2 f (1-f) and P(2) = f^2."""
     import torch
     dev = torch.device(device)
     if n < 2:  # one sample: Phi = [1]
@@ -160,10 +162,9 @@ def genotypes_torch(n: int, m: int, seed: int, device="cpu", chunk: int = 8192, 
     for s in range(0, m, chunk):
         c = min(chunk, m - s)
         f = torch.rand((c, 1), generator=gen, device=dev, dtype=torch.float32) * 0.45 + 0.05
-        u0 = torch.rand((c, n), generator=gen, device=dev, dtype=torch.float32)
-        x = (u0 < f).to(torch.int8)
-        u0 = torch.rand((c, n), generator=gen, device=dev, dtype=torch.float32, out=u0)
-        x += (u0 < f).to(torch.int8)
+        u = torch.rand((c, n), generator=gen, device=dev, dtype=torch.float32)
+        x = (u >= (1.0 - f) * (1.0 - f)).to(torch.int8)
+        x += u >= 1.0 - f * f
         out[s:s + c].copy_(x)
     return out
 
