@@ -599,6 +599,7 @@ def run_serve_workload(args, sw, torch):
                    "block_snps": sw["block"], "time_cap_s": cap, "parallelism": "replicas1"},
         "latency": {k: v for k, v in summ.items() if k.endswith("_s")},
         "completed": summ.get("completed", 0), "reused_factors": summ.get("reused", 0),
+        "loop_breakdown": srv.breakdown,
         "queue_depth_max": max(depth) if depth else 0,
         "queue_depth_last": depth[-1] if depth else 0,
         "wall_s": wall,
@@ -611,6 +612,22 @@ def config_for(wl, args):
             "precision": wl["precision"], "block_snps": wl["block"],
             "l2": "inputs larger than L2 (int8 genotypes n*m bytes)",
             "parallelism": f"replicas{args.gpus}"}
+
+
+# ----------------------------------------------------------------------------- ranks
+def max_over_ranks(t_local, e2e_local, dist, torch, device):
+    """The slowest rank's timed-region and end-to-end times (replicas run in
+    parallel, so the job takes as long as its slowest replica)."""
+    if not dist:
+        return t_local, e2e_local
+    tt = torch.tensor([t_local, e2e_local or 0.0], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt[0]), (float(tt[1]) or None)
+
+
+def whole_job_rate(world, m, steps, t):
+    """Solves/s of the whole job: every rank solves its own m SNPs per step."""
+    return world * m * steps / t
 
 
 # ----------------------------------------------------------------------------- main
@@ -680,13 +697,7 @@ def main():
         dist.barrier()
 
     res = run_gpu(args, wl, rank, world, torch, dist)
-    t_local = res["time"]
-    t_max = t_local
-    e2e_max = res.get("e2e_time")
-    if dist:
-        tt = torch.tensor([t_local, e2e_max or 0.0], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max, e2e_max = float(tt[0]), float(tt[1]) or None
+    t_max, e2e_max = max_over_ranks(res["time"], res.get("e2e_time"), dist, torch, "cuda")
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -695,7 +706,7 @@ def main():
     peaks, peak_src = load_peaks()
     n, p, m = wl["n"], wl["p"], wl["m"]
     K = args.steps
-    value = world * m * K / t_max
+    value = whole_job_rate(world, m, K, t_max)
     s = res["stats"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -736,7 +747,7 @@ def main():
                             "flops_per_launch": flops,
                             "per_unit": f"{S} slices x n^2 tensor flops per SNP"}
     if e2e_max:
-        line["e2e"] = {"value": world * m * K / e2e_max, "unit": UNIT,
+        line["e2e"] = {"value": whole_job_rate(world, m, K, e2e_max), "unit": UNIT,
                        "h2d_bytes_per_step": res["e2e_h2d"], "d2h_bytes_per_step": res["e2e_d2h"],
                        "h2d_gbps_measured": res.get("h2d_gbps")}
     if not args.skip_fp64 and wl["precision"] != "fp64":

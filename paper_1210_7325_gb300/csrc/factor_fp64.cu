@@ -85,6 +85,9 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ A,
   double(*W)[kLd] = reinterpret_cast<double(*)[kLd]>(sm + kT * kLd);  // W[i][c], lower
   __shared__ int fail;
   __shared__ double piv_d, piv_r;  // d_j and 1/sqrt(d_j) of the column to scale next
+  // tri[q] = (a << 8) | b for the q-th entry (a, b), b <= a, of a lower triangle
+  // numbered row by row; the trailing triangle of every column is a prefix
+  __shared__ uint16_t tri[(kT - 1) * kT / 2];
   const int tid = threadIdx.x;
   if (*(volatile int*)&flags[kFlagPotrf] != 0) return;
   for (int idx = tid; idx < kT * kT; idx += blockDim.x) {
@@ -92,6 +95,8 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ A,
     S[i][l] = (i >= l) ? A[(k0 + i) + (k0 + l) * ld] : 0.0;
     W[i][l] = (i == l) ? 1.0 : 0.0;
   }
+  for (int a = tid; a < kT - 1; a += blockDim.x)
+    for (int b = 0; b <= a; ++b) tri[a * (a + 1) / 2 + b] = (uint16_t)((a << 8) | b);
   if (tid == 0) fail = 0;
   __syncthreads();
   if (tid == 0) {
@@ -132,6 +137,7 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ A,
       }
     } else if (tid >= 32) {
       const int m = kT - 1 - j, ns = m * (m + 1) / 2, total = ns + m * (j + 1);
+      const float rj = 1.0f / (float)(j + 1);
       for (int q0 = tid - 32; q0 < total; q0 += 4 * kUpd) {
         double av[4], bv[4], lv[4];
         double* dst[4];
@@ -142,15 +148,15 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ A,
           if (q < total) {
             int i;
             if (q < ns) {
-              int ip = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
-              while ((ip + 1) * (ip + 2) / 2 <= q) ++ip;
-              while (ip * (ip + 1) / 2 > q) --ip;
-              const int l = j + 1 + (q - ip * (ip + 1) / 2);
-              i = j + 1 + ip;
+              const int e = tri[q];
+              const int l = j + 1 + (e & 0xFF);
+              i = j + 1 + (e >> 8);
               dst[u] = &S[i][l];
               bv[u] = S[l][j];
             } else {
-              const int r = q - ns, ip = r / (j + 1), c = r - ip * (j + 1);
+              // (r + 1/2) / (j + 1) is at least 1/128 away from an integer, so
+              // the FP32 quotient truncates to the exact row index
+              const int r = q - ns, ip = (int)(((float)r + 0.5f) * rj), c = r - ip * (j + 1);
               i = j + 1 + ip;
               dst[u] = &W[i][c];
               bv[u] = W[j][c];
