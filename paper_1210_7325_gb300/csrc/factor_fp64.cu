@@ -69,11 +69,12 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
 // flags[kFlagPotrf] (first failure wins) and stops.
 //
 // Right-looking over the 64 columns, the Cholesky and the inverse in the same
-// sweep.  At column j warp 0 scales column j of L and row j of W = L^{-1} by
-// r_j = 1/L_jj; then warps 1-7 apply the rank-1 updates S_il -= L_ij L_lj
-// (j < l <= i) and W_ic -= L_ij W_jc (c <= j < i), numbered densely so that
-// every lane of every binary64 instruction does useful work, while thread 0
-// already forms the next pivot d_{j+1} = S_{j+1,j+1} - L_{j+1,j}^2 and r_{j+1}.
+// sweep.  At column j the first 64 threads scale column j of L and row j of
+// W = L^{-1} by r_j = 1/L_jj (one element each); then warps 1-7 apply the
+// rank-1 updates S_il -= L_ij L_lj (j < l <= i, except S_{j+1,j+1}) and
+// W_ic -= L_ij W_jc (c <= j < i), numbered densely so that every lane of every
+// binary64 instruction does useful work, while thread 0 forms the next pivot
+// d_{j+1} = S_{j+1,j+1} - L_{j+1,j}^2 and r_{j+1}.
 // Dependent binary64 operations take about 64 cycles each on this part, so the
 // pivot's chain (about 700 cycles) runs beside the column's update instead of
 // before it.
@@ -109,25 +110,22 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ A,
     }
   }
   __syncthreads();
-  const int lane = tid % 32;
   constexpr int kUpd = 256 - 32;  // threads of warps 1-7
   for (int j = 0; j < kT; ++j) {
     if (fail) break;
-    double dd = 0.0;  // thread 0: S_{j+1,j+1} before column j's update
-    if (tid < 32) {
+    // column j of L and row j of W: one element per thread of the first 64
+    if (tid < kT) {
       const double r = piv_r;
-      for (int i = j + 1 + lane; i < kT; i += 32) S[i][j] *= r;
-      for (int c = lane; c <= j; c += 32) W[j][c] *= r;
-      if (lane == 0) {
-        S[j][j] = piv_d * r;
-        if (j + 1 < kT) dd = S[j + 1][j + 1];
-      }
+      if (tid > j) S[tid][j] *= r;
+      else W[j][tid] *= r;
+      if (tid == 0) S[j][j] = piv_d * r;
     }
     __syncthreads();
     if (tid == 0) {
+      // the next pivot; the update below leaves S_{j+1,j+1} to this thread
       if (j + 1 < kT) {
         const double l = S[j + 1][j];
-        const double d = fma(-l, l, dd);
+        const double d = fma(-l, l, S[j + 1][j + 1]);
         if (!(d > 0.0)) {
           fail = j + 2;
         } else {
@@ -138,7 +136,7 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ A,
     } else if (tid >= 32) {
       const int m = kT - 1 - j, ns = m * (m + 1) / 2, total = ns + m * (j + 1);
       const float rj = 1.0f / (float)(j + 1);
-      for (int q0 = tid - 32; q0 < total; q0 += 4 * kUpd) {
+      for (int q0 = tid - 32 + 1; q0 < total; q0 += 4 * kUpd) {  // q = 0 is S_{j+1,j+1}
         double av[4], bv[4], lv[4];
         double* dst[4];
 #pragma unroll

@@ -412,14 +412,6 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ---------------------------------------------------------------- slicing
-// Exponent E with max |x| < 2^E (frexp convention); 0 for an all-zero row.
-__device__ __forceinline__ int row_exponent(double m, bool nonfinite) {
-  if (nonfinite) return kExpNonFinite;
-  if (!(m > 0.0)) return 0;
-  const int ex = (int)((__double_as_longlong(m) >> 52) & 0x7FF);
-  return ex == 0 ? -1022 : ex - 1022;
-}
-
 // The kS slices of x relative to 2^E (see the file header), as BF16 bits.
 __device__ __forceinline__ void slice_value(double x, int E, uint16_t (&s)[kS]) {
   const long long bits = __double_as_longlong(x);
@@ -473,12 +465,18 @@ __device__ __forceinline__ void pack8(const uint16_t (&v)[8][kS], int t, uint4& 
 constexpr int kSliceWarps = 16;
 constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
 
+// |v| as a bit pattern (integer operations only: binary64 instructions are
+// scarce on this part); Inf and NaN sort above every finite value.
 __device__ __forceinline__ unsigned long long abs_bits(double v) {
-  return (unsigned long long)__double_as_longlong(fabs(v));  // Inf / NaN sort above finite
+  return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
 }
 
+// The row exponent E (max |x| < 2^E) from the bit pattern of max |x|.
 __device__ __forceinline__ int exponent_of_bits(unsigned long long mb) {
-  return row_exponent(__longlong_as_double((long long)(mb & ~(1ull << 63))), mb >= kInfBits);
+  if (mb >= kInfBits) return kExpNonFinite;
+  if (mb == 0) return 0;
+  const int ex = (int)(mb >> 52);
+  return ex == 0 ? -1022 : ex - 1022;
 }
 
 // 8 consecutive k (k0 .. k0+7) of one operand row: x(k) = base[k * stride],
