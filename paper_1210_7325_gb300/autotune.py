@@ -15,7 +15,7 @@ import json
 import os
 import threading
 
-DEFAULT_GROUPS = (2, 4, 8, 16)
+DEFAULT_GROUPS = (1, 2, 4, 8)
 _lock = threading.Lock()
 
 

@@ -138,6 +138,18 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t smem_addr) {
   return d;
 }
 
+// The same for 64-byte swizzling: rows of 64 bytes, 8-row groups 512 bytes
+// apart, layout 4.
+__device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t smem_addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(512u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
 // Instruction descriptor, kind::f16 with FP32 accumulation, both operands K-major.
 //   bits 4-5 D format (1 = F32)   bits 7-9 A format, 10-12 B format (0 = F16, 1 = BF16)
 //   bits 17-22 N >> 3             bits 24-28 M >> 4

@@ -17,10 +17,18 @@
 // BF16); the remainder terms are 2^-B smaller, so FP32 rounding in their sum
 // is negligible.  Slice H accumulates in one TMEM accumulator, R1 + R2 in a
 // second one.  The epilogue forms
-//     x~_r = u_r (acc_H + acc_R) + sum_{c in diag block} Z_rc x_c    (that sum in FP64)
+//     x~_r = u_r (acc_H + acc_R) + d_r,   d_r = sum_{c in diag block} Z_rc x_c
 // (the tensor part exactly, as an unevaluated pair of floats) and reduces
 // S_BR = x~^T x~ over the tile's 128 rows with error-free transforms in FP32,
-// written as FP64 partials.
+// written as FP64 partials.  d_r is formed in FP32 as well, from the split
+//     Z_rc = s_r k_rc + l_rc,   s_r = 2^(E_r - 12),   k_rc = rint(Z_rc / s_r),
+// where 2^E_r bounds the row's diagonal-block entries: the integers k (|k| <=
+// 2^12) times genotype codes sum exactly in FP32, the FP32 low parts l
+// (|l| <= s_r / 2) carry the rest, and d_r = fma(sum k x, s_r, sum l x) is
+// rounded once, to about the accuracy of rounding the exact d_r to FP32 (which
+// is all the two-sums below keep of it).  Binary64 arithmetic runs at a small
+// fraction of the FP32 rate on this part, and the epilogue is not overlapped
+// with the products.
 //
 // The other Gram entries of Fig. 1 are linear in x~, and
 //     S_BL_i = X~_L^T x~_i = (Z^T X~_L)^T x_i,   b_B_i = y~^T x~_i = (Z^T y~)^T x_i,
@@ -33,19 +41,28 @@
 // each row's scale.)
 //
 // Kernel shape (one persistent CTA per SM, 320 threads):
-//   warp 0      TMA producer: per stage the 128-SNP x 64 genotype tile and the S
-//               slices of Z (128 rows x 64 each), 128-byte swizzled, one mbarrier
+//   warp 0      TMA producer: per stage the 128-SNP x 32 genotype tile and the S
+//               slices of Z for the item's 256 rows (256 x 32 each), 64-byte
+//               swizzled, one mbarrier
 //   warp 1      TMEM allocator and the single thread issuing tcgen05.mma
-//               (M = 128 SNPs, N = 128 rows of x~, K = 16) into two
-//               double-buffered accumulator pairs; genotypes are operand A
+//               (M = 128 SNPs, N = 256 rows of x~, K = 16) into one accumulator
+//               pair (acc_H, acc_R: 256 columns each); genotypes are operand A.
+//               N = 256 rather than 128 cuts the operand bytes the tensor core
+//               reads from shared memory per multiply-add by a quarter and halves
+//               the genotype bytes the TMA writes there: shared-memory bandwidth,
+//               not the tensor rate, is what limits the 128 x 128 shape
 //   warps 2-9   epilogue, one SNP per thread (its TMEM lane), two warps per lane
-//               quarter each taking 64 of the 128 rows: tcgen05.ld of 32 rows at a
-//               time, the FP64 4 x 4 diagonal blocks from the SNP's own genotypes,
-//               and the S_BR sum in registers (the two halves meet in shared memory)
-// Work items (row block I, SNP tile J), I = 0..nI (I = nI is the W^T block), run
-// heaviest row blocks first in groups of `group` row blocks x all SNP tiles, so
-// the concurrently running CTAs share both the Z slices of a few row blocks and
-// the genotype panels of a few dozen SNP tiles in L2.
+//               quarter, each taking one of the item's two 128-row blocks:
+//               tcgen05.ld of 32 rows at a time, the FP64 4 x 4 diagonal blocks
+//               from the SNP's own genotypes, and the S_BR sum in registers
+// Work items (row-block pair I = blocks 2I and 2I+1, SNP tile J), I = 0..nP
+// (nP = ceil(nI / 2); I = nP is the W^T block, and an odd last pair holds one
+// block, both issued with N = 128), run heaviest first in groups of `group`
+// pairs x all SNP tiles, so the concurrently running CTAs share both the Z
+// slices of a few row blocks and the genotype panels of a few dozen SNP tiles
+// in L2.  The accumulators are single-buffered: the epilogue of an item is
+// short next to its K loop (K = 256 (I + 1) deep), so the tensor core waits on
+// it for a few percent of the time.
 //
 // One launch can serve many independent problems (scans with their own M, n,
 // p and SNP block): each problem has a descriptor in device memory (its TMA
@@ -75,18 +92,22 @@ using namespace sm100;
 
 namespace {
 
-constexpr int BM = 128;                 // rows of x~ per tile (TMEM lanes)
-constexpr int BN = 128;                 // SNPs per tile (accumulator columns)
-constexpr int BK = 64;                  // K per stage: 64 x 16-bit = one 128-byte swizzle row
-constexpr int kTileBytes = BM * BK * 2;  // one A slice or the B tile per stage
+constexpr int BM = 128;                 // rows of x~ per row block
+constexpr int kPair = 2 * BM;           // rows of x~ per work item (MMA N)
+constexpr int BN = 128;                 // SNPs per tile (MMA M, TMEM lanes)
+constexpr int BK = 32;                  // K per stage: 32 x 16-bit = one 64-byte swizzle row
+constexpr int kSliceBytes = kPair * BK * 2;  // one slice of Z for an item, per stage
+constexpr int kXBytes = BN * BK * 2;         // the genotype tile, per stage
+constexpr int kRowsBytes = kPair * (4 + 8 * 4 + 4);  // u_r, (k, l) of the diagonal blocks, s_r
 constexpr int kEpiWarps = 8;             // two per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr uint32_t kTmemCols = 512;     // 2 buffers x (acc_H + acc_R) x 128 columns
+constexpr uint32_t kTmemCols = 512;     // acc_H and acc_R, 256 columns each
+constexpr uint32_t kAccR = 256;         // column of acc_R
 constexpr int kMaxDynSmem = 232448;     // 227 KB
-constexpr int kDiag = 4;                // nd: FP64 diagonal block edge
+constexpr int kDiag = 4;                // nd: diagonal block edge
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // bounded waits give up after 1 s
 constexpr uint64_t kDrainLimitNs = 100000000ull;
-constexpr int kDefaultGroup = 8;        // row blocks per rasterization group
+constexpr int kDefaultGroup = 4;        // row-block pairs per rasterization group
 
 thread_local std::string g_err;
 
@@ -96,7 +117,8 @@ struct alignas(64) ProblemDesc {
   CUtensorMap tmB;        // genotype operand X16: (npad, kmax), 16-bit
   const uint8_t* x8a;     // genotypes as bytes, SNP-major [j][npad], zero rows >= n
   const float* rowscale;  // u_r, npad + 128 rows
-  const double* diagZ;    // npad x kDiag
+  const float* diagKL;    // npad x (k[4], l[4]): split diagonal blocks
+  const float* diagS;     // npad: s_r
   double* Pbr;            // S_BR partials, nI x ldp
   double* Glin;           // S_BL and b_B, p x ldp
   int64_t npad, ldp;
@@ -113,13 +135,13 @@ struct RunParams {
 
 struct KConst {
   int S, stages;
-  uint32_t idesc;
+  uint32_t idesc, idesc_half;  // N = 256 (two row blocks) and N = 128 (one)
   int* flags;
-  uint32_t off_rows, off_tab, off_red, off_bar, stage_bytes;
+  uint32_t off_rows, off_bar, stage_bytes;
 };
 
-// Work item t of one problem -> (row block I, SNP tile J): groups of `group` row
-// blocks, heaviest first; within a group SNP tiles advance slowest.
+// Work item t of one problem -> (row-block pair I, SNP tile J): groups of
+// `group` pairs, heaviest first; within a group SNP tiles advance slowest.
 __device__ __forceinline__ void decode_item(int t, int nIt, int nJ, int group, int& I, int& J) {
   const int per = group * nJ;
   const int full = nIt / group, tail = nIt - full * group;
@@ -150,14 +172,23 @@ __device__ __forceinline__ int find_problem(const RunParams& run, int t) {
 }
 
 struct Item {
-  int pi, I, J, nI;
+  int pi, I, J, nI, nP;  // I == nP: the W^T block
+  __device__ __forceinline__ bool lin() const { return I == nP; }
+  // both row blocks of a pair exist (MMA N = 256); else N = 128
+  __device__ __forceinline__ bool wide() const { return I < nP && 2 * I + 1 < nI; }
+  // 16-bit K extent: rows left of the pair's end, or all of them for W^T
+  __device__ __forceinline__ int kblocks() const {
+    return (lin() ? nI : min(2 * I + 2, nI)) * (BM / BK);
+  }
+  __device__ __forceinline__ int row0() const { return lin() ? nI * BM : I * kPair; }
 };
 
 __device__ __forceinline__ Item item_at(const ProblemDesc* probs, const RunParams& run, int t) {
   Item w;
   w.pi = find_problem(run, t);
   w.nI = probs[w.pi].nI;
-  decode_item(t - run.item_begin[w.pi], w.nI + 1, run.nJ[w.pi], run.group, w.I, w.J);
+  w.nP = (w.nI + 1) >> 1;
+  decode_item(t - run.item_begin[w.pi], w.nP + 1, run.nJ[w.pi], run.group, w.I, w.J);
   return w;
 }
 
@@ -185,6 +216,13 @@ __device__ __forceinline__ bool wait_drain(uint64_t* bar, uint32_t parity) {
   return mbar_wait_bounded(bar, parity, &never, kDrainLimitNs);
 }
 
+// Signed byte k of w as a float: the byte (offset by 128) becomes the low
+// mantissa bits of 2^23, and the subtraction is exact.
+template <int k>
+__device__ __forceinline__ float byte_to_float(uint32_t w_flipped) {
+  return __int_as_float((int)__byte_perm(w_flipped, 0x4B000000u, 0x7540u + k)) - 8388736.0f;
+}
+
 __device__ __forceinline__ float two_sum(float a, float b, float& err) {
   const float s = __fadd_rn(a, b);
   const float bp = __fsub_rn(s, a);
@@ -192,15 +230,14 @@ __device__ __forceinline__ float two_sum(float a, float b, float& err) {
   return s;
 }
 
-// Adds (u (aH + aR) + dg)^2 to the compensated sum (sum, comp).  The tensor
-// terms scale exactly by the power of two u; their sum and the FP64 diagonal
-// term (rounded once to FP32) join by error-free two-sums into hi + lo; hi^2 is
-// split exactly and 2 hi lo goes to the compensation.
-__device__ __forceinline__ void add_square(uint32_t aH, uint32_t aR, float u, double dg,
+// Adds (u (aH + aR) + dh)^2 to the compensated sum (sum, comp).  The tensor
+// terms scale exactly by the power of two u; their sum and the diagonal-block
+// term dh join by error-free two-sums into hi + lo; hi^2 is split exactly and
+// 2 hi lo goes to the compensation.
+__device__ __forceinline__ void add_square(uint32_t aH, uint32_t aR, float u, float dh,
                                            float& sum, float& comp) {
   const float th = __fmul_rn(__uint_as_float(aH), u);
   const float tr = __fmul_rn(__uint_as_float(aR), u);
-  const float dh = __double2float_rn(dg);
   float e1, e2, e3;
   const float s1 = two_sum(th, tr, e1);
   const float hi = two_sum(s1, dh, e2);
@@ -221,13 +258,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* full = reinterpret_cast<uint64_t*>(base + kc.off_bar);
   uint64_t* empty = full + kc.stages;
   uint64_t* tfull = empty + kc.stages;
-  uint64_t* tempty = tfull + 2;
-  uint64_t* drain = tempty + 2;
+  uint64_t* tempty = tfull + 1;
+  uint64_t* drain = tempty + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  // per-item row data, double-buffered: u_r (128 floats) then Z diagonal blocks (128 x 4 doubles)
+  // per-item row data, double-buffered: u_r, the split diagonal blocks (k[4], l[4]), s_r
   uint8_t* rows_base = base + kc.off_rows;
-  double* dtab = reinterpret_cast<double*>(base + kc.off_tab);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int S = kc.S, stages = kc.stages;
@@ -236,17 +272,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], kEpiWarps);
-    }
+    mbar_init(tfull, 1);
+    mbar_init(tempty, kEpiWarps);
     mbar_init(drain, 1);
     *abort_flag = 0;
     fence_barrier_init();
   }
-  if (warp >= 2)
-    for (int i = threadIdx.x - 64; i < 256; i += 32 * kEpiWarps)
-      dtab[i] = (double)(int8_t)(uint8_t)i;
   if (warp == 1) {
     tmem_alloc(tmem_slot, kTmemCols);
     tmem_relinquish();
@@ -271,7 +302,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           tma_prefetch_desc(&pd->tmB);
           last_pi = w.pi;
         }
-        const int kblocks = (w.I == w.nI) ? 2 * w.nI : 2 * (w.I + 1);
+        // always a 256-row box: rows past the W^T block read as zeros, and the
+        // rows an N = 128 product does not use are never read by the MMA
+        const int kblocks = w.kblocks(), row0 = w.row0();
         for (int kb = 0; kb < kblocks; ++kb, ++g) {
           const int st = (int)(g % stages);
           const uint32_t ph = g / stages;
@@ -279,11 +312,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(&full[st], (uint32_t)(S + 1) * kTileBytes);
+          mbar_arrive_expect_tx(&full[st], (uint32_t)S * kSliceBytes + kXBytes);
           uint8_t* sb = base + (size_t)st * kc.stage_bytes;
           for (int s = 0; s < S; ++s)
-            tma_load_3d(sb + s * kTileBytes, &pd->tmA, &full[st], kb * BK, w.I * BM, s);
-          tma_load_2d(sb + S * kTileBytes, &pd->tmB, &full[st], kb * BK, w.J * BN);
+            tma_load_3d(sb + s * kSliceBytes, &pd->tmA, &full[st], kb * BK, row0, s);
+          tma_load_2d(sb + S * kSliceBytes, &pd->tmB, &full[st], kb * BK, w.J * BN);
         }
       }
       if (!ok) {
@@ -300,18 +333,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t g = 0;
       bool ok = true;
       int it = 0;
+      const uint32_t dH = tmem, dR = tmem + kAccR;
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
         const Item w = item_at(probs, run, t);
-        const int kblocks = (w.I == w.nI) ? 2 * w.nI : 2 * (w.I + 1);
-        const int buf = it & 1;
-        const uint32_t u = (uint32_t)it >> 1;
-        if (!mbar_wait_bounded(&tempty[buf], (u & 1) ^ 1, abort_flag, kWaitLimitNs)) {
+        const int kblocks = w.kblocks();
+        const uint32_t idesc = w.wide() ? kc.idesc : kc.idesc_half;
+        // the epilogue has read the previous item's accumulators
+        if (!mbar_wait_bounded(tempty, ((uint32_t)it & 1) ^ 1, abort_flag, kWaitLimitNs)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t dH = tmem + (uint32_t)buf * 256u;
-        const uint32_t dR = dH + 128u;
         for (int kb = 0; kb < kblocks; ++kb, ++g) {
           const int st = (int)(g % stages);
           const uint32_t ph = g / stages;
@@ -321,19 +353,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t sz = smem_u32(base + (size_t)st * kc.stage_bytes);  // Z slices
-          const uint32_t sx = sz + (uint32_t)S * kTileBytes;                  // genotypes
+          const uint32_t sx = sz + (uint32_t)S * kSliceBytes;                 // genotypes
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t adesc = umma_desc_sw128(sx + kk * 32);
+            const uint64_t adesc = umma_desc_sw64(sx + kk * 32);
             const uint32_t first = (kb | kk) != 0;
-            umma_f16(dH, adesc, umma_desc_sw128(sz + kk * 32), kc.idesc, first);
+            umma_f16(dH, adesc, umma_desc_sw64(sz + kk * 32), idesc, first);
             for (int s = 1; s < S; ++s)
-              umma_f16(dR, adesc, umma_desc_sw128(sz + s * kTileBytes + kk * 32), kc.idesc,
+              umma_f16(dR, adesc, umma_desc_sw64(sz + s * kSliceBytes + kk * 32), idesc,
                        first | (s > 1));
           }
           umma_commit(&empty[st]);
         }
-        if (ok) umma_commit(&tfull[buf]);
+        if (ok) umma_commit(tfull);
       }
       if (!ok) raise_error(kc.flags, 2);
       // every issued MMA completes before the accumulators are released
@@ -343,44 +375,48 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ------------------------------------------------------------ epilogue
     const int quarter = warp & 3;            // TMEM lanes this warp may read
-    const int half = (warp - 2) >> 2;        // which 64 of the 128 rows this warp handles
+    const int half = (warp - 2) >> 2;        // which row block of the pair this warp handles
     const int lrow = quarter * 32 + lane;    // accumulator lane = SNP within the tile
     const int et = threadIdx.x - 64;         // 0..255
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-    float* red = reinterpret_cast<float*>(base + kc.off_red);  // [BM][2]
     int it = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
       const Item w = item_at(probs, run, t);
       const ProblemDesc* pd = probs + w.pi;
-      const int I = w.I, J = w.J;
-      const bool lin = (I == w.nI);
+      const bool lin = w.lin();
+      const int blk = 2 * w.I + half;        // this warp's row block
+      const bool bv = !lin && blk < w.nI;
       const int p = pd->p;
       const int64_t kk_j = run.k[w.pi];
       const int64_t ldp = pd->ldp;
-      const int buf = it & 1;
-      const uint32_t u = (uint32_t)it >> 1;
-      const int64_t j = (int64_t)J * BN + lrow;
+      const uint32_t ph = (uint32_t)it & 1;
+      const int64_t j = (int64_t)w.J * BN + lrow;
       const bool jv = j < kk_j;
-      float* su = reinterpret_cast<float*>(rows_base + buf * (BM * 4 + BM * kDiag * 8));
-      double* sz = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(su) + BM * 4);
-      if (et < BM) {
-        const int64_t r = (int64_t)I * BM + et;
-        su[et] = pd->rowscale[r];
-        if (!lin) {
-#pragma unroll
-          for (int q = 0; q < kDiag; ++q) sz[et * kDiag + q] = pd->diagZ[r * kDiag + q];
+      float* su = reinterpret_cast<float*>(rows_base + ph * kRowsBytes);
+      float* skl = su + kPair;           // row r: k[0..3], l[0..3]
+      float* ss = skl + kPair * 8;
+      {
+        const int64_t r = (int64_t)w.row0() + et;
+        if (lin) {
+          if (et < BM) su[et] = pd->rowscale[r];
+        } else if (r < pd->npad) {
+          su[et] = pd->rowscale[r];
+          const float4* src = reinterpret_cast<const float4*>(pd->diagKL + r * 8);
+          reinterpret_cast<float4*>(skl)[et * 2] = src[0];
+          reinterpret_cast<float4*>(skl)[et * 2 + 1] = src[1];
+          ss[et] = pd->diagS[r];
         }
       }
-      uint4 xv[BM / 32];  // this SNP's genotypes of the 64 rows this warp handles
+      uint4 xv[BM / 16];  // this SNP's genotypes of this warp's 128 rows
 #pragma unroll
-      for (int i = 0; i < BM / 32; ++i) xv[i] = make_uint4(0, 0, 0, 0);
-      if (!lin && jv) {
-        const uint4* src = reinterpret_cast<const uint4*>(pd->x8a + j * pd->npad +
-                                                          (int64_t)I * BM + half * 64);
+      for (int i = 0; i < BM / 16; ++i) xv[i] = make_uint4(0, 0, 0, 0);
+      if (bv && jv) {
+        const uint4* src =
+            reinterpret_cast<const uint4*>(pd->x8a + j * pd->npad + (int64_t)blk * BM);
 #pragma unroll
-        for (int i = 0; i < BM / 32; ++i) xv[i] = __ldg(src + i);
+        for (int i = 0; i < BM / 16; ++i) xv[i] = __ldg(src + i);
       }
-      const bool got = mbar_wait_bounded(&tfull[buf], u & 1, abort_flag, kWaitLimitNs);
+      const bool got = mbar_wait_bounded(tfull, ph, abort_flag, kWaitLimitNs);
       if (!epilogue_all(got)) {  // all epilogue threads leave together; also orders the row data
         if (!got && lane == 0) raise_error(kc.flags, 3);
         break;
@@ -390,13 +426,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         // W^T block: column q < p holds (M^{-1}[X_L | y])_q^T x_j
         if (half == 0) {
           uint32_t aH[32], aR[32];
-          tmem_ld32(lane_base + (uint32_t)buf * 256u, aH);
-          tmem_ld32(lane_base + (uint32_t)buf * 256u + 128u, aR);
+          tmem_ld32(lane_base, aH);
+          tmem_ld32(lane_base + kAccR, aR);
           tmem_ld_wait(aH);
           tmem_ld_fence(aR);
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(&tempty[buf]);
+          if (lane == 0) mbar_arrive(tempty);
           if (jv) {
 #pragma unroll
             for (int q = 0; q < 32; ++q)
@@ -408,57 +444,63 @@ __global__ void __launch_bounds__(kThreads, 1)
         } else {
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(&tempty[buf]);
+          if (lane == 0) mbar_arrive(tempty);
         }
+        continue;
+      }
+      if (!bv) {  // the missing second block of an odd last pair
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty);
         continue;
       }
       float sum = 0.f, comp = 0.f;
 #pragma unroll 1
-      for (int cc = 0; cc < 2; ++cc) {
-        const int c = half * 2 + cc;  // 32-row chunk of the item
+      for (int c = 0; c < BM / 32; ++c) {  // 32-row chunk of this warp's block
+        const uint32_t col = (uint32_t)(half * BM + c * 32);
         uint32_t aH[32], aR[32];
-        tmem_ld32(lane_base + (uint32_t)buf * 256u + (uint32_t)c * 32u, aH);
-        tmem_ld32(lane_base + (uint32_t)buf * 256u + 128u + (uint32_t)c * 32u, aR);
+        tmem_ld32(lane_base + col, aH);
+        tmem_ld32(lane_base + kAccR + col, aR);
+        uint4 v0 = xv[0], v1 = xv[1];
+#pragma unroll
+        for (int q = 1; q < BM / 32; ++q)
+          if (c == q) {
+            v0 = xv[2 * q];
+            v1 = xv[2 * q + 1];
+          }
         tmem_ld_wait(aH);
         tmem_ld_fence(aR);
-        if (cc == 1) {
+        if (c == BM / 32 - 1) {
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(&tempty[buf]);
+          if (lane == 0) mbar_arrive(tempty);
         }
 #pragma unroll
         for (int g4 = 0; g4 < 8; ++g4) {
           // rows 4*g4 .. 4*g4+3 of this chunk form one FP64 diagonal block
-          const int word = cc * 8 + g4;  // genotype word within this warp's 64 rows
-          const uint4 v4 = xv[word >> 2];
-          const uint32_t wv = (word & 3) == 0 ? v4.x : (word & 3) == 1 ? v4.y
-                            : (word & 3) == 2 ? v4.z : v4.w;
-          const double x0 = dtab[wv & 0xffu], x1 = dtab[(wv >> 8) & 0xffu];
-          const double x2 = dtab[(wv >> 16) & 0xffu], x3 = dtab[wv >> 24];
-          const int rl = c * 32 + g4 * 4;
-          const double* z = sz + rl * kDiag;
-          const double d0 = z[0] * x0;
-          const double d1 = fma(z[4], x0, z[5] * x1);
-          const double d2 = fma(z[8], x0, fma(z[9], x1, z[10] * x2));
-          const double d3 = fma(z[12], x0, fma(z[13], x1, fma(z[14], x2, z[15] * x3)));
+          const uint4 v4 = g4 < 4 ? v0 : v1;
+          const uint32_t wv = ((g4 & 3) == 0 ? v4.x : (g4 & 3) == 1 ? v4.y
+                             : (g4 & 3) == 2 ? v4.z : v4.w) ^ 0x80808080u;
+          const float x0 = byte_to_float<0>(wv), x1 = byte_to_float<1>(wv);
+          const float x2 = byte_to_float<2>(wv), x3 = byte_to_float<3>(wv);
+          const int rl = half * BM + c * 32 + g4 * 4;  // row within the pair
+          const float* z = skl + rl * 8;               // row rl + i: k at 8i, l at 8i + 4
+          const float4 s4 = *reinterpret_cast<const float4*>(ss + rl);
+          // integer parts: exact; low parts: one rounding each; d = fma(k x, s, l x)
+          const float d0 = fmaf(z[0] * x0, s4.x, z[4] * x0);
+          const float d1 = fmaf(fmaf(z[9], x1, z[8] * x0), s4.y, fmaf(z[13], x1, z[12] * x0));
+          const float d2 = fmaf(fmaf(z[18], x2, fmaf(z[17], x1, z[16] * x0)), s4.z,
+                                fmaf(z[22], x2, fmaf(z[21], x1, z[20] * x0)));
+          const float d3 =
+              fmaf(fmaf(z[27], x3, fmaf(z[26], x2, fmaf(z[25], x1, z[24] * x0))), s4.w,
+                   fmaf(z[31], x3, fmaf(z[30], x2, fmaf(z[29], x1, z[28] * x0))));
           add_square(aH[g4 * 4 + 0], aR[g4 * 4 + 0], su[rl + 0], d0, sum, comp);
           add_square(aH[g4 * 4 + 1], aR[g4 * 4 + 1], su[rl + 1], d1, sum, comp);
           add_square(aH[g4 * 4 + 2], aR[g4 * 4 + 2], su[rl + 2], d2, sum, comp);
           add_square(aH[g4 * 4 + 3], aR[g4 * 4 + 3], su[rl + 3], d3, sum, comp);
         }
       }
-      // the two halves of each SNP meet in shared memory; half 0 writes
-      if (half == 1) {
-        red[lrow * 2 + 0] = sum;
-        red[lrow * 2 + 1] = comp;
-      }
-      named_barrier_sync(1, 32 * kEpiWarps);
-      if (half == 0 && jv) {
-        float e;
-        const float s = two_sum(sum, red[lrow * 2 + 0], e);
-        const float cmp = __fadd_rn(__fadd_rn(comp, red[lrow * 2 + 1]), e);
-        pd->Pbr[(int64_t)I * ldp + j] = (double)s + (double)cmp;
-      }
+      if (jv) pd->Pbr[(int64_t)blk * ldp + j] = (double)sum + (double)comp;
     }
   }
   tc_fence_before();
@@ -515,7 +557,8 @@ __device__ __forceinline__ double from16(uint16_t b) {
 }
 
 // Splits the part of each row of Z left of its diagonal block into S slices
-// (see the file header); also writes u_r and the FP64 diagonal blocks.
+// (see the file header); also writes u_r and the split diagonal blocks
+// (k_rc, l_rc, s_r).
 // One CTA per 32-row stripe; Z is read column-major (coalesced along rows) and
 // the slices are written row-major through a shared-memory transpose.
 template <bool kBF16>
@@ -523,7 +566,8 @@ __global__ void __launch_bounds__(256) split_kernel(const double* __restrict__ Z
                                                     int64_t npad, int S, int bits, int naive,
                                                     uint16_t* __restrict__ slices,
                                                     float* __restrict__ rowscale,
-                                                    double* __restrict__ diagZ) {
+                                                    float* __restrict__ diagKL,
+                                                    float* __restrict__ diagS) {
   __shared__ double red[8][33];
   __shared__ uint16_t sh[3][32][64 + 8];
   const int l = threadIdx.x % 32, w = threadIdx.x / 32;
@@ -543,9 +587,25 @@ __global__ void __launch_bounds__(256) split_kernel(const double* __restrict__ Z
     }
     red[0][l] = u;
     rowscale[r] = (float)u;
+    double zd[kDiag], dm = 0.0;
 #pragma unroll
-    for (int q = 0; q < kDiag; ++q)
-      diagZ[r * kDiag + q] = (r0 + q <= r) ? Z[r + (r0 + q) * ldz] : 0.0;
+    for (int q = 0; q < kDiag; ++q) {
+      zd[q] = (r0 + q <= r) ? Z[r + (r0 + q) * ldz] : 0.0;
+      dm = fmax(dm, fabs(zd[q]));
+    }
+    double sr = 0.0;
+    if (dm > 0.0) {
+      int e;
+      frexp(dm, &e);  // dm < 2^e, so |k| <= 2^12
+      sr = ldexp(1.0, e - 12);
+    }
+#pragma unroll
+    for (int q = 0; q < kDiag; ++q) {
+      const double k = sr > 0.0 ? rint(zd[q] / sr) : 0.0;
+      diagKL[r * 8 + q] = (float)k;
+      diagKL[r * 8 + 4 + q] = (float)(zd[q] - k * sr);
+    }
+    diagS[r] = (float)sr;
   }
   __syncthreads();
   const double inv_u = 1.0 / red[0][l];  // power of two: exact
@@ -690,7 +750,8 @@ struct MixedState {
   int num_sms = 1;
   uint16_t* slices = nullptr;  // 3 planes x (npad + 128) x npad, row-major (K-major)
   float* rowscale = nullptr;   // npad + 128
-  double* diagZ = nullptr;     // npad x kDiag
+  float* diagKL = nullptr;     // npad x 8: k[4], l[4] of the diagonal blocks
+  float* diagS = nullptr;      // npad
   double* Wm = nullptr;        // W = M^{-1} [X_L | y], npad x p
   uint16_t* x16 = nullptr;     // kmax x npad
   uint8_t* x8a = nullptr;      // kmax x npad
@@ -712,10 +773,9 @@ struct MixedBatch {
 namespace {
 
 size_t smem_bytes(int S, int stages) {
-  const uint32_t stage_bytes = (uint32_t)(S + 1) * kTileBytes;
-  const uint32_t rows_bytes = 2u * (BM * 4 + BM * kDiag * 8);
-  const uint32_t epi = rows_bytes + 256 * 8 + BM * 2 * 4;
-  const uint32_t bars = 8 * (2 * 4 + 5) + 16;
+  const uint32_t stage_bytes = (uint32_t)S * kSliceBytes + kXBytes;
+  const uint32_t epi = 2u * kRowsBytes;
+  const uint32_t bars = 8 * (2 * stages + 3) + 16;
   return (size_t)stages * stage_bytes + epi + bars + 1024;
 }
 
@@ -727,7 +787,7 @@ size_t mixed_footprint(int64_t n, int64_t npad, int p, int64_t kmax, int split_t
   (void)n;
   (void)split_terms;
   size_t b = (size_t)3 * (npad + 128) * npad * 2;
-  b += (size_t)(npad + 128) * 4 + (size_t)npad * (kDiag * 8 + 8 * p);
+  b += (size_t)(npad + 128) * 4 + (size_t)npad * (9 * 4 + 8 * p);
   b += (size_t)kmax * npad * 3 + sizeof(ProblemDesc);
   return b;
 }
@@ -740,7 +800,8 @@ void mixed_free(MixedState* ms) {
   if (!ms) return;
   cudaFree(ms->slices);
   cudaFree(ms->rowscale);
-  cudaFree(ms->diagZ);
+  cudaFree(ms->diagKL);
+  cudaFree(ms->diagS);
   cudaFree(ms->Wm);
   cudaFree(ms->x16);
   cudaFree(ms->x8a);
@@ -779,7 +840,8 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   const size_t rows = (size_t)npad + 128;
   if (cudaMalloc(&ms->slices, 3 * rows * npad * 2) != cudaSuccess ||
       cudaMalloc(&ms->rowscale, rows * 4) != cudaSuccess ||
-      cudaMalloc(&ms->diagZ, (size_t)npad * kDiag * 8) != cudaSuccess ||
+      cudaMalloc(&ms->diagKL, (size_t)npad * 8 * 4) != cudaSuccess ||
+      cudaMalloc(&ms->diagS, (size_t)npad * 4) != cudaSuccess ||
       cudaMalloc(&ms->Wm, (size_t)npad * p * 8) != cudaSuccess ||
       cudaMalloc(&ms->x16, (size_t)kmax * npad * 2) != cudaSuccess ||
       cudaMalloc(&ms->x8a, (size_t)kmax * npad) != cudaSuccess ||
@@ -793,7 +855,7 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
     cudaGetLastError();
     return fail(GLS_ERR_CUDA, "cudaMemset of the operand slices failed");
   }
-  int stages = 4;
+  int stages = 6;
   while (stages > 2 && smem_bytes(ms->S, stages) > (size_t)kMaxDynSmem) --stages;
   if (smem_bytes(ms->S, stages) > (size_t)kMaxDynSmem)
     return fail(GLS_ERR_UNSUPPORTED, "shared-memory budget exceeded for this split");
@@ -802,12 +864,11 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   KConst& kc = ms->kc;
   kc.S = ms->S;
   kc.stages = stages;
-  kc.stage_bytes = (uint32_t)(ms->S + 1) * kTileBytes;
+  kc.stage_bytes = (uint32_t)ms->S * kSliceBytes + kXBytes;
   kc.off_rows = (uint32_t)stages * kc.stage_bytes;
-  kc.off_tab = kc.off_rows + 2u * (BM * 4 + BM * kDiag * 8);
-  kc.off_red = kc.off_tab + 256 * 8;
-  kc.off_bar = kc.off_red + BM * 2 * 4;
-  kc.idesc = umma_idesc_f16(BM, BN, ms->bf16);
+  kc.off_bar = kc.off_rows + 2u * kRowsBytes;
+  kc.idesc = umma_idesc_f16(BN, kPair, ms->bf16);
+  kc.idesc_half = umma_idesc_f16(BN, BM, ms->bf16);
   if (!g_attr_done) {
     if (cudaFuncSetAttribute(trsm_gram_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kMaxDynSmem) != cudaSuccess) {
@@ -825,10 +886,10 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   {
     cuuint64_t dims[3] = {(cuuint64_t)npad, (cuuint64_t)rows, (cuuint64_t)ms->S};
     cuuint64_t strides[2] = {(cuuint64_t)npad * 2, (cuuint64_t)rows * npad * 2};
-    cuuint32_t box[3] = {BK, BM, 1};
+    cuuint32_t box[3] = {BK, kPair, 1};
     cuuint32_t es[3] = {1, 1, 1};
     if (enc(&d.tmA, dt, 3, ms->slices, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return fail(GLS_ERR_CUDA, "tensor map encode (slices) failed");
   }
@@ -838,13 +899,14 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
     cuuint32_t box[2] = {BK, BN};
     cuuint32_t es[2] = {1, 1};
     if (enc(&d.tmB, dt, 2, ms->x16, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return fail(GLS_ERR_CUDA, "tensor map encode (genotypes) failed");
   }
   d.x8a = ms->x8a;
   d.rowscale = ms->rowscale;
-  d.diagZ = ms->diagZ;
+  d.diagKL = ms->diagKL;
+  d.diagS = ms->diagS;
   d.npad = npad;
   d.nI = (int)(npad / BM);
   d.p = p;
@@ -860,10 +922,10 @@ gls_status_t mixed_prepare(MixedState* ms, const double* Z, int64_t ldz, const d
     const unsigned grid = (unsigned)(ms->npad / 32);
     if (ms->bf16)
       split_kernel<true><<<grid, 256, 0, st>>>(Z, ldz, ms->npad, ms->S, ms->bits, ms->naive,
-                                               ms->slices, ms->rowscale, ms->diagZ);
+                                               ms->slices, ms->rowscale, ms->diagKL, ms->diagS);
     else
       split_kernel<false><<<grid, 256, 0, st>>>(Z, ldz, ms->npad, ms->S, ms->bits, ms->naive,
-                                                ms->slices, ms->rowscale, ms->diagZ);
+                                                ms->slices, ms->rowscale, ms->diagKL, ms->diagS);
   }
   if (!w_ready)
     wtrans_kernel<<<(unsigned)(ms->npad / 64), 256, 0, st>>>(Z, ldz, ms->npad, Wt, ldw, ms->p,
@@ -898,8 +960,9 @@ cudaError_t mixed_convert(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_
 
 namespace {
 
+// (row-block pairs + the W^T block) x SNP tiles
 int items_of(const MixedState* ms, int64_t k) {
-  return (int)(ms->npad / BM + 1) * (int)ceil_div(k, BN);
+  return (int)(ceil_div(ms->npad / BM, 2) + 1) * (int)ceil_div(k, BN);
 }
 
 cudaError_t launch(const MixedState* ms0, const ProblemDesc* d_desc, const RunParams& run,
