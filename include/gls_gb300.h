@@ -72,6 +72,14 @@ typedef enum {
 /* FP64 path: factor M with the tensor-core binary64 products instead of the
  * default plain binary64 CUDA-core kernels. */
 #define GLS_FLAG_FACTOR_TENSOR 4u
+/* Launch every kernel directly.  By default a launch sequence that repeats
+ * with the same arguments (the factor of M on a plan, one block of
+ * gls_solve_block / gls_solve_stream, one gls_batch_solve round) is captured
+ * as a CUDA graph the second time it is seen and replayed from then on (one
+ * graph launch instead of up to ~1500 kernel launches for the factor).  Only
+ * plans that own their stream (desc.stream == NULL) use graphs; results are
+ * the same either way.  For a batch the flag of its first plan decides. */
+#define GLS_FLAG_EAGER 8u
 
 /* Plan description.  Zero-initialise and fill the fields that matter. */
 typedef struct {

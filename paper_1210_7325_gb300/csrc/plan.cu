@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -67,6 +68,11 @@ namespace gls {
 void set_last_error_text(const char* msg) { g_last_error = msg ? msg : ""; }
 }  // namespace gls
 
+namespace {
+struct Capture;
+struct ReplayCache;
+}  // namespace
+
 struct gls_plan {
   gls_plan_desc_t desc{};
   int device = 0;
@@ -111,6 +117,8 @@ struct gls_plan {
   bool has_factor = false;  // L and Z valid
   bool has_xl = false;      // X_L staged
   bool factored = false;    // ready for solves
+  Capture* cap = nullptr;   // set while a launch sequence is being captured
+  ReplayCache* replays = nullptr;  // captured launch sequences of this plan
 };
 
 namespace {
@@ -129,27 +137,206 @@ cudaEvent_t pool_event(gls_plan* pl) {
   return e;
 }
 
-// Brackets one kernel (or phase) with events on the plan's stream when timing is on.
+// ------------------------------------------------------------------ CUDA graphs
+// A launch sequence that repeats with the same arguments is captured as a CUDA
+// graph the second time it is seen and replayed from then on: the factor of M
+// on a plan (about 1500 launches at n = 10^4), one block of the SNP loop, one
+// batched round.  The first run is eager, so one-off sequences (the rounds of a
+// serving loop) cost no instantiation and first-use setup stays outside any
+// capture.  Timing brackets inside a captured sequence become event-record
+// nodes that get fresh events at every replay.
+struct Capture {
+  struct Mark {
+    cudaEvent_t e0, e1;
+    gls_plan::Slot* slot;
+  };
+  std::vector<cudaEvent_t> spare;  // created before the capture began
+  std::vector<cudaEvent_t> used;
+  std::vector<Mark> marks;
+  cudaEvent_t take() {
+    if (spare.empty()) return nullptr;
+    cudaEvent_t e = spare.back();
+    spare.pop_back();
+    used.push_back(e);
+    return e;
+  }
+};
+
+struct Replay {
+  struct Mark {
+    cudaGraphNode_t n0 = nullptr, n1 = nullptr;
+    gls_plan::Slot* slot = nullptr;
+  };
+  uint64_t key = 0, used = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> events;  // the placeholders the graph's event-record nodes name
+  int64_t launches = 0;
+  ~Replay() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+  }
+};
+
+struct ReplayCache {
+  static constexpr size_t kMaxGraphs = 48;  // least recently used beyond this are dropped
+  static constexpr size_t kMaxSeen = 256;
+  std::vector<std::unique_ptr<Replay>> items;
+  std::vector<uint64_t> seen;  // keys run eagerly once
+  uint64_t clock = 0;
+  bool enabled = true;
+};
+
+// FNV-1a over 64-bit words.
+struct KeyHash {
+  uint64_t h = 1469598103934665603ull;
+  KeyHash& operator<<(uint64_t v) {
+    for (int i = 0; i < 8; ++i) {
+      h ^= (v >> (8 * i)) & 0xFFu;
+      h *= 1099511628211ull;
+    }
+    return *this;
+  }
+  KeyHash& operator<<(const void* p) { return *this << (uint64_t)(uintptr_t)p; }
+};
+
+// Brackets one kernel (or phase) with events on the plan's stream when timing
+// is on; inside a capture the events become event-record nodes of the graph.
 struct Timed {
   gls_plan* pl;
   gls_plan::Slot* slot;
+  Capture* cap;
   cudaEvent_t e0 = nullptr;
-  Timed(gls_plan* p, gls_plan::Slot* s) : pl(p), slot(s) {
-    if (pl->timing && (e0 = pool_event(pl))) cudaEventRecord(e0, pl->stream);
+  Timed(gls_plan* p, gls_plan::Slot* s) : pl(p), slot(s), cap(p->cap) {
+    if (!pl->timing) return;
+    e0 = cap ? cap->take() : pool_event(pl);
+    if (e0) record(e0);
+  }
+  void record(cudaEvent_t e) {
+    if (cap) cudaEventRecordWithFlags(e, pl->stream, cudaEventRecordExternal);
+    else cudaEventRecord(e, pl->stream);
   }
   void finish() {
     if (!e0) return;
-    cudaEvent_t e1 = pool_event(pl);
+    cudaEvent_t e1 = cap ? cap->take() : pool_event(pl);
     if (!e1) {
-      pl->event_pool.push_back(e0);
+      if (!cap) pl->event_pool.push_back(e0);
     } else {
-      cudaEventRecord(e1, pl->stream);
-      slot->pending.emplace_back(e0, e1);
+      record(e1);
+      if (cap) cap->marks.push_back({e0, e1, slot});
+      else slot->pending.emplace_back(e0, e1);
     }
     e0 = nullptr;
   }
   ~Timed() { finish(); }
 };
+
+gls_status_t launch_replay(gls_plan* pl, Replay& r) {
+  if (pl->timing) {
+    for (Replay::Mark& m : r.marks) {
+      cudaEvent_t e0 = pool_event(pl), e1 = pool_event(pl);
+      if (!e0 || !e1) {
+        if (e0) pl->event_pool.push_back(e0);
+        if (e1) pl->event_pool.push_back(e1);
+        continue;
+      }
+      GLS_CUDA(cudaGraphExecEventRecordNodeSetEvent(r.exec, m.n0, e0));
+      GLS_CUDA(cudaGraphExecEventRecordNodeSetEvent(r.exec, m.n1, e1));
+      m.slot->pending.emplace_back(e0, e1);
+    }
+  }
+  GLS_CUDA(cudaGraphLaunch(r.exec, pl->stream));
+  pl->launches += r.launches;
+  return GLS_OK;
+}
+
+// Runs body() (launches on pl->stream only, no host synchronisation) through
+// the cache rc: eagerly the first time `key` is seen, captured and replayed
+// from the second time on.  A failed capture runs body() eagerly and turns
+// the cache off.
+template <class F>
+gls_status_t replayed(gls_plan* pl, ReplayCache* rc, uint64_t key, F&& body) {
+  if (!rc || !rc->enabled || !pl->own_stream || (pl->desc.flags & GLS_FLAG_EAGER)) return body();
+  key = (KeyHash() << key << (uint64_t)pl->timing).h;
+  for (auto& r : rc->items)
+    if (r->key == key) {
+      r->used = ++rc->clock;
+      return launch_replay(pl, *r);
+    }
+  if (std::find(rc->seen.begin(), rc->seen.end(), key) == rc->seen.end()) {
+    if (rc->seen.size() >= ReplayCache::kMaxSeen) rc->seen.erase(rc->seen.begin());
+    rc->seen.push_back(key);
+    return body();
+  }
+  Capture cap;
+  for (int i = 0; i < 8 && pl->timing; ++i) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      break;
+    }
+    cap.spare.push_back(e);
+  }
+  auto r = std::make_unique<Replay>();
+  r->key = key;
+  const int64_t l0 = pl->launches;
+  bool ok = cudaStreamBeginCapture(pl->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  gls_status_t s = GLS_OK;
+  if (ok) {
+    pl->cap = &cap;
+    s = body();
+    pl->cap = nullptr;
+    ok = cudaStreamEndCapture(pl->stream, &r->graph) == cudaSuccess && r->graph && s == GLS_OK;
+  }
+  r->launches = pl->launches - l0;
+  pl->launches = l0;
+  r->events = cap.used;
+  r->events.insert(r->events.end(), cap.spare.begin(), cap.spare.end());
+  if (ok) ok = cudaGraphInstantiate(&r->exec, r->graph, 0) == cudaSuccess;
+  if (ok && !cap.marks.empty()) {
+    size_t nn = 0;
+    ok = cudaGraphGetNodes(r->graph, nullptr, &nn) == cudaSuccess;
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (ok && nn) ok = cudaGraphGetNodes(r->graph, nodes.data(), &nn) == cudaSuccess;
+    auto node_of = [&](cudaEvent_t e) -> cudaGraphNode_t {
+      for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        cudaEvent_t ev = nullptr;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeEventRecord &&
+            cudaGraphEventRecordNodeGetEvent(nd, &ev) == cudaSuccess && ev == e)
+          return nd;
+      }
+      return nullptr;
+    };
+    for (const Capture::Mark& m : cap.marks) {
+      Replay::Mark rm;
+      rm.n0 = node_of(m.e0);
+      rm.n1 = node_of(m.e1);
+      rm.slot = m.slot;
+      if (!rm.n0 || !rm.n1) ok = false;
+      r->marks.push_back(rm);
+    }
+  }
+  if (!ok) {
+    cudaGetLastError();
+    rc->enabled = false;
+    r.reset();
+    return body();  // nothing ran during the capture
+  }
+  if (rc->items.size() >= ReplayCache::kMaxGraphs) {
+    cudaStreamSynchronize(pl->stream);  // the evicted graph may still be running
+    auto lru = std::min_element(rc->items.begin(), rc->items.end(),
+                                [](const std::unique_ptr<Replay>& a,
+                                   const std::unique_ptr<Replay>& b) { return a->used < b->used; });
+    rc->items.erase(lru);
+  }
+  r->used = ++rc->clock;
+  Replay& ref = *r;
+  rc->items.push_back(std::move(r));
+  return launch_replay(pl, ref);
+}
 
 // FP64 path: per 64-row block, p + 1 partial sums per SNP.  Mixed path: one S_BR
 // partial per 128-row block per SNP, plus the p linear Gram entries per SNP.
@@ -207,7 +394,8 @@ gls_status_t validate_desc(const gls_plan_desc_t* d) {
     set_error("split_terms must be 0, 2 or 3");
     return GLS_ERR_INVALID_ARG;
   }
-  const uint32_t known = GLS_FLAG_NAIVE_SPLIT | GLS_FLAG_FACTOR_NATIVE | GLS_FLAG_FACTOR_TENSOR;
+  const uint32_t known =
+      GLS_FLAG_NAIVE_SPLIT | GLS_FLAG_FACTOR_NATIVE | GLS_FLAG_FACTOR_TENSOR | GLS_FLAG_EAGER;
   if ((d->flags & ~known) != 0) {
     set_error("unknown flag bits 0x%x", d->flags);
     return GLS_ERR_INVALID_ARG;
@@ -229,6 +417,8 @@ void free_plan(gls_plan* pl) {
   if (pl->stream) cudaStreamSynchronize(pl->stream);
   if (pl->h2d) cudaStreamSynchronize(pl->h2d);
   if (pl->d2h) cudaStreamSynchronize(pl->d2h);
+  delete pl->replays;
+  pl->replays = nullptr;
   if (pl->mixed) gls::mixed_free(pl->mixed);
   if (pl->tcf) gls::tc_factor_free(pl->tcf);
   cudaFree(pl->A);
@@ -427,6 +617,7 @@ gls_status_t gls_plan_create(const gls_plan_desc_t* desc, gls_plan_t* out) {
     }
     pl->own_stream = true;
   }
+  pl->replays = new ReplayCache();
   if (cudaStreamCreateWithFlags(&pl->h2d, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&pl->d2h, cudaStreamNonBlocking) != cudaSuccess) {
     set_error("cudaStreamCreate failed");
@@ -520,26 +711,33 @@ gls_status_t gls_factor(gls_plan_t pl, const double* M, int64_t ldm, const doubl
   const int p = pl->p;
   cudaStream_t st = pl->stream;
   Timed phase(pl, &pl->t_factor);
-  const int64_t tc_before = pl->tc ? gls::tc_launches(pl->tcf) : 0;
   GLS_CUDA(cudaMemsetAsync(pl->flags, 0, sizeof(int) * gls::kFlagCount, st));
   if (M) {
-    const int64_t N = npad / gls::kT;
-    pl->launches += 2 + (pl->tc ? 0 : N + 4 * (N - 1));
     pl->has_factor = false;
     GLS_CUDA(cudaMemcpy2DAsync(pl->A, npad * sizeof(double), M, ldm * sizeof(double),
                                n * sizeof(double), n, cudaMemcpyDefault, st));
-    gls::launch_pad_lower(pl->A, npad, n, npad, st);
-    gls::launch_identity(pl->Z, npad, npad, st);
-    if (pl->tc) {
-      cudaError_t e = gls::tc_potrf_trtri(pl->tcf, pl->A, pl->Z, npad, npad, pl->flags, st);
-      if (e != cudaSuccess) {
-        set_error("tensor-core factor: %s %s", cudaGetErrorString(e), gls::tc_factor_last_error());
-        return GLS_ERR_CUDA;
+    // from here on the factor touches plan buffers only: one graph per plan
+    GLS_TRY(replayed(pl, pl->replays, (KeyHash() << 1u).h, [&]() -> gls_status_t {
+      gls::launch_pad_lower(pl->A, npad, n, npad, st);
+      gls::launch_identity(pl->Z, npad, npad, st);
+      if (pl->tc) {
+        const int64_t tc0 = gls::tc_launches(pl->tcf);
+        cudaError_t e = gls::tc_potrf_trtri(pl->tcf, pl->A, pl->Z, npad, npad, pl->flags, st);
+        if (e != cudaSuccess) {
+          set_error("tensor-core factor: %s %s", cudaGetErrorString(e),
+                    gls::tc_factor_last_error());
+          return GLS_ERR_CUDA;
+        }
+        pl->launches += 2 + gls::tc_launches(pl->tcf) - tc0;
+      } else {
+        const int64_t N = npad / gls::kT;
+        GLS_CUDA(gls::potrf_trtri_fp64(pl->A, pl->Z, npad, npad, pl->flags, st));
+        pl->launches += 2 + N + 4 * (N - 1);
       }
-    } else {
-      GLS_CUDA(gls::potrf_trtri_fp64(pl->A, pl->Z, npad, npad, pl->flags, st));
-    }
+      return GLS_OK;
+    }));
   }
+  const int64_t tc_before = pl->tc ? gls::tc_launches(pl->tcf) : 0;
   if (p > 1 && XL) {
     GLS_CUDA(cudaMemcpy2DAsync(pl->Wrhs, npad * sizeof(double), XL, ldxl * sizeof(double),
                                n * sizeof(double), p - 1, cudaMemcpyDefault, st));
@@ -658,7 +856,9 @@ gls_status_t gls_solve_block(gls_plan_t pl, const int8_t* XR, int64_t ldxr, int6
   double* bout = (mb == Mem::Device) ? B : pl->bdev[0];
   const int64_t ldout = (mb == Mem::Device) ? ldb : pl->p;
   int32_t* sout = snp_status ? ((ms == Mem::Device) ? snp_status : pl->sdev[0]) : nullptr;
-  GLS_TRY(run_block(pl, xin, ldin, k, bout, ldout, sout));
+  GLS_TRY(replayed(pl, pl->replays,
+                   (KeyHash() << 2u << xin << ldin << k << bout << ldout << sout).h,
+                   [&]() { return run_block(pl, xin, ldin, k, bout, ldout, sout); }));
   const bool sync = (mx != Mem::Device) || (mb != Mem::Device) || (ms != Mem::Device);
   if (mb != Mem::Device)
     GLS_CUDA(cudaMemcpy2DAsync(B, ldb * sizeof(double), bout, pl->p * sizeof(double),
@@ -777,7 +977,9 @@ gls_status_t gls_solve_stream(gls_plan_t pl, const int8_t* XR, int64_t ldxr, int
     double* bout = out_b_host ? pl->bdev[s] : B + s0 * ldb;
     const int64_t ldout = out_b_host ? p : ldb;
     int32_t* sout = snp_status ? (out_s_host ? pl->sdev[s] : snp_status + s0) : nullptr;
-    GLS_TRY(run_block(pl, xin, ldin, kb, bout, ldout, sout));
+    GLS_TRY(replayed(pl, pl->replays,
+                     (KeyHash() << 2u << xin << ldin << kb << bout << ldout << sout).h,
+                     [&]() { return run_block(pl, xin, ldin, kb, bout, ldout, sout); }));
     GLS_CUDA(cudaEventRecord(pl->ev_computed[s], cs));
     if (out_b_host || out_s_host) {
       GLS_CUDA(cudaStreamWaitEvent(pl->d2h, pl->ev_computed[s], 0));
@@ -814,6 +1016,7 @@ struct gls_batch {
   int* flags = nullptr;
   cudaEvent_t ev = nullptr;
   int device = 0;
+  ReplayCache replays;  // rounds captured on the first plan's stream
 };
 
 extern "C" {
@@ -911,28 +1114,41 @@ gls_status_t gls_batch_solve(gls_batch_t b, const int8_t* const* XR, const int64
     GLS_CUDA(cudaEventRecord(b->ev, b->plans[i]->stream));
     GLS_CUDA(cudaStreamWaitEvent(st, b->ev, 0));
   }
-  GLS_CUDA(cudaMemsetAsync(b->flags, 0, sizeof(int) * gls::kFlagCount, st));
-  for (int i = 0; i < count; ++i) {
-    if (k[i] == 0) continue;
-    Timed t(p0, &p0->t_convert);
-    GLS_CUDA(gls::mixed_convert(b->plans[i]->mixed, XR[i], ldxr[i], k[i], st));
-    p0->launches += 1;
-  }
-  {
-    Timed t(p0, &p0->t_trsm);
-    GLS_CUDA(gls::mixed_batch_run(b->mb, k, group, b->flags, st));
-    p0->launches += 1;
-  }
-  for (int i = 0; i < count; ++i) {
-    if (k[i] == 0) continue;
-    gls_plan* pl = b->plans[i];
+  KeyHash key;
+  key << 3u << (uint64_t)group;
+  for (int i = 0; i < count; ++i)
+    key << XR[i] << ldxr[i] << k[i] << B[i] << ldb[i]
+        << (snp_status ? (const void*)snp_status[i] : nullptr);
+  // one round: every conversion, the persistent solve over all scans, every
+  // p x p assembly; captured as one graph when the same round repeats
+  GLS_TRY(replayed(p0, &b->replays, key.h, [&]() -> gls_status_t {
+    GLS_CUDA(cudaMemsetAsync(b->flags, 0, sizeof(int) * gls::kFlagCount, st));
+    {
+      Timed t(p0, &p0->t_convert);
+      for (int i = 0; i < count; ++i) {
+        if (k[i] == 0) continue;
+        GLS_CUDA(gls::mixed_convert(b->plans[i]->mixed, XR[i], ldxr[i], k[i], st));
+        p0->launches += 1;
+      }
+    }
+    {
+      Timed t(p0, &p0->t_trsm);
+      GLS_CUDA(gls::mixed_batch_run(b->mb, k, group, b->flags, st));
+      p0->launches += 1;
+    }
     Timed t(p0, &p0->t_solve);
-    gls::launch_assemble_solve_split(pl->partials + (int64_t)pl->nI * pl->ldp, pl->partials,
-                                     pl->ldp, pl->nI, pl->p, k[i], pl->RTL, pl->zT,
-                                     gls::kTauMixed, B[i], ldb[i],
-                                     snp_status ? snp_status[i] : nullptr, st);
-    p0->launches += 1;
-  }
+    for (int i = 0; i < count; ++i) {
+      if (k[i] == 0) continue;
+      gls_plan* pl = b->plans[i];
+      gls::launch_assemble_solve_split(pl->partials + (int64_t)pl->nI * pl->ldp, pl->partials,
+                                       pl->ldp, pl->nI, pl->p, k[i], pl->RTL, pl->zT,
+                                       gls::kTauMixed, B[i], ldb[i],
+                                       snp_status ? snp_status[i] : nullptr, st);
+      p0->launches += 1;
+    }
+    GLS_CUDA(cudaGetLastError());
+    return GLS_OK;
+  }));
   GLS_CUDA(cudaGetLastError());
   GLS_CUDA(cudaEventRecord(b->ev, st));
   for (int i = 1; i < count; ++i) GLS_CUDA(cudaStreamWaitEvent(b->plans[i]->stream, b->ev, 0));
@@ -951,6 +1167,7 @@ gls_status_t gls_batch_destroy(gls_batch_t b) {
   if (!b) return GLS_OK;
   DeviceGuard guard(b->device);
   if (!b->plans.empty()) cudaStreamSynchronize(b->plans[0]->stream);
+  b->replays.items.clear();
   gls::mixed_batch_free(b->mb);
   cudaFree(b->flags);
   if (b->ev) cudaEventDestroy(b->ev);

@@ -28,6 +28,7 @@ PRECISIONS = {"fp64": 0, "bf16": 1, "fp16": 2}
 GLS_FLAG_NAIVE_SPLIT = 1
 GLS_FLAG_FACTOR_NATIVE = 2
 GLS_FLAG_FACTOR_TENSOR = 4
+GLS_FLAG_EAGER = 8
 
 
 class GlsError(RuntimeError):
