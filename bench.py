@@ -178,7 +178,7 @@ def run_gpu(args, wl, rank, world, torch, dist):
     yd = torch.from_numpy(y).to(dev)
     B = torch.empty((m, p), dtype=torch.float64, device=dev)
     st = torch.empty(m, dtype=torch.int32, device=dev)
-    plan = gls.Plan(n, p, kmax, precision=prec, device=dev.index)
+    plan = gls.Plan(n, p, kmax, precision=prec, device=dev.index, flags=launch_flags(args, gls))
     stream = torch.cuda.ExternalStream(plan.stream, device=dev)
 
     def step():
@@ -209,8 +209,10 @@ def run_gpu(args, wl, rank, world, torch, dist):
     nan = int(torch.isnan(B).any().item())
     res = dict(time=t, stats=stats, clocks=clk.summary(), bad_status=bad, nan=nan)
 
-    # end to end through the public API with host buffers (pinned)
+    # end to end through the public API with host buffers (pinned); per-kernel
+    # timing is instrumentation a user would not run with, so it is off here
     if not args.skip_e2e:
+        plan.set_timing(False)
         XRh = torch.empty((m, n), dtype=torch.int8, pin_memory=True)
         XRh.copy_(XR)
         Mh = torch.from_numpy(np.ascontiguousarray(M.T)).pin_memory().t()
@@ -263,7 +265,7 @@ def run_factor_only(args, wl, torch):
     XLd = torch.from_numpy(np.ascontiguousarray(XL.T)).cuda().t()
     yd = torch.from_numpy(y).cuda()
     flags = gls.GLS_FLAG_FACTOR_NATIVE if (args.factor_native and prec != "fp64") else 0
-    plan = gls.Plan(n, p, 1024, precision=prec, flags=flags)
+    plan = gls.Plan(n, p, 1024, precision=prec, flags=flags | launch_flags(args, gls))
     for _ in range(args.warmup):
         plan.factor(Md, XLd, yd)
     plan.synchronize()
@@ -436,7 +438,7 @@ def run_batch_workload(args, bw, torch):
         XLd = torch.from_numpy(np.ascontiguousarray(XL.T)).cuda().t()
         yd = torch.from_numpy(y).cuda()
         kb = autotune.choose_block(m, bw["block"])
-        plans.append(gls.Plan(n, p, kb, precision=bw["precision"]))
+        plans.append(gls.Plan(n, p, kb, precision=bw["precision"], flags=launch_flags(args, gls)))
         inputs.append((Md, XLd, yd, XR))
         outs.append((torch.empty((m, p), dtype=torch.float64, device="cuda"),
                      torch.empty(m, dtype=torch.int32, device="cuda")))
@@ -523,7 +525,9 @@ def run_batch_workload(args, bw, torch):
                    "n_range": bw["n"], "p_range": bw["p"], "m_range": bw["m"],
                    "m_divisor": bw.get("m_div", 1),
                    "rounds": rounds, "group_autotuned": group,
-                   "group_trials_s": tune_times, "parallelism": "replicas1"},
+                   "group_trials_s": tune_times,
+                   "launch": "eager" if args.eager else "CUDA-graph replay of repeated sequences",
+                   "parallelism": "replicas1"},
         "gpu_launches": None,
         "phase_ms_per_step": {"solve_kernels": st0["trsm_ms"] / args.steps,
                               "convert": st0["convert_ms"] / args.steps,
@@ -607,10 +611,15 @@ def run_serve_workload(args, sw, torch):
     return line
 
 
+def launch_flags(args, gls):
+    return gls.GLS_FLAG_EAGER if getattr(args, "eager", False) else 0
+
+
 def config_for(wl, args):
     return {"workload": args.workload, "n": wl["n"], "p": wl["p"], "m": wl["m"], "h": wl["h"],
             "precision": wl["precision"], "block_snps": wl["block"],
             "l2": "inputs larger than L2 (int8 genotypes n*m bytes)",
+            "launch": "eager" if args.eager else "CUDA-graph replay of repeated sequences",
             "parallelism": f"replicas{args.gpus}"}
 
 
@@ -646,6 +655,8 @@ def main():
                     help="time gls_factor alone on the workload's M (setup phase, Alg. 5 lines 1-6)")
     ap.add_argument("--factor-native", action="store_true",
                     help="with --factor-only on a mixed workload: the binary64 CUDA-core factor")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch every kernel directly (no CUDA-graph replay of repeated sequences)")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
