@@ -1,9 +1,11 @@
 """Autotuner for the batched mixed-precision solve.
 
-The tunable knobs do not change results (each work item's arithmetic is the
-same whichever CTA runs it), only speed:
-  * group  -- row blocks per L2 rasterization group of a launch;
+Two knobs do not change results (each work item's arithmetic is the same
+whichever CTA runs it), only speed:
+  * group  -- row-block pairs per L2 rasterization group of a launch;
   * block  -- SNPs per plan per launch (bounded by max_block_snps).
+One trades accuracy for speed and is gated by a measured error:
+  * split  -- 16-bit slices of L^{-1} (2 or 3), ``tune_split``.
 ``tune_group`` times each candidate group on the caller's real launch with CUDA
 events on the launching stream and keeps the fastest; results are cached in a
 small JSON file keyed by device name and a signature of the batch, so later
@@ -101,3 +103,40 @@ def choose_block(m: int, kmax: int, rounds_hint: int = 0) -> int:
         return max(m, 1)
     rounds = max(rounds_hint, -(-m // kmax))
     return -(-m // rounds)
+
+
+def tune_split(n, p, precision, M, XL, y, XR_sample, tol: float = 1e-6, margin: float = 8.0,
+               device: int = 0) -> tuple[int, dict]:
+    """Operand split of L^{-1} (2 or 3 16-bit slices) for one scan of the mixed
+    paths: the 2-slice split does two thirds of the tensor work, and is chosen
+    only when its b_i on a sample of the scan's SNPs stay within tol / margin
+    of the 3-slice b_i (relative 2-norm per SNP).  The 3-slice error is far
+    below the 2-slice one (BF16: about 1/100 of it; FP16: about 1/10), so
+    that difference bounds the 2-slice error to within the margin.  The
+    caller's tolerance is for the whole scan; the margin covers SNPs outside
+    the sample.  Arrays are device tensors in the layouts of ``gls.Plan``
+    (M and XL column-major, XR_sample n x k column-major); returns
+    (split_terms, {"err_2_vs_3": max relative difference, "threshold": ...}).
+    """
+    import numpy as np
+    import torch
+    from . import gls
+    k = XR_sample.shape[1]
+    outs = {}
+    for S in (3, 2):
+        with gls.Plan(n, p, k, precision=precision, device=device, split_terms=S) as pl:
+            pl.factor(M, XL, y)
+            B = torch.empty((k, p), dtype=torch.float64, device=XR_sample.device)
+            st = torch.empty(k, dtype=torch.int32, device=XR_sample.device)
+            pl.solve_block(XR_sample, B.t(), st, k=k)
+            pl.synchronize()
+            outs[S] = (B.cpu().numpy(), st.cpu().numpy())
+    (B3, s3), (B2, s2) = outs[3], outs[2]
+    ok = (s3 == 0) & (s2 == 0)
+    num = np.linalg.norm(B2[ok] - B3[ok], axis=1)
+    den = np.linalg.norm(B3[ok], axis=1)
+    err = float((num / np.where(den > 0, den, 1.0)).max()) if ok.any() else float("inf")
+    thr = tol / margin
+    same_status = bool(np.array_equal(s2, s3))
+    S = 2 if (err <= thr and same_status) else 3
+    return S, {"err_2_vs_3": err, "threshold": thr, "status_agree": same_status}
