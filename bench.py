@@ -239,21 +239,33 @@ def run_gpu(args, wl, rank, world, torch, dist):
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
+        marks = [t0]
         for _ in range(args.steps):
             e2e_step()
-        te = time.perf_counter() - t0
+            marks.append(time.perf_counter())
+        te = marks[-1] - t0
         res["e2e_time"] = te
+        res["e2e_step_ms"] = [round((b - a) * 1e3, 2) for a, b in zip(marks, marks[1:])]
         # context for the end-to-end figure: this box's pinned host -> device copy rate
+        # ... over every block of the pinned genotype buffer (placement of its
+        # pages can differ along the buffer), best of 3 per block
         probe = torch.empty((min(m, kmax), n), dtype=torch.int8, device=dev)
-        best = float("inf")
-        for _ in range(3):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            probe.copy_(XRh[:probe.shape[0]], non_blocking=True)
-            e1.record()
-            e1.synchronize()
-            best = min(best, e0.elapsed_time(e1) / 1e3)
-        res["h2d_gbps"] = probe.numel() / best / 1e9
+        rates = []
+        for s0 in range(0, m, kmax):
+            k = min(kmax, m - s0)
+            best = float("inf")
+            for _ in range(3):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                probe[:k].copy_(XRh[s0:s0 + k], non_blocking=True)
+                e1.record()
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+            rates.append(k * n / best / 1e9)
+        res["h2d_gbps"] = rates[0]
+        res["h2d_gbps_blocks"] = {"min": min(rates), "median": float(np.median(rates)),
+                                  "max": max(rates), "blocks": len(rates)}
         del probe
         res["e2e_h2d"] = n * n * 8 + n * (p - 1) * 8 + n * 8 + n * m
         res["e2e_d2h"] = p * m * 8 + 4 * m
@@ -785,7 +797,9 @@ def main():
     if e2e_max:
         line["e2e"] = {"value": whole_job_rate(world, m, K, e2e_max), "unit": UNIT,
                        "h2d_bytes_per_step": res["e2e_h2d"], "d2h_bytes_per_step": res["e2e_d2h"],
-                       "h2d_gbps_measured": res.get("h2d_gbps")}
+                       "h2d_gbps_measured": res.get("h2d_gbps"),
+                       "h2d_gbps_per_block": res.get("h2d_gbps_blocks"),
+                       "step_ms": res.get("e2e_step_ms")}
     if not args.skip_fp64 and wl["precision"] != "fp64":
         try:
             line["fp64"] = fp64_sample(wl, torch)

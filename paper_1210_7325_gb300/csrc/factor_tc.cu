@@ -35,8 +35,9 @@
 //     [A11    ]      L11 Z11  = factor(A11)
 //     [A21 A22]  ->  L21      = A21 Z11^T           (L21 = A21 L11^{-T})
 //                    A22     -= L21 L21^T           (trailing update)
+//                    T        = L21 Z11             (kept in the Z21 block)
 //                    L22 Z22  = factor(A22)
-//                    Z21      = -Z22 (L21 Z11)      (block of L^{-1})
+//                    Z21      = -Z22 T              (block of L^{-1})
 // with the 64 x 64 leaves factored and inverted in binary64 (factor_fp64.cu).
 // Every product has a long inner dimension, so the binary64 epilogue runs once
 // per output element of each product rather than once per 64-deep update.
@@ -411,6 +412,82 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 1) tmem_dealloc(tmem, Sh::kTmemCols);
 }
 
+// ---------------------------------------------------------------- small nodes
+// Recursion nodes of at most kSmallNode rows hold few multiply-adds (n1 n2
+// (n1 + n2) in all), so on the tensor path their cost is the latency of a
+// slicing and a product launch each.  Here each product is one binary64
+// launch spread over the SMs, one CTA per output row (column), with the
+// usual binary64 rounding of a dot product.  A CTA first stages the row
+// (column) of the operand that it overwrites in shared memory, which makes
+// the in-place forms safe: no other CTA reads that row (column).
+constexpr int kSmallNode = 384;
+constexpr int kSmallThreads = 128;
+
+enum SmallMode : int {
+  kSmL21 = 0,   // L21 = A21 Z11^T in place: b(k, j) = Z11(j, k), k <= j
+  kSmSyrk = 1,  // A22 -= L21 L21^T, lower: b(k, j) = L21(j, k), j <= i
+  kSmT = 2      // T = L21 Z11 into the Z21 block: b(k, j) = Z11(k, j), k >= j
+};
+
+// C(i, j) (= or -=) sum_k a(i, k) b(k, j), one row i per CTA, a(i, k) =
+// a[i + k ld] staged in shared memory; b as the mode says, from B.  Four
+// partial sums break the dependent chain of binary64 FMAs.
+__global__ void __launch_bounds__(kSmallThreads)
+    small_rows_kernel(const double* a, double* C, const double* B, int64_t ld, int N, int K,
+                      int mode, const int* flags) {
+  if (*(volatile const int*)&flags[kFlagPotrf] != 0) return;
+  __shared__ double row[kSmallNode];
+  const int i = blockIdx.x;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) row[k] = a[i + (int64_t)k * ld];
+  __syncthreads();
+  const int jend = mode == kSmSyrk ? min(N, i + 1) : N;
+  for (int j = threadIdx.x; j < jend; j += blockDim.x) {
+    const int k0 = mode == kSmT ? j : 0;
+    const int k1 = mode == kSmL21 ? min(K, j + 1) : K;
+    // b(k, j) = B[j + k ld] (L21, Syrk) or B[k + j ld] (T)
+    const int64_t sk = mode == kSmT ? 1 : ld, sj = mode == kSmT ? ld : 1;
+    const double* bj = B + (int64_t)j * sj;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int k = k0;
+    for (; k + 3 < k1; k += 4) {
+      s0 = fma(row[k], bj[k * sk], s0);
+      s1 = fma(row[k + 1], bj[(k + 1) * sk], s1);
+      s2 = fma(row[k + 2], bj[(k + 2) * sk], s2);
+      s3 = fma(row[k + 3], bj[(k + 3) * sk], s3);
+    }
+    for (; k < k1; ++k) s0 = fma(row[k], bj[k * sk], s0);
+    const double acc = (s0 + s1) + (s2 + s3);
+    double* c = C + i + (int64_t)j * ld;
+    if (mode == kSmSyrk) *c -= acc;
+    else *c = acc;
+  }
+}
+
+// Z21 = -Z22 T with T held in the Z21 block (n2 x n1): one column j per CTA,
+// staged before it is overwritten; Z22 lower, so row i needs k <= i.
+__global__ void __launch_bounds__(kSmallThreads)
+    small_z21_kernel(const double* __restrict__ Z22, double* Z21, int64_t ld, int n2,
+                     const int* flags) {
+  if (*(volatile const int*)&flags[kFlagPotrf] != 0) return;
+  __shared__ double col[kSmallNode];
+  const int j = blockIdx.x;
+  double* zc = Z21 + (int64_t)j * ld;
+  for (int k = threadIdx.x; k < n2; k += blockDim.x) col[k] = zc[k];
+  __syncthreads();
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int k = 0;
+    for (; k + 3 <= i; k += 4) {
+      s0 = fma(Z22[i + (int64_t)k * ld], col[k], s0);
+      s1 = fma(Z22[i + (int64_t)(k + 1) * ld], col[k + 1], s1);
+      s2 = fma(Z22[i + (int64_t)(k + 2) * ld], col[k + 2], s2);
+      s3 = fma(Z22[i + (int64_t)(k + 3) * ld], col[k + 3], s3);
+    }
+    for (; k <= i; ++k) s0 = fma(Z22[i + (int64_t)k * ld], col[k], s0);
+    zc[i] = -((s0 + s1) + (s2 + s3));
+  }
+}
+
 // ---------------------------------------------------------------- slicing
 // The kS slices of x relative to 2^E (see the file header), as BF16 bits.
 __device__ __forceinline__ void slice_value(double x, int E, uint16_t (&s)[kS]) {
@@ -643,7 +720,6 @@ struct TcFactor {
   int* eB = nullptr;          // npad
   unsigned long long* maxA = nullptr;  // npad: row maxima of split operands
   unsigned long long* maxB = nullptr;
-  double* T = nullptr;        // half x half
   int num_sms = 1;
   int64_t launches = 0;       // kernels enqueued so far
 };
@@ -728,12 +804,6 @@ cudaError_t slice2(TcFactor* w, const SliceJob& a, const SliceJob& b, const int*
   return cudaGetLastError();
 }
 
-cudaError_t slice1(TcFactor* w, const SliceJob& a, const int* flags, cudaStream_t st) {
-  SliceJob none = a;
-  none.nblocks = 0;
-  return slice2(w, a, none, flags, st);
-}
-
 template <int BN>
 cudaError_t launch_gemm(TcFactor* w, const Operand& A, const Operand& B, OzParams q,
                         cudaStream_t st);
@@ -816,6 +886,21 @@ cudaError_t rec(TcFactor* w, double* A, double* Z, int64_t ld, int64_t r0, int64
   double* Z11 = Z + r0 + r0 * ld;
   double* Z21 = Z + (r0 + n1) + r0 * ld;
   double* Z22 = Z + (r0 + n1) + (r0 + n1) * ld;
+  if (n <= kSmallNode) {
+    const dim3 rows((unsigned)n2), cols((unsigned)n1);
+    small_rows_kernel<<<rows, kSmallThreads, 0, st>>>(A21, A21, Z11, ld, (int)n1, (int)n1,
+                                                      kSmL21, flags);
+    small_rows_kernel<<<rows, kSmallThreads, 0, st>>>(A21, A22, A21, ld, (int)n2, (int)n1,
+                                                      kSmSyrk, flags);
+    small_rows_kernel<<<rows, kSmallThreads, 0, st>>>(A21, Z21, Z11, ld, (int)n1, (int)n1, kSmT,
+                                                      flags);
+    w->launches += 3;
+    TC_TRY(cudaGetLastError());
+    TC_TRY(rec(w, A, Z, ld, r0 + n1, n2, flags, st));
+    small_z21_kernel<<<cols, kSmallThreads, 0, st>>>(Z22, Z21, ld, (int)n2, flags);
+    ++w->launches;
+    return cudaGetLastError();
+  }
   const Operand SA1{w->SA, w->eA, n2, round_up(n1, kKAlign)};
   const Operand SB1{w->SB, w->eB, n1, round_up(n1, kKAlign)};
   // L21 = A21 Z11^T (Z11 lower: column block J needs k < (J+1) BN)
@@ -823,21 +908,25 @@ cudaError_t rec(TcFactor* w, double* A, double* Z, int64_t ld, int64_t r0, int64
                 job(Z11, ld, n1, n1, true, w->SB, w->eB, w->maxB), flags, st));
   TC_TRY(gemm(w, SA1, SB1, A21, ld, (int)n2, (int)n1, (int)n1, kKLeJ, 0, false, 0, false, 0,
               flags, st));
-  // A22 -= L21 L21^T (lower triangle)
-  TC_TRY(slice1(w, job(A21, ld, n2, n1, true, w->SA, w->eA, w->maxA), flags, st));
-  TC_TRY(gemm(w, SA1, SA1, A22, ld, (int)n2, (int)n2, (int)n1, kKFull, 0, true, 1, true, 0, flags,
-              st));
-  TC_TRY(rec(w, A, Z, ld, r0 + n1, n2, flags, st));
-  // T = L21 Z11 (Z11 lower: column j needs k >= j)
+  // One slicing of L21 serves both the trailing update and T = L21 Z11, which
+  // does not depend on the factor of A22 and is formed before it.  T is kept
+  // in the Z21 block (zero until Z21 = -Z22 T overwrites it below); the
+  // recursion on A22 touches only A22 and Z22.
   TC_TRY(slice2(w, job(A21, ld, n2, n1, true, w->SA, w->eA, w->maxA),
                 job(Z11, ld, n1, n1, false, w->SB, w->eB, w->maxB), flags, st));
-  TC_TRY(gemm(w, SA1, SB1, w->T, n2, (int)n2, (int)n1, (int)n1, kKGeJ, 0, false, 0, false, 0,
+  // A22 -= L21 L21^T (lower triangle)
+  TC_TRY(gemm(w, SA1, SA1, A22, ld, (int)n2, (int)n2, (int)n1, kKFull, 0, true, 1, true, 0, flags,
+              st));
+  // T = L21 Z11 (Z11 lower: column j needs k >= j)
+  TC_TRY(gemm(w, SA1, SB1, Z21, ld, (int)n2, (int)n1, (int)n1, kKGeJ, 0, false, 0, false, 0,
               flags, st));
-  // Z21 = -Z22 T (Z22 lower: row block I needs k < (I+1) 128)
+  TC_TRY(rec(w, A, Z, ld, r0 + n1, n2, flags, st));
+  // Z21 = -Z22 T (Z22 lower: row block I needs k < (I+1) 128); T's slices are
+  // taken before the product overwrites it
   const Operand SA2{w->SA, w->eA, n2, round_up(n2, kKAlign)};
   const Operand SB2{w->SB, w->eB, n1, round_up(n2, kKAlign)};
   TC_TRY(slice2(w, job(Z22, ld, n2, n2, true, w->SA, w->eA, w->maxA),
-                job(w->T, n2, n1, n2, false, w->SB, w->eB, w->maxB), flags, st));
+                job(Z21, ld, n1, n2, false, w->SB, w->eB, w->maxB), flags, st));
   TC_TRY(gemm(w, SA2, SB2, Z21, ld, (int)n2, (int)n1, (int)n2, kKLeI, 0, true, 0, false, 0, flags,
               st));
   return cudaSuccess;
@@ -853,8 +942,7 @@ int64_t panel_rows(const TcFactor* w, int64_t K) {
 }  // namespace
 
 size_t tc_factor_bytes(int64_t npad) {
-  const int64_t h = half_of(npad);
-  return 2 * (size_t)kS * plane_cap(npad) * 2 + 2 * (size_t)npad * (4 + 8) + (size_t)h * h * 8;
+  return 2 * (size_t)kS * plane_cap(npad) * 2 + 2 * (size_t)npad * (4 + 8);
 }
 
 const char* tc_factor_last_error() { return g_err.c_str(); }
@@ -867,7 +955,6 @@ void tc_factor_free(TcFactor* w) {
   cudaFree(w->eB);
   cudaFree(w->maxA);
   cudaFree(w->maxB);
-  cudaFree(w->T);
   delete w;
 }
 
@@ -889,8 +976,7 @@ gls_status_t tc_factor_create(TcFactor** out, int64_t npad) {
       cudaMalloc(&w->eA, (size_t)npad * 4) != cudaSuccess ||
       cudaMalloc(&w->eB, (size_t)npad * 4) != cudaSuccess ||
       cudaMalloc(&w->maxA, (size_t)npad * 8) != cudaSuccess ||
-      cudaMalloc(&w->maxB, (size_t)npad * 8) != cudaSuccess ||
-      cudaMalloc(&w->T, (size_t)w->half * w->half * 8) != cudaSuccess) {
+      cudaMalloc(&w->maxB, (size_t)npad * 8) != cudaSuccess) {
     cudaGetLastError();
     tc_factor_free(w);
     g_err = "cudaMalloc of the tensor-core factor workspace failed";
