@@ -70,15 +70,18 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
 //
 // Right-looking over the 64 columns, the Cholesky and the inverse in the same
 // sweep.  At column j the first 64 threads scale column j of L and row j of
-// W = L^{-1} by r_j = 1/L_jj (one element each); then warps 1-7 apply the
+// W = L^{-1} by r_j = 1/L_jj (one element each); then warps 1-15 apply the
 // rank-1 updates S_il -= L_ij L_lj (j < l <= i, except S_{j+1,j+1}) and
 // W_ic -= L_ij W_jc (c <= j < i), numbered densely so that every lane of every
 // binary64 instruction does useful work, while thread 0 forms the next pivot
 // d_{j+1} = S_{j+1,j+1} - L_{j+1,j}^2 and r_{j+1}.
 // Dependent binary64 operations take about 64 cycles each on this part, so the
 // pivot's chain (about 700 cycles) runs beside the column's update instead of
-// before it.
-__global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ A,
+// before it.  The column loop is latency-bound, so the CTA has 16 warps: the
+// more warps share a column's update, the more of its latency they hide.
+constexpr int kLeafThreads = 512;
+
+__global__ void __launch_bounds__(kLeafThreads) potrf_diag_kernel(double* __restrict__ A,
                                                          double* __restrict__ Z, int64_t ld,
                                                          int64_t k0, int* flags) {
   extern __shared__ double sm[];
@@ -110,7 +113,7 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ A,
     }
   }
   __syncthreads();
-  constexpr int kUpd = 256 - 32;  // threads of warps 1-7
+  constexpr int kUpd = kLeafThreads - 32;  // threads of warps 1-15
   for (int j = 0; j < kT; ++j) {
     if (fail) break;
     // column j of L and row j of W: one element per thread of the first 64
@@ -430,7 +433,7 @@ cudaError_t potrf_trtri_fp64(double* A, double* Z, int64_t ld, int64_t npad, int
   if (e != cudaSuccess) return e;
   const int N = (int)(npad / kT);
   for (int K = 0; K < N; ++K) {
-    potrf_diag_kernel<<<1, 256, kTileSmem, st>>>(A, Z, ld, (int64_t)K * kT, flags);
+    potrf_diag_kernel<<<1, kLeafThreads, kTileSmem, st>>>(A, Z, ld, (int64_t)K * kT, flags);
     const int64_t m = N - K - 1;
     if (m > 0) {
       tile_gemm_kernel<<<(unsigned)m, 256, kTileSmem, st>>>(A, Z, ld, K, kPanel, flags);
@@ -451,7 +454,7 @@ cudaError_t potrf_trtri_fp64(double* A, double* Z, int64_t ld, int64_t npad, int
 void launch_potrf_diag64(double* A, double* Z, int64_t ld, int64_t k0, int* flags,
                          cudaStream_t st) {
   if (set_attrs() != cudaSuccess) return;
-  potrf_diag_kernel<<<1, 256, kTileSmem, st>>>(A, Z, ld, k0, flags);
+  potrf_diag_kernel<<<1, kLeafThreads, kTileSmem, st>>>(A, Z, ld, k0, flags);
 }
 
 void launch_whiten(const double* Z, int64_t ldz, int64_t n, int64_t npad, const double* rhs,
