@@ -246,6 +246,18 @@ def run_gpu(args, wl, rank, world, torch, dist):
         te = marks[-1] - t0
         res["e2e_time"] = te
         res["e2e_step_ms"] = [round((b - a) * 1e3, 2) for a, b in zip(marks, marks[1:])]
+        # one more step with per-kernel device timing (not in the figure): does
+        # the step's time go to the kernels or to waiting on the host link?
+        plan.set_timing(True)
+        t1 = time.perf_counter()
+        e2e_step()
+        t2 = time.perf_counter()
+        sd = plan.stats()
+        plan.set_timing(False)
+        res["e2e_diag"] = {"wall_ms": round((t2 - t1) * 1e3, 2),
+                           "factor_ms": round(sd["factor_ms"], 2),
+                           "solve_kernels_ms": round(sd["trsm_ms"] + sd["convert_ms"]
+                                                     + sd["solve_ms"], 2)}
         # context for the end-to-end figure: this box's pinned host -> device copy rate
         # ... over every block of the pinned genotype buffer (placement of its
         # pages can differ along the buffer), best of 3 per block
@@ -263,6 +275,19 @@ def run_gpu(args, wl, rank, world, torch, dist):
                 e1.synchronize()
                 best = min(best, e0.elapsed_time(e1) / 1e3)
             rates.append(k * n / best / 1e9)
+        # and the device -> host return of b into the pinned output buffer
+        bdev = torch.empty((min(m, kmax), p), dtype=torch.float64, device=dev)
+        best = float("inf")
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            Bh[:bdev.shape[0]].copy_(bdev, non_blocking=True)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        res["d2h_gbps"] = bdev.numel() * 8 / best / 1e9
+        del bdev
         res["h2d_gbps"] = rates[0]
         res["h2d_gbps_blocks"] = {"min": min(rates), "median": float(np.median(rates)),
                                   "max": max(rates), "blocks": len(rates)}
@@ -799,7 +824,9 @@ def main():
                        "h2d_bytes_per_step": res["e2e_h2d"], "d2h_bytes_per_step": res["e2e_d2h"],
                        "h2d_gbps_measured": res.get("h2d_gbps"),
                        "h2d_gbps_per_block": res.get("h2d_gbps_blocks"),
-                       "step_ms": res.get("e2e_step_ms")}
+                       "d2h_gbps_measured": res.get("d2h_gbps"),
+                       "step_ms": res.get("e2e_step_ms"),
+                       "diagnostic_step": res.get("e2e_diag")}
     if not args.skip_fp64 and wl["precision"] != "fp64":
         try:
             line["fp64"] = fp64_sample(wl, torch)
