@@ -20,7 +20,8 @@ void mixed_free(MixedState* ms);
 const char* mixed_last_error();
 
 // After the FP64 setup: splits the off-diagonal part of Z = L^{-1} into
-// tensor-core slices and keeps its FP64 diagonal blocks (only when new_factor),
+// tensor-core slices and keeps its diagonal blocks as exact FP32 splits
+// (integer part and low part per entry; only when new_factor),
 // then forms W = Z^T [X~_L | y~] = M^{-1} [X_L | y] in binary64 and splits W^T
 // into the extra row block of the A operand.
 // With w_ready, W has already been written to mixed_w_buffer(ms) by the caller.
@@ -39,7 +40,7 @@ cudaError_t mixed_trsm_gram(MixedState* ms, const int8_t* xr, int64_t ldxr, int6
                             double* Pbr, double* Glin, int64_t ldp, int* flags,
                             cudaStream_t st);
 
-// Size of the FP64 diagonal blocks kept out of the tensor-core slices.
+// Size of the diagonal blocks kept out of the tensor-core slices.
 int mixed_diag_block(const MixedState* ms);
 int mixed_split_terms(const MixedState* ms);
 bool mixed_is_bf16(const MixedState* ms);

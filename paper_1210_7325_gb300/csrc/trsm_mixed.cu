@@ -53,7 +53,7 @@
 //               not the tensor rate, is what limits the 128 x 128 shape
 //   warps 2-9   epilogue, one SNP per thread (its TMEM lane), two warps per lane
 //               quarter, each taking one of the item's two 128-row blocks:
-//               tcgen05.ld of 32 rows at a time, the FP64 4 x 4 diagonal blocks
+//               tcgen05.ld of 32 rows at a time, the 4 x 4 diagonal blocks (FP32 split)
 //               from the SNP's own genotypes, and the S_BR sum in registers
 // Work items (row-block pair I = blocks 2I and 2I+1, SNP tile J), I = 0..nP
 // (nP = ceil(nI / 2); I = nP is the W^T block, and an odd last pair holds one
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
 #pragma unroll
         for (int g4 = 0; g4 < 8; ++g4) {
-          // rows 4*g4 .. 4*g4+3 of this chunk form one FP64 diagonal block
+          // rows 4*g4 .. 4*g4+3 of this chunk form one diagonal block
           const uint4 v4 = g4 < 4 ? v0 : v1;
           const uint32_t wv = ((g4 & 3) == 0 ? v4.x : (g4 & 3) == 1 ? v4.y
                              : (g4 & 3) == 2 ? v4.z : v4.w) ^ 0x80808080u;
