@@ -78,7 +78,9 @@ typedef enum {
  * as a CUDA graph the second time it is seen and replayed from then on (one
  * graph launch instead of up to ~1500 kernel launches for the factor).  Only
  * plans that own their stream (desc.stream == NULL) use graphs; results are
- * the same either way.  For a batch the flag of its first plan decides. */
+ * the same either way.  For a batch the flag of its first plan decides.
+ * While such a call runs, nothing else may enqueue work on the plan's stream
+ * (gls_plan_stream) from another thread: a capture would take it in. */
 #define GLS_FLAG_EAGER 8u
 
 /* Plan description.  Zero-initialise and fill the fields that matter. */
