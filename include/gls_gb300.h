@@ -174,7 +174,7 @@ gls_status_t gls_batch_create(const gls_plan_t* plans, int32_t nplans, gls_batch
  * XR[i] (device memory, n_i x k[i] int8, ldxr[i] >= n_i) into B[i] (device,
  * p_i x k[i], ldb[i] >= p_i) and snp_status[i] (device, may be NULL; the array
  * snp_status itself may be NULL).  0 <= k[i] <= max_block_snps of plan i.
- * group: pairs of 128-row blocks per L2 rasterization group of the launch (0 = default 4;
+ * group: pairs of 128-row blocks per L2 rasterization group of the launch (0 = default 3;
  * a tuning knob only, results do not depend on it).  Runs on the first plan's
  * stream after the work already queued on every plan's stream, and returns
  * when the launch has finished.  Errors: INVALID_ARG, STATE, CUDA, TIMEOUT.

@@ -17,7 +17,7 @@ import json
 import os
 import threading
 
-DEFAULT_GROUPS = (1, 2, 4, 8)
+DEFAULT_GROUPS = (1, 2, 3, 4, 6, 8)
 _lock = threading.Lock()
 
 

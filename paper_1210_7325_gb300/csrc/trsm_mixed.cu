@@ -107,7 +107,7 @@ constexpr int kMaxDynSmem = 232448;     // 227 KB
 constexpr int kDiag = 4;                // nd: diagonal block edge
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // bounded waits give up after 1 s
 constexpr uint64_t kDrainLimitNs = 100000000ull;
-constexpr int kDefaultGroup = 4;        // row-block pairs per rasterization group
+constexpr int kDefaultGroup = 3;        // row-block pairs per rasterization group
 
 thread_local std::string g_err;
 
