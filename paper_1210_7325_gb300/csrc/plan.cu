@@ -455,6 +455,16 @@ void free_plan(gls_plan* pl) {
   delete pl;
 }
 
+// A pitched copy, issued as one contiguous copy when both pitches equal the
+// row width (the usual case for X_R blocks and b): one large transfer for the
+// copy engine instead of a row-by-row description.
+cudaError_t copy2d(void* dst, size_t dpitch, const void* src, size_t spitch, size_t width,
+                   size_t height, cudaMemcpyKind kind, cudaStream_t st) {
+  if (dpitch == width && spitch == width)
+    return cudaMemcpyAsync(dst, src, width * height, kind, st);
+  return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, height, kind, st);
+}
+
 template <class T>
 gls_status_t dev_alloc(T** p, size_t count) {
   if (cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
@@ -714,7 +724,7 @@ gls_status_t gls_factor(gls_plan_t pl, const double* M, int64_t ldm, const doubl
   GLS_CUDA(cudaMemsetAsync(pl->flags, 0, sizeof(int) * gls::kFlagCount, st));
   if (M) {
     pl->has_factor = false;
-    GLS_CUDA(cudaMemcpy2DAsync(pl->A, npad * sizeof(double), M, ldm * sizeof(double),
+    GLS_CUDA(copy2d(pl->A, npad * sizeof(double), M, ldm * sizeof(double),
                                n * sizeof(double), n, cudaMemcpyDefault, st));
     // from here on the factor touches plan buffers only: one graph per plan
     GLS_TRY(replayed(pl, pl->replays, (KeyHash() << 1u).h, [&]() -> gls_status_t {
@@ -739,7 +749,7 @@ gls_status_t gls_factor(gls_plan_t pl, const double* M, int64_t ldm, const doubl
   }
   const int64_t tc_before = pl->tc ? gls::tc_launches(pl->tcf) : 0;
   if (p > 1 && XL) {
-    GLS_CUDA(cudaMemcpy2DAsync(pl->Wrhs, npad * sizeof(double), XL, ldxl * sizeof(double),
+    GLS_CUDA(copy2d(pl->Wrhs, npad * sizeof(double), XL, ldxl * sizeof(double),
                                n * sizeof(double), p - 1, cudaMemcpyDefault, st));
     pl->has_xl = true;
   }
@@ -813,10 +823,10 @@ gls_status_t gls_plan_get_factor(gls_plan_t pl, double* L, int64_t ldl, double* 
   DeviceGuard guard(pl->device);
   const int64_t n = pl->n, npad = pl->npad;
   if (L)
-    GLS_CUDA(cudaMemcpy2DAsync(L, ldl * sizeof(double), pl->A, npad * sizeof(double),
+    GLS_CUDA(copy2d(L, ldl * sizeof(double), pl->A, npad * sizeof(double),
                                n * sizeof(double), n, cudaMemcpyDefault, pl->stream));
   if (Zinv)
-    GLS_CUDA(cudaMemcpy2DAsync(Zinv, ldz * sizeof(double), pl->Z, npad * sizeof(double),
+    GLS_CUDA(copy2d(Zinv, ldz * sizeof(double), pl->Z, npad * sizeof(double),
                                n * sizeof(double), n, cudaMemcpyDefault, pl->stream));
   GLS_CUDA(cudaStreamSynchronize(pl->stream));
   return GLS_OK;
@@ -849,7 +859,7 @@ gls_status_t gls_solve_block(gls_plan_t pl, const int8_t* XR, int64_t ldxr, int6
   const int8_t* xin = XR;
   int64_t ldin = ldxr;
   if (mx != Mem::Device) {
-    GLS_CUDA(cudaMemcpy2DAsync(pl->xr[0], pl->n, XR, ldxr, pl->n, k, cudaMemcpyHostToDevice, st));
+    GLS_CUDA(copy2d(pl->xr[0], pl->n, XR, ldxr, pl->n, k, cudaMemcpyHostToDevice, st));
     xin = pl->xr[0];
     ldin = pl->n;
   }
@@ -861,7 +871,7 @@ gls_status_t gls_solve_block(gls_plan_t pl, const int8_t* XR, int64_t ldxr, int6
                    [&]() { return run_block(pl, xin, ldin, k, bout, ldout, sout); }));
   const bool sync = (mx != Mem::Device) || (mb != Mem::Device) || (ms != Mem::Device);
   if (mb != Mem::Device)
-    GLS_CUDA(cudaMemcpy2DAsync(B, ldb * sizeof(double), bout, pl->p * sizeof(double),
+    GLS_CUDA(copy2d(B, ldb * sizeof(double), bout, pl->p * sizeof(double),
                                pl->p * sizeof(double), k, cudaMemcpyDeviceToHost, st));
   if (snp_status && ms != Mem::Device)
     GLS_CUDA(cudaMemcpyAsync(snp_status, sout, k * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -939,7 +949,7 @@ gls_status_t gls_solve_stream(gls_plan_t pl, const int8_t* XR, int64_t ldxr, int
     // device buffer s is free once the compute of block jb-2 is done
     GLS_CUDA(cudaStreamWaitEvent(pl->h2d, pl->ev_computed[s], 0));
     if (!pageable_in) {
-      GLS_CUDA(cudaMemcpy2DAsync(pl->xr[s], n, XR + s0 * ldxr, ldxr, n, kb,
+      GLS_CUDA(copy2d(pl->xr[s], n, XR + s0 * ldxr, ldxr, n, kb,
                                  cudaMemcpyHostToDevice, pl->h2d));
     } else {
       GLS_CUDA(cudaEventSynchronize(pl->ev_staged[s]));  // pinned staging s is free
@@ -985,7 +995,7 @@ gls_status_t gls_solve_stream(gls_plan_t pl, const int8_t* XR, int64_t ldxr, int
       GLS_CUDA(cudaStreamWaitEvent(pl->d2h, pl->ev_computed[s], 0));
       if (out_b_host) {
         if (mb == Mem::Pinned)
-          GLS_CUDA(cudaMemcpy2DAsync(B + s0 * ldb, ldb * sizeof(double), bout, p * sizeof(double),
+          GLS_CUDA(copy2d(B + s0 * ldb, ldb * sizeof(double), bout, p * sizeof(double),
                                      p * sizeof(double), kb, cudaMemcpyDeviceToHost, pl->d2h));
         else
           GLS_CUDA(cudaMemcpyAsync(pl->h_b[s], bout, sizeof(double) * p * kb,
