@@ -158,6 +158,27 @@ gls_status_t gls_solve_stream(gls_plan_t plan, const int8_t* XR, int64_t ldxr, i
                               double* B, int64_t ldb, int32_t* snp_status);
 
 /*
+ * gls_solve_block and gls_solve_stream with the genotype codes packed four to
+ * a byte, a quarter of the host-to-device bytes of int8 input (the blocked
+ * solve of Alg. 5 line 3 on X_R as stored; the storage format is not the
+ * paper's, which reads binary64 blocks).  Column j of XP holds ceil(n/4)
+ * bytes (ldxp >= ceil(n/4)); genotype i is the 2-bit code in bits
+ * 2 (i mod 4) .. 2 (i mod 4) + 1 of byte floor(i/4) of its column (the first
+ * sample in the lowest bits), read as the value 0, 1, 2 or 3.  Each block is
+ * unpacked on the device into the plan's int8 staging and solved as an int8
+ * block, so results equal those of the int8 calls on the same values.  XP may
+ * be device, pinned or pageable memory; B and snp_status as for the int8
+ * calls.  The first call allocates 2 x ceil(n/4) x max_block_snps bytes of
+ * device staging (and as much pinned host memory for pageable input to the
+ * stream); an allocation failure returns OOM.  Errors otherwise as for the
+ * int8 calls.
+ */
+gls_status_t gls_solve_block_packed(gls_plan_t plan, const uint8_t* XP, int64_t ldxp, int64_t k,
+                                    double* B, int64_t ldb, int32_t* snp_status);
+gls_status_t gls_solve_stream_packed(gls_plan_t plan, const uint8_t* XP, int64_t ldxp,
+                                     int64_t m, double* B, int64_t ldb, int32_t* snp_status);
+
+/*
  * Batched uneven scans: several independent sequences (each its own plan, with
  * its own M, n, p and SNP block) solved by ONE persistent launch of the
  * mixed-precision blocked solve, so that small scans fill the GPU together.

@@ -65,4 +65,8 @@ void launch_assemble_solve_split(const double* Glin, const double* Pbr, int64_t 
                                  const double* zT, double tau, double* B, int64_t ldb,
                                  int32_t* status, cudaStream_t st);
 
+// genotypes.cu: 2-bit packed genotype columns (ldp bytes each) -> int8 X_R (ldx)
+cudaError_t launch_unpack2(const uint8_t* xp, int64_t ldp, int64_t n, int64_t k, int8_t* x,
+                           int64_t ldx, cudaStream_t st);
+
 }  // namespace gls

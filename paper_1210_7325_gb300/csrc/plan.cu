@@ -99,6 +99,8 @@ struct gls_plan {
   int64_t ldp = 0;
   int nI = 0;               // row blocks of the active path
   int8_t* h_xr[2]{};        // pinned staging for pageable inputs
+  uint8_t* xp[2]{};         // device staging of 2-bit packed blocks (first packed call)
+  uint8_t* h_xp[2]{};       // pinned staging for pageable packed inputs
   double* h_b[2]{};
   int32_t* h_s[2]{};
   gls::MixedState* mixed = nullptr;
@@ -435,6 +437,8 @@ void free_plan(gls_plan* pl) {
     cudaFree(pl->bdev[s]);
     cudaFree(pl->sdev[s]);
     cudaFreeHost(pl->h_xr[s]);
+    cudaFree(pl->xp[s]);
+    cudaFreeHost(pl->h_xp[s]);
     cudaFreeHost(pl->h_b[s]);
     cudaFreeHost(pl->h_s[s]);
     if (pl->ev_loaded[s]) cudaEventDestroy(pl->ev_loaded[s]);
@@ -882,30 +886,30 @@ gls_status_t gls_solve_block(gls_plan_t pl, const int8_t* XR, int64_t ldxr, int6
   return GLS_OK;
 }
 
-gls_status_t gls_solve_stream(gls_plan_t pl, const int8_t* XR, int64_t ldxr, int64_t m,
-                              double* B, int64_t ldb, int32_t* snp_status) {
-  g_last_error.clear();
-  if (!pl) {
-    set_error("plan is NULL");
-    return GLS_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// Device staging of packed blocks (and pinned staging for pageable input),
+// allocated by the first packed call.
+gls_status_t packed_staging(gls_plan* pl, bool pinned) {
+  const size_t bytes = (size_t)gls::ceil_div(pl->n, 4) * (size_t)pl->kmax;
+  for (int s = 0; s < 2; ++s) {
+    if (!pl->xp[s]) GLS_TRY(dev_alloc(&pl->xp[s], bytes));
+    if (pinned && !pl->h_xp[s]) GLS_TRY(host_alloc(&pl->h_xp[s], bytes));
   }
-  if (!pl->factored) {
-    set_error("gls_solve_stream before a successful gls_factor");
-    return GLS_ERR_STATE;
-  }
-  if (m < 0) {
-    set_error("m < 0");
-    return GLS_ERR_INVALID_ARG;
-  }
-  if (m == 0) return GLS_OK;
-  if (!XR || !B || ldxr < pl->n || ldb < pl->p) {
-    set_error("bad XR/B pointer or leading dimension");
-    return GLS_ERR_INVALID_ARG;
-  }
+  return GLS_OK;
+}
+
+// The SNP stream of Alg. 8 for int8 (packed = false, ldx >= n) or 2-bit
+// packed (packed = true, ldx >= ceil(n/4)) genotype columns X.
+gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packed, int64_t m,
+                         double* B, int64_t ldb, int32_t* snp_status) {
   DeviceGuard guard(pl->device);
   const int64_t n = pl->n, kmax = pl->kmax;
   const int p = pl->p;
-  const Mem mx = classify(XR), mb = classify(B);
+  const int64_t width = packed ? gls::ceil_div(n, 4) : n;  // bytes per column
+  const Mem mx = classify(X), mb = classify(B);
   const Mem ms = snp_status ? classify(snp_status) : Mem::Device;
 
   // Block schedule: a short first block (its load is not overlapped), then
@@ -924,13 +928,22 @@ gls_status_t gls_solve_stream(gls_plan_t pl, const int8_t* XR, int64_t ldxr, int
   const bool out_b_host = (mb != Mem::Device);
   const bool out_s_host = snp_status && (ms != Mem::Device);
   const bool pageable_out = (mb == Mem::Pageable) || (snp_status && ms == Mem::Pageable);
+  if (packed) GLS_TRY(packed_staging(pl, pageable_in));
   for (int s = 0; s < 2; ++s) {
-    if (pageable_in && !pl->h_xr[s]) GLS_TRY(host_alloc(&pl->h_xr[s], (size_t)n * kmax));
+    if (!packed && pageable_in && !pl->h_xr[s])
+      GLS_TRY(host_alloc(&pl->h_xr[s], (size_t)n * kmax));
     if (pageable_out && !pl->h_b[s]) {
       GLS_TRY(host_alloc(&pl->h_b[s], (size_t)p * kmax));
       GLS_TRY(host_alloc(&pl->h_s[s], (size_t)kmax));
     }
   }
+  // where the H2D copy of block s lands, and its pinned staging if pageable
+  auto dev_in = [&](int s) -> uint8_t* {
+    return packed ? pl->xp[s] : reinterpret_cast<uint8_t*>(pl->xr[s]);
+  };
+  auto host_in = [&](int s) -> uint8_t* {
+    return packed ? pl->h_xp[s] : reinterpret_cast<uint8_t*>(pl->h_xr[s]);
+  };
   cudaStream_t cs = pl->stream;
   // Order the side streams after any earlier work on the compute stream.
   cudaEvent_t ev0 = pl->ev_computed[1];
@@ -949,14 +962,14 @@ gls_status_t gls_solve_stream(gls_plan_t pl, const int8_t* XR, int64_t ldxr, int
     // device buffer s is free once the compute of block jb-2 is done
     GLS_CUDA(cudaStreamWaitEvent(pl->h2d, pl->ev_computed[s], 0));
     if (!pageable_in) {
-      GLS_CUDA(copy2d(pl->xr[s], n, XR + s0 * ldxr, ldxr, n, kb,
-                                 cudaMemcpyHostToDevice, pl->h2d));
+      GLS_CUDA(copy2d(dev_in(s), width, X + s0 * ldx, ldx, width, kb, cudaMemcpyHostToDevice,
+                      pl->h2d));
     } else {
       GLS_CUDA(cudaEventSynchronize(pl->ev_staged[s]));  // pinned staging s is free
       for (int64_t c = 0; c < kb; ++c)
-        memcpy(pl->h_xr[s] + c * n, XR + (s0 + c) * ldxr, (size_t)n);
-      GLS_CUDA(cudaMemcpyAsync(pl->xr[s], pl->h_xr[s], (size_t)n * kb, cudaMemcpyHostToDevice,
-                               pl->h2d));
+        memcpy(host_in(s) + c * width, X + (s0 + c) * ldx, (size_t)width);
+      GLS_CUDA(cudaMemcpyAsync(dev_in(s), host_in(s), (size_t)width * kb,
+                               cudaMemcpyHostToDevice, pl->h2d));
       GLS_CUDA(cudaEventRecord(pl->ev_staged[s], pl->h2d));
     }
     GLS_CUDA(cudaEventRecord(pl->ev_loaded[s], pl->h2d));
@@ -980,10 +993,22 @@ gls_status_t gls_solve_stream(gls_plan_t pl, const int8_t* XR, int64_t ldxr, int
     const int s = (int)(jb % 2);
     const int64_t s0 = blocks[jb].first, kb = blocks[jb].second;
     if (mx != Mem::Device && jb + 1 < blocks.size()) GLS_TRY(issue_load(jb + 1));
-    const int8_t* xin = (mx == Mem::Device) ? XR + s0 * ldxr : pl->xr[s];
-    const int64_t ldin = (mx == Mem::Device) ? ldxr : n;
     if (mx != Mem::Device) GLS_CUDA(cudaStreamWaitEvent(cs, pl->ev_loaded[s], 0));
     GLS_CUDA(cudaStreamWaitEvent(cs, pl->ev_stored[s], 0));  // output slot s copied out
+    const int8_t* xin;
+    int64_t ldin;
+    if (packed) {
+      // unpack into the int8 staging of slot s (free: the compute stream is in order)
+      const uint8_t* src = (mx == Mem::Device) ? X + s0 * ldx : pl->xp[s];
+      GLS_CUDA(gls::launch_unpack2(src, (mx == Mem::Device) ? ldx : width, n, kb, pl->xr[s], n,
+                                   cs));
+      pl->launches += 1;
+      xin = pl->xr[s];
+      ldin = n;
+    } else {
+      xin = (mx == Mem::Device) ? reinterpret_cast<const int8_t*>(X) + s0 * ldx : pl->xr[s];
+      ldin = (mx == Mem::Device) ? ldx : n;
+    }
     double* bout = out_b_host ? pl->bdev[s] : B + s0 * ldb;
     const int64_t ldout = out_b_host ? p : ldb;
     int32_t* sout = snp_status ? (out_s_host ? pl->sdev[s] : snp_status + s0) : nullptr;
@@ -996,7 +1021,7 @@ gls_status_t gls_solve_stream(gls_plan_t pl, const int8_t* XR, int64_t ldxr, int
       if (out_b_host) {
         if (mb == Mem::Pinned)
           GLS_CUDA(copy2d(B + s0 * ldb, ldb * sizeof(double), bout, p * sizeof(double),
-                                     p * sizeof(double), kb, cudaMemcpyDeviceToHost, pl->d2h));
+                          p * sizeof(double), kb, cudaMemcpyDeviceToHost, pl->d2h));
         else
           GLS_CUDA(cudaMemcpyAsync(pl->h_b[s], bout, sizeof(double) * p * kb,
                                    cudaMemcpyDeviceToHost, pl->d2h));
@@ -1016,6 +1041,89 @@ gls_status_t gls_solve_stream(gls_plan_t pl, const int8_t* XR, int64_t ldxr, int
   int hf[gls::kFlagCount];
   GLS_TRY(check_flags(pl, hf));
   return GLS_OK;
+}
+
+// Common argument checks of the two stream entry points.
+gls_status_t stream_args(gls_plan* pl, const void* X, int64_t ldx, int64_t min_ld, int64_t m,
+                         const double* B, int64_t ldb, const char* name) {
+  if (!pl) {
+    set_error("plan is NULL");
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (!pl->factored) {
+    set_error("%s before a successful gls_factor", name);
+    return GLS_ERR_STATE;
+  }
+  if (m < 0) {
+    set_error("m < 0");
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (m > 0 && (!X || !B || ldx < min_ld || ldb < pl->p)) {
+    set_error("bad XR/B pointer or leading dimension");
+    return GLS_ERR_INVALID_ARG;
+  }
+  return GLS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gls_status_t gls_solve_stream(gls_plan_t pl, const int8_t* XR, int64_t ldxr, int64_t m,
+                              double* B, int64_t ldb, int32_t* snp_status) {
+  g_last_error.clear();
+  GLS_TRY(stream_args(pl, XR, ldxr, pl ? pl->n : 0, m, B, ldb, "gls_solve_stream"));
+  if (m == 0) return GLS_OK;
+  return stream_impl(pl, reinterpret_cast<const uint8_t*>(XR), ldxr, false, m, B, ldb,
+                     snp_status);
+}
+
+gls_status_t gls_solve_stream_packed(gls_plan_t pl, const uint8_t* XP, int64_t ldxp, int64_t m,
+                                     double* B, int64_t ldb, int32_t* snp_status) {
+  g_last_error.clear();
+  GLS_TRY(stream_args(pl, XP, ldxp, pl ? gls::ceil_div(pl->n, 4) : 0, m, B, ldb,
+                      "gls_solve_stream_packed"));
+  if (m == 0) return GLS_OK;
+  return stream_impl(pl, XP, ldxp, true, m, B, ldb, snp_status);
+}
+
+gls_status_t gls_solve_block_packed(gls_plan_t pl, const uint8_t* XP, int64_t ldxp, int64_t k,
+                                    double* B, int64_t ldb, int32_t* snp_status) {
+  g_last_error.clear();
+  if (!pl) {
+    set_error("plan is NULL");
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (!pl->factored) {
+    set_error("gls_solve_block_packed before a successful gls_factor");
+    return GLS_ERR_STATE;
+  }
+  if (k < 0 || k > pl->kmax) {
+    set_error("k = %lld outside [0, max_block_snps = %lld]", (long long)k, (long long)pl->kmax);
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (k == 0) return GLS_OK;
+  const int64_t width = gls::ceil_div(pl->n, 4);
+  if (!XP || !B || ldxp < width || ldb < pl->p) {
+    set_error("bad XP/B pointer or leading dimension");
+    return GLS_ERR_INVALID_ARG;
+  }
+  {
+    DeviceGuard guard(pl->device);
+    const Mem mx = classify(XP);
+    GLS_TRY(packed_staging(pl, false));
+    const uint8_t* src = XP;
+    int64_t ld = ldxp;
+    if (mx != Mem::Device) {
+      GLS_CUDA(copy2d(pl->xp[0], width, XP, ldxp, width, k, cudaMemcpyHostToDevice, pl->stream));
+      src = pl->xp[0];
+      ld = width;
+    }
+    GLS_CUDA(gls::launch_unpack2(src, ld, pl->n, k, pl->xr[0], pl->n, pl->stream));
+    pl->launches += 1;
+  }
+  // the unpacked block is device-resident int8: the int8 entry point from here
+  return gls_solve_block(pl, pl->xr[0], pl->n, k, B, ldb, snp_status);
 }
 
 }  // extern "C"

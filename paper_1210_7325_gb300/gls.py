@@ -90,6 +90,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.gls_solve_block.restype = i32
     lib.gls_solve_stream.argtypes = [vp, vp, i64, i64, vp, i64, vp]
     lib.gls_solve_stream.restype = i32
+    lib.gls_solve_block_packed.argtypes = [vp, vp, i64, i64, vp, i64, vp]
+    lib.gls_solve_block_packed.restype = i32
+    lib.gls_solve_stream_packed.argtypes = [vp, vp, i64, i64, vp, i64, vp]
+    lib.gls_solve_stream_packed.restype = i32
     lib.gls_synchronize.argtypes = [vp]
     lib.gls_synchronize.restype = i32
     lib.gls_plan_stream.argtypes = [vp]
@@ -181,6 +185,45 @@ def _colmajor(a, rows: int, itemsize: int, name: str):
     return ctypes.c_void_p(a.ctypes.data), max(a.shape[0], 1)
 
 
+def packed_rows(n: int) -> int:
+    """Bytes per SNP column of the 2-bit packed genotype layout."""
+    return (int(n) + 3) // 4
+
+
+def pack_genotypes(X):
+    """Packs n x k genotype codes 0..3 (int8 or uint8, numpy or torch) four to a
+    byte: column j -> ceil(n/4) bytes, genotype i in bits 2 (i mod 4) ..
+    2 (i mod 4) + 1 of byte i // 4 (the layout of gls_solve_*_packed).  The
+    result is column-major uint8 in the same library (and device) as X."""
+    n = X.shape[0]
+    k = X.shape[1] if X.ndim == 2 else 1
+    nb = packed_rows(n)
+    try:
+        import torch
+        if isinstance(X, torch.Tensor):
+            x = X.reshape(n, k).to(torch.int16)
+            if bool(((x < 0) | (x > 3)).any()):
+                raise ValueError("packed genotype codes must be in 0..3")
+            pad = torch.zeros((4 * nb, k), dtype=torch.int16, device=X.device)
+            pad[:n] = x
+            q = pad.reshape(nb, 4, k)
+            b = q[:, 0] | (q[:, 1] << 2) | (q[:, 2] << 4) | (q[:, 3] << 6)
+            out = torch.empty((k, nb), dtype=torch.uint8, device=X.device).t()
+            out.copy_(b)
+            return out
+    except ImportError:
+        pass
+    import numpy as np
+    x = np.asarray(X).reshape(n, k, order="F").astype(np.int16)
+    if ((x < 0) | (x > 3)).any():
+        raise ValueError("packed genotype codes must be in 0..3")
+    pad = np.zeros((4 * nb, k), dtype=np.int16)
+    pad[:n] = x
+    q = pad.reshape(nb, 4, k)
+    b = q[:, 0] | (q[:, 1] << 2) | (q[:, 2] << 4) | (q[:, 3] << 6)
+    return np.asfortranarray(b.astype(np.uint8))
+
+
 def _ptr(a):
     if a is None:
         return None
@@ -246,6 +289,25 @@ class Plan:
             m = XR.shape[1]
         _check(lib.gls_solve_stream(self._h, px, ldx, int(m), pb, ldb, _ptr(status)),
                "gls_solve_stream")
+
+    def solve_block_packed(self, XP, B, status=None, k=None):
+        """XP: ceil(n/4) x k uint8 column-major, 2-bit codes (see pack_genotypes)."""
+        lib = load()
+        px, ldx = _colmajor(XP, packed_rows(self.n), 1, "XP")
+        pb, ldb = _colmajor(B, self.p, 8, "B")
+        if k is None:
+            k = XP.shape[1] if XP.ndim == 2 else 1
+        _check(lib.gls_solve_block_packed(self._h, px, ldx, int(k), pb, ldb, _ptr(status)),
+               "gls_solve_block_packed")
+
+    def solve_stream_packed(self, XP, B, status=None, m=None):
+        lib = load()
+        px, ldx = _colmajor(XP, packed_rows(self.n), 1, "XP")
+        pb, ldb = _colmajor(B, self.p, 8, "B")
+        if m is None:
+            m = XP.shape[1]
+        _check(lib.gls_solve_stream_packed(self._h, px, ldx, int(m), pb, ldb, _ptr(status)),
+               "gls_solve_stream_packed")
 
     def get_factor(self, L=None, Zinv=None):
         """Copies L and L^{-1} (n x n column-major, host or device) of the last factor."""
