@@ -551,7 +551,7 @@ gls_status_t run_block(gls_plan* pl, const int8_t* xr, int64_t ldxr, int64_t k, 
 
 extern "C" {
 
-int32_t gls_version(void) { return 100; }
+int32_t gls_version(void) { return 200; }  // 0.2.0: packed input, graph replay, factor flags
 
 const char* gls_last_error(void) { return g_last_error.c_str(); }
 
