@@ -164,9 +164,11 @@ gls_status_t gls_solve_stream(gls_plan_t plan, const int8_t* XR, int64_t ldxr, i
  * paper's, which reads binary64 blocks).  Column j of XP holds ceil(n/4)
  * bytes (ldxp >= ceil(n/4)); genotype i is the 2-bit code in bits
  * 2 (i mod 4) .. 2 (i mod 4) + 1 of byte floor(i/4) of its column (the first
- * sample in the lowest bits), read as the value 0, 1, 2 or 3.  Each block is
- * unpacked on the device into the plan's int8 staging and solved as an int8
- * block, so results equal those of the int8 calls on the same values.  XP may
+ * sample in the lowest bits), read as the value 0, 1, 2 or 3.  The mixed
+ * paths of the stream convert the packed codes straight to their tensor-core
+ * operand; otherwise a block is unpacked on the device into the plan's int8
+ * staging and solved as an int8 block.  Either way the results equal those of
+ * the int8 calls on the same values, bit for bit.  XP may
  * be device, pinned or pageable memory; B and snp_status as for the int8
  * calls.  The first call allocates 2 x ceil(n/4) x max_block_snps bytes of
  * device staging (and as much pinned host memory for pageable input to the

@@ -33,6 +33,9 @@ double* mixed_w_buffer(MixedState* ms);
 // One block, step 1: int8 genotypes -> the 16-bit operand layout read by TMA.
 cudaError_t mixed_convert(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,
                           cudaStream_t st);
+// The same from 2-bit packed genotype columns (ldp bytes each, four codes a byte).
+cudaError_t mixed_convert_packed(MixedState* ms, const uint8_t* xp, int64_t ldp, int64_t k,
+                                 cudaStream_t st);
 // One block, step 2: the persistent tcgen05 solve + Gram epilogue.  Writes the
 // S_BR partials Pbr[I][j] (I < npad/128) and the linear Gram entries
 // Glin[q][j] (q < p-1: S_BL, q = p-1: b_B), j < k, leading dimension ldp.

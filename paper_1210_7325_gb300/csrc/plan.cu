@@ -513,8 +513,11 @@ gls_status_t check_flags(gls_plan* pl, int host_flags[gls::kFlagCount]) {
 }
 
 // Solves one block whose inputs/outputs are all device resident, on pl->stream.
+// Mixed paths only: with xp set, the genotypes are 2-bit packed columns (ldp
+// bytes each) converted straight to the tensor-core operand (xr unused).
 gls_status_t run_block(gls_plan* pl, const int8_t* xr, int64_t ldxr, int64_t k, double* B,
-                       int64_t ldb, int32_t* status) {
+                       int64_t ldb, int32_t* status, const uint8_t* xp = nullptr,
+                       int64_t ldp = 0) {
   if (k == 0) return GLS_OK;
   if (pl->precision == GLS_PREC_FP64) {
     {
@@ -531,7 +534,8 @@ gls_status_t run_block(gls_plan* pl, const int8_t* xr, int64_t ldxr, int64_t k, 
     double* Glin = pl->partials + (int64_t)pl->nI * pl->ldp;  // p x ldp
     {
       Timed t(pl, &pl->t_convert);
-      GLS_CUDA(gls::mixed_convert(pl->mixed, xr, ldxr, k, pl->stream));
+      if (xp) GLS_CUDA(gls::mixed_convert_packed(pl->mixed, xp, ldp, k, pl->stream));
+      else GLS_CUDA(gls::mixed_convert(pl->mixed, xr, ldxr, k, pl->stream));
     }
     {
       Timed t(pl, &pl->t_trsm);
@@ -995,26 +999,37 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
     if (mx != Mem::Device && jb + 1 < blocks.size()) GLS_TRY(issue_load(jb + 1));
     if (mx != Mem::Device) GLS_CUDA(cudaStreamWaitEvent(cs, pl->ev_loaded[s], 0));
     GLS_CUDA(cudaStreamWaitEvent(cs, pl->ev_stored[s], 0));  // output slot s copied out
-    const int8_t* xin;
-    int64_t ldin;
-    if (packed) {
-      // unpack into the int8 staging of slot s (free: the compute stream is in order)
-      const uint8_t* src = (mx == Mem::Device) ? X + s0 * ldx : pl->xp[s];
-      GLS_CUDA(gls::launch_unpack2(src, (mx == Mem::Device) ? ldx : width, n, kb, pl->xr[s], n,
-                                   cs));
-      pl->launches += 1;
-      xin = pl->xr[s];
-      ldin = n;
-    } else {
-      xin = (mx == Mem::Device) ? reinterpret_cast<const int8_t*>(X) + s0 * ldx : pl->xr[s];
-      ldin = (mx == Mem::Device) ? ldx : n;
-    }
     double* bout = out_b_host ? pl->bdev[s] : B + s0 * ldb;
     const int64_t ldout = out_b_host ? p : ldb;
     int32_t* sout = snp_status ? (out_s_host ? pl->sdev[s] : snp_status + s0) : nullptr;
-    GLS_TRY(replayed(pl, pl->replays,
-                     (KeyHash() << 2u << xin << ldin << kb << bout << ldout << sout).h,
-                     [&]() { return run_block(pl, xin, ldin, kb, bout, ldout, sout); }));
+    if (packed && pl->precision != GLS_PREC_FP64) {
+      // the mixed paths convert the packed codes straight to their operand
+      const uint8_t* src = (mx == Mem::Device) ? X + s0 * ldx : pl->xp[s];
+      const int64_t ld = (mx == Mem::Device) ? ldx : width;
+      GLS_TRY(replayed(pl, pl->replays,
+                       (KeyHash() << 3u << src << ld << kb << bout << ldout << sout).h,
+                       [&]() {
+                         return run_block(pl, nullptr, 0, kb, bout, ldout, sout, src, ld);
+                       }));
+    } else {
+      const int8_t* xin;
+      int64_t ldin;
+      if (packed) {
+        // unpack into the int8 staging of slot s (free: the compute stream is in order)
+        const uint8_t* src = (mx == Mem::Device) ? X + s0 * ldx : pl->xp[s];
+        GLS_CUDA(gls::launch_unpack2(src, (mx == Mem::Device) ? ldx : width, n, kb, pl->xr[s],
+                                     n, cs));
+        pl->launches += 1;
+        xin = pl->xr[s];
+        ldin = n;
+      } else {
+        xin = (mx == Mem::Device) ? reinterpret_cast<const int8_t*>(X) + s0 * ldx : pl->xr[s];
+        ldin = (mx == Mem::Device) ? ldx : n;
+      }
+      GLS_TRY(replayed(pl, pl->replays,
+                       (KeyHash() << 2u << xin << ldin << kb << bout << ldout << sout).h,
+                       [&]() { return run_block(pl, xin, ldin, kb, bout, ldout, sout); }));
+    }
     GLS_CUDA(cudaEventRecord(pl->ev_computed[s], cs));
     if (out_b_host || out_s_host) {
       GLS_CUDA(cudaStreamWaitEvent(pl->d2h, pl->ev_computed[s], 0));

@@ -545,6 +545,48 @@ __global__ void convert_x_kernel(const int8_t* __restrict__ x8, int64_t ldx, int
   }
 }
 
+// The same outputs from 2-bit packed genotype columns (ldp bytes each; row i
+// in bits 2 (i mod 4) .. 2 (i mod 4) + 1 of byte i / 4): the 8 rows of a
+// thread are two packed bytes, so the block is read once, at a quarter of
+// the int8 bytes, with no separate unpacking pass.
+template <bool kBF16>
+__global__ void convert_xp_kernel(const uint8_t* __restrict__ xp, int64_t ldp, int64_t n,
+                                  int64_t k, int64_t npad, uint16_t* __restrict__ x16,
+                                  uint8_t* __restrict__ x8a) {
+  const int64_t per_col = npad / 8;
+  const int64_t total = k * per_col;
+  const int64_t nb = (n + 3) / 4;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = idx / per_col;
+    const int64_t c0 = (idx - j * per_col) * 8;
+    const int64_t b0 = c0 / 4;
+    uint32_t w = 0;
+    if (b0 < nb) w = xp[j * ldp + b0];
+    if (b0 + 1 < nb) w |= (uint32_t)xp[j * ldp + b0 + 1] << 8;
+    uint16_t v[8];
+    uint32_t b[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int xi = (c0 + e < n) ? (int)((w >> (2 * e)) & 3u) : 0;
+      b[e] = (uint32_t)xi;
+      const float xf = (float)xi;
+      v[e] = kBF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(xf))
+                   : __half_as_ushort(__float2half_rn(xf));
+    }
+    uint4 o;
+    o.x = (uint32_t)v[0] | ((uint32_t)v[1] << 16);
+    o.y = (uint32_t)v[2] | ((uint32_t)v[3] << 16);
+    o.z = (uint32_t)v[4] | ((uint32_t)v[5] << 16);
+    o.w = (uint32_t)v[6] | ((uint32_t)v[7] << 16);
+    *reinterpret_cast<uint4*>(x16 + j * npad + c0) = o;
+    uint2 bb;
+    bb.x = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
+    bb.y = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
+    *reinterpret_cast<uint2*>(x8a + j * npad + c0) = bb;
+  }
+}
+
 template <bool kBF16>
 __device__ __forceinline__ uint16_t to16(double v) {
   return kBF16 ? __bfloat16_as_ushort(__float2bfloat16_rn((float)v))
@@ -955,6 +997,20 @@ cudaError_t mixed_convert(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_
   else
     convert_x_kernel<false><<<cgrid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, ms->x16,
                                                    ms->x8a);
+  return cudaGetLastError();
+}
+
+cudaError_t mixed_convert_packed(MixedState* ms, const uint8_t* xp, int64_t ldp, int64_t k,
+                                 cudaStream_t st) {
+  if (k <= 0) return cudaSuccess;
+  const int64_t work = k * (ms->npad / 8);
+  const unsigned cgrid = (unsigned)std::min<int64_t>(ceil_div(work, 256), 65535 * 4);
+  if (ms->bf16)
+    convert_xp_kernel<true><<<cgrid, 256, 0, st>>>(xp, ldp, ms->n, k, ms->npad, ms->x16,
+                                                   ms->x8a);
+  else
+    convert_xp_kernel<false><<<cgrid, 256, 0, st>>>(xp, ldp, ms->n, k, ms->npad, ms->x16,
+                                                    ms->x8a);
   return cudaGetLastError();
 }
 
