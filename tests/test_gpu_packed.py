@@ -63,8 +63,10 @@ def test_packed_block_equals_int8(prec, n, m, kmax):
     assert relerr(B8[:, ok], Bref[:, ok]).max() <= tol
 
 
-@pytest.mark.parametrize("source", ["pinned", "pageable", "device"])
-def test_packed_stream_equals_int8(source):
+@pytest.mark.parametrize("prec,source", [("bf16", "pinned"), ("bf16", "pageable"),
+                                         ("bf16", "device"), ("fp16", "pinned"),
+                                         ("fp64", "pinned")])
+def test_packed_stream_equals_int8(prec, source):
     import torch
     pr = synth.problem(777, 5, 3000, 0.4, seed=77, n_markers=1500)
     n, m = pr["XR"].shape
@@ -79,7 +81,7 @@ def test_packed_stream_equals_int8(source):
         XPt = torch.from_numpy(np.ascontiguousarray(XPw.T)).cuda().t()[:gls.packed_rows(n)]
     else:  # pageable host memory
         XPt = torch.from_numpy(np.ascontiguousarray(XPw.T)).t()[:gls.packed_rows(n)]
-    with plan_for(pr, "bf16", 512) as plan:
+    with plan_for(pr, prec, 512) as plan:
         B8 = np.zeros((p, m), order="F")
         s8 = np.zeros(m, np.int32)
         plan.solve_stream(XR, B8, s8, m=m)
@@ -87,9 +89,10 @@ def test_packed_stream_equals_int8(source):
         sp = np.full(m, -1, np.int32)
         plan.solve_stream_packed(XPt, Bp, sp, m=m)
     assert np.array_equal(B8, Bp) and np.array_equal(s8, sp)
-    Bref, sref = oracle_ref(pr, oracle.TAU_MIXED)
+    fp64 = prec == "fp64"
+    Bref, sref = oracle_ref(pr, oracle.TAU_FP64 if fp64 else oracle.TAU_MIXED)
     assert np.array_equal(sp, sref)
-    assert relerr(Bp, Bref).max() <= 1e-6
+    assert relerr(Bp, Bref).max() <= (1e-10 if fp64 else 1e-6)
 
 
 def test_packed_rejects_short_leading_dimension():
