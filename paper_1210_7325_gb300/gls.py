@@ -194,19 +194,25 @@ def pack_genotypes(X):
     """Packs n x k genotype codes 0..3 (int8 or uint8, numpy or torch) four to a
     byte: column j -> ceil(n/4) bytes, genotype i in bits 2 (i mod 4) ..
     2 (i mod 4) + 1 of byte i // 4 (the layout of gls_solve_*_packed).  The
-    result is column-major uint8 in the same library (and device) as X."""
+    result is column-major uint8 in the same library (and device) as X.  Works
+    on byte views: the temporaries are about n x k / 4 bytes each."""
     n = X.shape[0]
     k = X.shape[1] if X.ndim == 2 else 1
     nb = packed_rows(n)
     try:
         import torch
         if isinstance(X, torch.Tensor):
-            x = X.reshape(n, k).to(torch.int16)
-            if bool(((x < 0) | (x > 3)).any()):
+            if X.dtype not in (torch.int8, torch.uint8):
+                raise TypeError("packed genotype codes must be int8 or uint8")
+            x = X.reshape(n, k)
+            if x.numel() and (int(x.min()) < 0 or int(x.max()) > 3):
                 raise ValueError("packed genotype codes must be in 0..3")
-            pad = torch.zeros((4 * nb, k), dtype=torch.int16, device=X.device)
-            pad[:n] = x
-            q = pad.reshape(nb, 4, k)
+            x = x.view(torch.uint8)  # same bits for 0..3
+            if n % 4:
+                pad = torch.zeros((4 * nb, k), dtype=torch.uint8, device=X.device)
+                pad[:n] = x
+                x = pad
+            q = x.reshape(nb, 4, k)
             b = q[:, 0] | (q[:, 1] << 2) | (q[:, 2] << 4) | (q[:, 3] << 6)
             out = torch.empty((k, nb), dtype=torch.uint8, device=X.device).t()
             out.copy_(b)
@@ -214,10 +220,14 @@ def pack_genotypes(X):
     except ImportError:
         pass
     import numpy as np
-    x = np.asarray(X).reshape(n, k, order="F").astype(np.int16)
-    if ((x < 0) | (x > 3)).any():
+    x = np.asarray(X)
+    if x.dtype not in (np.int8, np.uint8):
+        raise TypeError("packed genotype codes must be int8 or uint8")
+    x = x.reshape(n, k, order="F")
+    if x.size and (int(x.min()) < 0 or int(x.max()) > 3):
         raise ValueError("packed genotype codes must be in 0..3")
-    pad = np.zeros((4 * nb, k), dtype=np.int16)
+    x = x.view(np.uint8)
+    pad = np.zeros((4 * nb, k), dtype=np.uint8)  # row-major: row 4 b + q -> q[b, q]
     pad[:n] = x
     q = pad.reshape(nb, 4, k)
     b = q[:, 0] | (q[:, 1] << 2) | (q[:, 2] << 4) | (q[:, 3] << 6)
