@@ -215,6 +215,12 @@ def run_gpu(args, wl, rank, world, torch, dist):
     nan = int(torch.isnan(B).any().item())
     res = dict(time=t, stats=stats, clocks=clk.summary(), bad_status=bad, nan=nan,
                split=split or None, split_info=split_info)
+    # the oracle leg solves a seeded sample of the timed run's own SNP columns
+    cols = sample_columns(m, args.cpu_snps, seed=rank)
+    ci = torch.as_tensor(cols, device=dev)
+    res["sample"] = dict(cols=cols, XR=np.asfortranarray(XR[ci].cpu().numpy().T),
+                         B=B[ci].cpu().numpy().T.copy(), st=st[ci].cpu().numpy(),
+                         M=M, XL=XL, y=y)
 
     # end to end through the public API with host buffers (pinned); per-kernel
     # timing is instrumentation a user would not run with, so it is off here
@@ -258,18 +264,28 @@ def run_gpu(args, wl, rank, world, torch, dist):
         res["e2e_int8_time"], res["e2e_int8_step_ms"] = timed(e2e_int8)
         te, res["e2e_step_ms"] = timed(e2e_step)
         res["e2e_time"] = te
-        # one more step with per-kernel device timing (not in the figure): does
-        # the step's time go to the kernels or to waiting on the host link?
-        plan.set_timing(True)
-        t1 = time.perf_counter()
-        e2e_step()
-        t2 = time.perf_counter()
-        sd = plan.stats()
-        plan.set_timing(False)
-        res["e2e_diag"] = {"wall_ms": round((t2 - t1) * 1e3, 2),
-                           "factor_ms": round(sd["factor_ms"], 2),
-                           "solve_kernels_ms": round(sd["trsm_ms"] + sd["convert_ms"]
-                                                     + sd["solve_ms"], 2)}
+        # one more step of each with per-kernel device timing and every block
+        # copy timed on its side stream while overlapped (not in the figures):
+        # does the step's time go to the kernels or to waiting on the host link?
+        def diag(fn):
+            plan.set_timing(True)
+            t1 = time.perf_counter()
+            fn()
+            t2 = time.perf_counter()
+            sd = plan.stats()
+            plan.set_timing(False)
+            return {"wall_ms": round((t2 - t1) * 1e3, 2),
+                    "factor_ms": round(sd["factor_ms"], 2),
+                    "solve_kernels_ms": round(sd["trsm_ms"] + sd["convert_ms"]
+                                              + sd["solve_ms"], 2),
+                    "h2d_copies": sd["h2d_copies"], "h2d_ms": round(sd["h2d_ms"], 2),
+                    "h2d_gbps_overlapped": (sd["h2d_bytes"] / (sd["h2d_ms"] / 1e3) / 1e9
+                                            if sd["h2d_ms"] > 0 else None),
+                    "d2h_ms": round(sd["d2h_ms"], 2),
+                    "d2h_gbps_overlapped": (sd["d2h_bytes"] / (sd["d2h_ms"] / 1e3) / 1e9
+                                            if sd["d2h_ms"] > 0 else None)}
+        res["e2e_diag"] = diag(e2e_step)
+        res["e2e_int8_diag"] = diag(e2e_int8)
         # context for the end-to-end figure: this box's pinned host -> device copy rate
         # ... over every block of the pinned genotype buffer (placement of its
         # pages can differ along the buffer), best of 3 per block
@@ -390,30 +406,45 @@ def fp64_dgemm_tflops(torch):
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_sample(wl, s_snps, nthreads, M=None, XL=None, y=None):
-    """Times the oracle as it stands on the host: the Cholesky of M once, then
-    the per-SNP loop on s_snps SNPs.  Returns the timings and the projected
-    whole-job rate for the workload's m."""
+def sample_columns(m, count, seed=0):
+    """SNP columns checked against the oracle: the first half of `count` in
+    order, the rest seeded uniform over the whole scan (sorted, distinct)."""
     import numpy as np
+    count = min(count, m)
+    head = np.arange(count // 2)
+    rest = np.random.Generator(np.random.Philox(20121030 + seed)).choice(
+        np.arange(count // 2, m), size=count - count // 2, replace=False)
+    return np.sort(np.concatenate([head, rest])).astype(np.int64)
+
+
+def oracle_sample(wl, nthreads, M, XL, y, XR):
+    """Times the oracle as it stands on the host: the Cholesky of M once, then
+    the per-SNP loop on the columns of XR (n x s int8).  Returns the timings,
+    the projected whole-job rate for the workload's m, and the oracle's b_i."""
     import oracle
-    from paper_1210_7325_gb300 import synth
-    n, p = wl["n"], wl["p"]
-    seed = synth.BASE_SEED + wl["seed_offset"]
-    if M is None:
-        M = synth.kinship_M(n, wl["h"], seed, device="cuda")
-        XL = synth.covariates(n, p, seed)
-        y = synth.phenotype(n, seed)
-    XR = synth.genotypes_np(n, s_snps, seed)
+    s_snps = XR.shape[1]
     t0 = time.perf_counter()
     L, info = oracle.potrf(M, nthreads=nthreads)
     t1 = time.perf_counter()
-    B, st = oracle.gls_factored(L, XL, y, XR, tau=oracle.TAU_MIXED, nthreads=nthreads)
+    tau = oracle.TAU_FP64 if wl["precision"] == "fp64" else oracle.TAU_MIXED
+    B, st = oracle.gls_factored(L, XL, y, XR, tau=tau, nthreads=nthreads)
     t2 = time.perf_counter()
     assert info == 0
     tf, ts = t1 - t0, t2 - t1
     whole = wl["m"] / (tf + wl["m"] / s_snps * ts)
     return dict(factor_s=tf, snp_s=ts, s_snps=s_snps, value=whole,
-                steady=s_snps / ts, cores=nthreads)
+                steady=s_snps / ts, cores=nthreads, B=B, st=st)
+
+
+def error_summary(B, st, Bref, sref, tol):
+    """Relative 2-norm error of b_i against the oracle's on the same SNPs."""
+    import numpy as np
+    ok = sref == 0
+    e = np.linalg.norm(B[:, ok] - Bref[:, ok], axis=0) / np.linalg.norm(Bref[:, ok], axis=0)
+    return {"max": float(e.max()) if e.size else None,
+            "p99": float(np.quantile(e, 0.99)) if e.size else None,
+            "n_sampled": int(B.shape[1]), "status_mismatches": int((st != sref).sum()),
+            "tolerance": tol, "reference": "FP64 oracle on the same SNP columns"}
 
 
 def run_reference(args, wl):
@@ -433,12 +464,13 @@ def run_reference(args, wl):
     XL = synth.covariates(n, p, seed)
     y = synth.phenotype(n, seed)
     s_snps = args.ref_snps
+    XR = synth.genotypes_np(n, s_snps, seed)
     for _ in range(args.warmup):
-        oracle_sample(wl, s_snps, nthreads, M, XL, y)
+        oracle_sample(wl, nthreads, M, XL, y, XR)
     vals, steps = [], []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        r = oracle_sample(wl, s_snps, nthreads, M, XL, y)
+        r = oracle_sample(wl, nthreads, M, XL, y, XR)
         steps.append(r)
         vals.append(r["value"])
     total = time.perf_counter() - t0
@@ -487,6 +519,7 @@ def run_batch_workload(args, bw, torch):
     specs = batch_specs(bw)
     plans, inputs, outs, blocks = [], [], [], []
     fp64 = bw["precision"] == "fp64"
+    t_setup = time.perf_counter()
     for (n, p, m, h, seed) in specs:
         Md = synth.kinship_M_torch(n, h, seed, device="cuda").t()
         XL = synth.covariates(n, p, seed)
@@ -538,6 +571,7 @@ def run_batch_workload(args, bw, torch):
         batch = gls.Batch(plans)
         group, tune_times = autotune.tune_group(batch, *round_args(0))
     rargs = [round_args(r) for r in range(rounds)]
+    t_setup = time.perf_counter() - t_setup
 
     def step():
         factor_all()
@@ -609,11 +643,48 @@ def run_batch_workload(args, bw, torch):
         "check": {"bad_status": bad},
     }
     line["gpu_launches"] = int(sum(s["launches"] for s in sts))
+    line["config"]["setup_s"] = round(t_setup, 2)
+    line["config"]["operand_precision"] = sorted({pl.operand_precision for pl in plans})
+    line["error"] = batch_error(specs, inputs, outs, fp64)
     if batch is not None:
         batch.close()
     for pl in plans:
         pl.close()
     return line
+
+
+def batch_error(specs, inputs, outs, fp64, max_scans=6, n_max=3000, snps=48):
+    """b_i of the batched run against the oracle: every scan with n <= n_max
+    (up to max_scans, smallest n first), `snps` seeded SNP columns each."""
+    import numpy as np
+    import torch
+
+    import oracle
+    order = sorted((sp[0], i) for i, sp in enumerate(specs) if sp[0] <= n_max)[:max_scans]
+    tau = oracle.TAU_FP64 if fp64 else oracle.TAU_MIXED
+    Bs, Brefs, sts, srefs, scans = [], [], [], [], []
+    for n, i in order:
+        m = specs[i][2]
+        Md, XLd, yd, XR = inputs[i]
+        cols = sample_columns(m, snps, seed=i)
+        ci = torch.as_tensor(cols, device=XR.device)
+        Bref, sref, info = oracle.gls(Md.cpu().numpy(), XLd.cpu().numpy(), yd.cpu().numpy(),
+                                      np.asfortranarray(XR[ci].cpu().numpy().T), tau=tau,
+                                      nthreads=oracle.default_threads())
+        if info != 0:
+            continue
+        Bs.append(outs[i][0][ci].cpu().numpy().T)
+        sts.append(outs[i][1][ci].cpu().numpy())
+        Brefs.append(Bref)
+        srefs.append(sref)
+        scans.append(int(n))
+    if not Bs:
+        return {"max": None, "p99": None, "n_sampled": 0}
+    e = error_summary(np.concatenate(Bs, axis=1), np.concatenate(sts),
+                      np.concatenate(Brefs, axis=1), np.concatenate(srefs),
+                      1e-10 if fp64 else 1e-6)
+    e["scans_n"] = scans
+    return e
 
 
 SERVE_WORKLOADS = {
@@ -626,62 +697,157 @@ SERVE_WORKLOADS = {
 }
 
 
-def serve_inputs_factory(seed_base):
-    import numpy as np
-    from paper_1210_7325_gb300 import serve, synth
+def serve_inputs_factory(bank, seed_base):
+    """Request inputs as slices of a pre-drawn bank (synth.ServingBank): the
+    server's latency then excludes synthesizing them."""
+    from paper_1210_7325_gb300 import serve
 
     def make_inputs(req, torch, reuse):
-        seed = seed_base + req.mkey
-        M = XL = None
-        if not reuse:
-            M = synth.kinship_M_torch(req.n, req.h, seed, device="cuda").t()
-            XL = torch.from_numpy(np.ascontiguousarray(synth.covariates(req.n, req.p, seed).T))
-            XL = XL.cuda().t()
-        y = torch.from_numpy(synth.phenotype(req.n, req.y_seed)).cuda()
-        XR = synth.genotypes_torch(req.n, req.m, seed, device="cuda")
+        M, XL, y, XR = bank.request(req.n, req.p, req.m, req.h, seed_base + req.mkey,
+                                    req.y_seed, with_factor_inputs=not reuse)
         return serve.Inputs(M, XL, XR, y)
     return make_inputs
 
 
-def run_serve_workload(args, sw, torch):
-    """Config: Poisson stream of scan requests served with continuous batching."""
+def serve_kept(reqs, count=6, n_max=3000):
+    """Request ids whose outputs the serving run keeps for the oracle check:
+    `count` requests with n <= n_max spread over the stream (new and reused)."""
+    small = [r for r in reqs if r.n <= n_max]
+    if not small:
+        return set()
+    step = max(1, len(small) // count)
+    return {r.rid for r in small[::step][:count]}
+
+
+def serve_error(bank, seed_base, reqs, results, tau, snps=48):
+    """Relative error of served b_i against the oracle: for every kept request,
+    `snps` seeded SNP columns solved by the oracle from the same inputs."""
+    import numpy as np
+    import torch
+
+    import oracle
+    errs, nreq = [], 0
+    for r in reqs:
+        got = results.get(r.rid)
+        if got is None or "B" not in got:
+            continue
+        M, XL, y, XR = bank.request(r.n, r.p, r.m, r.h, seed_base + r.mkey, r.y_seed)
+        cols = np.sort(np.random.default_rng(r.rid).choice(r.m, size=min(snps, r.m),
+                                                           replace=False))
+        ci = torch.as_tensor(cols, device=XR.device)
+        Xs = np.asfortranarray(XR[ci].cpu().numpy().T)
+        Bref, sref, info = oracle.gls(M.cpu().numpy(), None if XL is None else XL.cpu().numpy(),
+                                      y.cpu().numpy(), Xs, tau=tau,
+                                      nthreads=oracle.default_threads())
+        B = got["B"][ci].cpu().numpy().T
+        st = got["status"][ci].cpu().numpy()
+        if info != 0 or not np.array_equal(st, sref):
+            errs.append(float("inf"))
+            continue
+        ok = sref == 0
+        e = np.linalg.norm(B[:, ok] - Bref[:, ok], axis=0) / np.linalg.norm(Bref[:, ok], axis=0)
+        errs.extend(float(v) for v in e)
+        nreq += 1
+    if not errs:
+        return {"max": None, "p99": None, "n_sampled": 0, "requests": 0}
+    a = np.array(errs)
+    return {"max": float(a.max()), "p99": float(np.quantile(a, 0.99)), "n_sampled": int(a.size),
+            "requests": nreq, "reference": "FP64 oracle on the same inputs",
+            "tolerance": 1e-10 if tau == 2.0 ** -30 else 1e-6}
+
+
+def run_serve_workload(args, sw, torch, time_cap=None):
+    """Config: Poisson stream of scan requests served with continuous batching.
+    Request inputs are slices of banks drawn before the clock starts; a sample
+    of requests is checked against the oracle after the run."""
+    import oracle
     from paper_1210_7325_gb300 import serve, synth
     seed = synth.BASE_SEED + sw["seed_offset"]
-    count = args.requests or sw["requests"]
+    count = getattr(args, "requests", 0) or sw["requests"]
     reqs = serve.poisson_requests(count, sw["rate"], seed, sw["n"], sw["p"], sw["m"],
                                   sw["reuse"])
-    make = serve_inputs_factory(seed * 10)
+    t_bank = time.perf_counter()
+    bank = synth.ServingBank(sw["n"][1], sw["m"][1], seed * 7, device="cuda")
+    torch.cuda.synchronize()
+    t_bank = time.perf_counter() - t_bank
+    make = serve_inputs_factory(bank, seed * 10)
     # warm-up: load kernels and encode maps on a few small requests (not timed)
     warm = serve.poisson_requests(4, 100.0, seed + 1, (1000, 1200), (2, 4), (2000, 4000), 0.0)
     srv = serve.Server(make, sw["precision"], sw["budget"], sw["block"])
     srv.run(warm)
     srv.close()
-    srv = serve.Server(make, sw["precision"], sw["budget"], sw["block"])
-    cap = args.time_cap if args.time_cap else sw["time_cap"]
+    kept = serve_kept(reqs)
+    srv = serve.Server(make, sw["precision"], sw["budget"], sw["block"], keep=kept)
+    cap = time_cap or getattr(args, "time_cap", 0) or sw["time_cap"]
     t0 = time.perf_counter()
     results = srv.run(reqs, time_cap=cap)
     wall = time.perf_counter() - t0
     summ = serve.latency_summary(results)
     depth = [d[1] for d in srv.queue_depth]
     srv.close()
+    tau = oracle.TAU_FP64 if sw["precision"] == "fp64" else oracle.TAU_MIXED
+    err = serve_error(bank, seed * 10, [r for r in reqs if r.rid in kept], results, tau)
     line = {
         "metric": METRIC, "value": summ.get("solves_per_s", 0.0), "unit": UNIT, "n_gpus": 1,
         "steps": 1, "warmup": 1, "ms_per_step": wall * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"bf16": "bf16", "fp16": "f16", "fp64": "f64"}[sw["precision"]],
-        "data": "synthetic Poisson request stream (seeded)",
-        "config": {"workload": args.workload, "requests": count, "rate_per_s": sw["rate"],
-                   "n_range": sw["n"], "p_range": sw["p"], "m_range": sw["m"],
-                   "reuse_fraction": sw["reuse"], "hbm_budget_bytes": sw["budget"],
-                   "block_snps": sw["block"], "time_cap_s": cap, "parallelism": "replicas1"},
+        "data": "synthetic Poisson request stream (seeded); inputs sliced from banks drawn "
+                "before the clock",
+        "config": {"workload": getattr(args, "workload", None), "requests": count,
+                   "rate_per_s": sw["rate"], "n_range": sw["n"], "p_range": sw["p"],
+                   "m_range": sw["m"], "reuse_fraction": sw["reuse"],
+                   "hbm_budget_bytes": sw["budget"], "block_snps": sw["block"],
+                   "time_cap_s": cap, "bank_build_s": round(t_bank, 2),
+                   "parallelism": "replicas1"},
         "latency": {k: v for k, v in summ.items() if k.endswith("_s")},
         "completed": summ.get("completed", 0), "reused_factors": summ.get("reused", 0),
+        "error": err,
         "loop_breakdown": srv.breakdown,
         "queue_depth_max": max(depth) if depth else 0,
         "queue_depth_last": depth[-1] if depth else 0,
         "wall_s": wall,
     }
+    del bank
+    torch.cuda.empty_cache()
     return line
+
+
+def sub_batch(args, torch, name="batch48_uneven_bf16", steps=2, warmup=1):
+    """The batched uneven-scan workload as a sub-object of the default line."""
+    sub = argparse.Namespace(**vars(args))
+    sub.steps, sub.warmup, sub.workload = steps, warmup, name
+    try:
+        ln = run_batch_workload(sub, BATCH_WORKLOADS[name], torch)
+    except Exception as ex:  # reported, not fatal to the headline line
+        return {"workload": name, "error_raised": repr(ex)}
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "roofline",
+            "phase_ms_per_step", "error", "gpu_launches", "check")
+    out = {"workload": name}
+    out.update({k: ln[k] for k in keep if k in ln})
+    out["config"] = {k: ln["config"][k] for k in ("scans", "total_snps", "rounds",
+                                                  "group_autotuned", "split_terms_autotuned",
+                                                  "operand_precision", "setup_s")
+                     if k in ln["config"]}
+    return out
+
+
+def sub_serve(args, torch, name="serve2000_bf16", time_cap=180.0):
+    """The serving workload as a sub-object of the default line (time-capped)."""
+    try:
+        ln = run_serve_workload(argparse.Namespace(workload=name, requests=0, time_cap=0),
+                                SERVE_WORKLOADS[name], torch, time_cap=time_cap)
+    except Exception as ex:  # reported, not fatal to the headline line
+        return {"workload": name, "error_raised": repr(ex)}
+    keep = ("value", "unit", "latency", "completed", "reused_factors", "error",
+            "queue_depth_max", "queue_depth_last", "wall_s", "dtype")
+    out = {"workload": name}
+    out.update({k: ln[k] for k in keep if k in ln})
+    out["config"] = {k: ln["config"][k] for k in ("requests", "rate_per_s", "time_cap_s",
+                                                  "bank_build_s", "hbm_budget_bytes")}
+    out["loop_breakdown"] = {k: round(v, 3) if isinstance(v, float) else v
+                             for k, v in ln["loop_breakdown"].items()}
+    return out
 
 
 def launch_flags(args, gls):
@@ -731,6 +897,8 @@ def main():
     ap.add_argument("--eager", action="store_true",
                     help="launch every kernel directly (no CUDA-graph replay of repeated sequences)")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-sub", action="store_true",
+                    help="default workload: skip the batched-scan and serving legs")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--cpu-snps", type=int, default=2048)
@@ -847,7 +1015,8 @@ def main():
                                 "h2d_bytes_per_step": res["e2e_int8_h2d"],
                                 "d2h_bytes_per_step": res["e2e_d2h"],
                                 "genotype_input": "int8 (gls_solve_stream)",
-                                "step_ms": res.get("e2e_int8_step_ms")}
+                                "step_ms": res.get("e2e_int8_step_ms"),
+                                "diagnostic_step": res.get("e2e_int8_diag")}
     if not args.skip_fp64 and wl["precision"] != "fp64":
         try:
             line["fp64"] = fp64_sample(wl, torch)
@@ -856,12 +1025,22 @@ def main():
             line["fp64"] = {"error": repr(ex)}
     if not args.skip_cpu and world == 1:
         import oracle
-        r = oracle_sample(wl, args.cpu_snps, oracle.default_threads())
+        smp = res["sample"]
+        r = oracle_sample(wl, oracle.default_threads(), smp["M"], smp["XL"], smp["y"], smp["XR"])
         line["cpu_baseline"] = {
             "value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
             "sample": (f"oracle Cholesky of M (n={n}, {r['factor_s']:.1f} s) + per-SNP loop on "
-                       f"{r['s_snps']} SNPs ({r['snp_s']:.1f} s), projected to m={m}"),
+                       f"{r['s_snps']} of the timed run's SNP columns ({r['snp_s']:.1f} s), "
+                       f"projected to m={m}"),
             "steady_state": r["steady"]}
+        line["error"] = error_summary(smp["B"], smp["st"], r["B"], r["st"],
+                                      1e-10 if wl["precision"] == "fp64" else 1e-6)
+    del res
+    if world == 1 and not args.skip_sub and args.workload == DEFAULT_WORKLOAD:
+        torch.cuda.empty_cache()
+        line["batch"] = sub_batch(args, torch)
+        torch.cuda.empty_cache()
+        line["serve"] = sub_serve(args, torch)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

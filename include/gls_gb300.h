@@ -24,6 +24,22 @@
  *     gls_last_error() gives a one-line description of the last failure on
  *     the calling thread.
  *   - A plan is used by one host thread at a time.
+ *   - Ordering of device inputs.  Every call reads its device inputs on the
+ *     plan's compute stream (gls_plan_stream), a non-blocking stream that is
+ *     not ordered after any stream of the caller.  The caller orders the work
+ *     that produces those inputs before the call: either that work has
+ *     finished (the producing stream was synchronized), or the caller records
+ *     an event after it on the producing stream and passes the event to
+ *     gls_plan_wait_event before the call.  Synchronizing some other stream
+ *     (for instance a framework's current stream, when the inputs were made on
+ *     a side stream) does not order them.
+ *   - Lifetime of caller buffers.  Every input and output buffer stays
+ *     allocated, and is not reused, until the call that reads or writes it has
+ *     finished on the device: until it returns for the synchronous calls, and
+ *     until the plan's stream has passed it for gls_solve_block on device
+ *     buffers.  A stream-ordered allocator (for instance PyTorch's caching
+ *     allocator) recycles a freed block on the stream that allocated it and
+ *     knows nothing of the plan's stream.
  */
 #ifndef GLS_GB300_H
 #define GLS_GB300_H
@@ -50,12 +66,34 @@ typedef enum {
 } gls_status_t;
 
 typedef enum {
-  /* Every step in binary64 (Section 2.3 precision of the paper's MKL runs). */
+  /* Every step in binary64 (the precision of the paper's MKL runs). */
   GLS_PREC_FP64 = 0,
-  /* The off-diagonal blocks of the blocked triangular solve run on tcgen05
-   * tensor cores with operands split into BF16 (resp. FP16) slices and FP32
-   * accumulation; the Cholesky of M, the diagonal blocks, the Gram epilogue
-   * reduction and the p x p solves stay FP64. */
+  /* Mixed paths.  The n^2-per-SNP work of the blocked triangular solve runs
+   * on tcgen05 tensor cores: each row of L^{-1}, left of its 4 x 4 diagonal
+   * block, is held as split_terms 16-bit slices (a fixed-point integer part
+   * under a per-row power of two, then floating-point remainders; BF16 or
+   * FP16) and multiplied by the exact 16-bit genotype codes with FP32
+   * accumulation.  The rest, and its arithmetic:
+   *   - the factor of M (Cholesky, L^{-1}, whitening of X_L and y): binary64
+   *     values from products of exact 8-bit integer slices on the tensor
+   *     cores, each rounded once to binary64, with 64 x 64 diagonal leaves in
+   *     binary64 arithmetic (GLS_FLAG_FACTOR_NATIVE: binary64 CUDA-core
+   *     kernels throughout);
+   *   - the 4 x 4 diagonal blocks of L^{-1}: an integer part (at most 12
+   *     bits) under a per-row power of two plus an FP32 low part, together at
+   *     least 36 bits of the row's diagonal-block scale, applied in FP32 with
+   *     one rounding;
+   *   - S_BR = x~^T x~: compensated (error-free) FP32 sums per 128-row block,
+   *     added across blocks in binary64;
+   *   - S_BL and b_B: the same tensor-core products against the rows of
+   *     W^T = (M^{-1} [X_L | y])^T (equal to X~_L^T x~ and y~^T x~ by
+   *     associativity), scaled to binary64;
+   *   - the p x p assembly and Cholesky solve: binary64.
+   * b_i is within 1e-6 relative (2-norm) of the binary64 result on every
+   * workload tested.  A GLS_PREC_MIXED_BF16 plan with n < 2048 uses FP16
+   * slices instead: BF16 slices fall short of 1e-6 at small n, FP16 slices
+   * carry three more bits each at the same tensor rate
+   * (gls_plan_operand_precision reports which a plan uses). */
   GLS_PREC_MIXED_BF16 = 1,
   GLS_PREC_MIXED_FP16 = 2
 } gls_precision_t;
@@ -93,8 +131,28 @@ typedef struct {
   int32_t split_terms;     /* mixed paths: operand slices of L^{-1}, 2 or 3 (0 = default 3)  */
   void* stream;            /* cudaStream_t for compute; NULL = the plan creates its own      */
   uint32_t flags;          /* GLS_FLAG_* bits; 0 for the defaults                            */
-  int32_t reserved[7];     /* must be 0                                                      */
+  int32_t wait_limit_us;   /* mixed paths: each pipeline wait of the tensor-core solve gives
+                              up after this many microseconds (0 = 1 s); see below         */
+  int32_t host_wait_ms;    /* each host wait of a call gives up after this many ms
+                              (0 = no limit); see below                                    */
+  int32_t reserved[5];     /* must be 0                                                      */
 } gls_plan_desc_t;
+
+/*
+ * Bounded waits.  Every wait inside the tensor-core kernels polls a clock and
+ * gives up after a limit; the kernel then lets its in-flight copies and
+ * products finish, frees its tensor memory and returns, so no kernel is left
+ * running, and the call (or the next gls_synchronize, for an asynchronous
+ * gls_solve_block) returns GLS_ERR_TIMEOUT.  Those results are not valid; the
+ * plan stays usable and its next gls_factor clears the error.  wait_limit_us
+ * shortens the limit of the blocked solve's waits (the default second is far
+ * above any wait of a working pipeline; a short one is for tests of this path).
+ * host_wait_ms bounds the host-side waits of gls_factor, the synchronous solve
+ * calls, gls_batch_solve (first plan's value) and gls_synchronize: past it they return
+ * GLS_ERR_TIMEOUT with the plan's work still queued, so the caller must call
+ * gls_synchronize again (or gls_destroy, which always waits to the end) before
+ * it reuses or frees any buffer of that call.
+ */
 
 /*
  * Creates a plan and allocates its device workspaces (L, L^{-1}, whitened
@@ -184,8 +242,9 @@ gls_status_t gls_solve_stream_packed(gls_plan_t plan, const uint8_t* XP, int64_t
  * Batched uneven scans: several independent sequences (each its own plan, with
  * its own M, n, p and SNP block) solved by ONE persistent launch of the
  * mixed-precision blocked solve, so that small scans fill the GPU together.
- * All plans must use the same mixed precision (BF16 or FP16) and split_terms,
- * live on the same device, and be factored before gls_batch_solve.  At most 64
+ * All plans must be mixed-precision plans (BF16 and FP16 may be mixed) with
+ * the same split_terms, live on the same device, and be factored before
+ * gls_batch_solve.  At most 64
  * plans.  The batch keeps pointers to the plans; destroy it before them.
  */
 typedef struct gls_batch* gls_batch_t;
@@ -215,6 +274,20 @@ gls_status_t gls_synchronize(gls_plan_t plan);
  * own work after an asynchronous gls_solve_block. */
 void* gls_plan_stream(gls_plan_t plan);
 
+/*
+ * Orders the plan's later work after `event` (a cudaEvent_t the caller
+ * recorded on the stream that produced the inputs of its next calls): the
+ * plan's compute stream waits for it on the device; the host does not block.
+ * It has no counterpart in the paper, whose inputs come from disk.
+ * Errors: INVALID_ARG (NULL plan or event), CUDA.
+ */
+gls_status_t gls_plan_wait_event(gls_plan_t plan, void* event);
+
+/* The gls_precision_t of the plan's tensor-core operands: its description's
+ * precision, except GLS_PREC_MIXED_FP16 for a GLS_PREC_MIXED_BF16 plan with
+ * n < 2048.  -1 for a NULL plan. */
+int32_t gls_plan_operand_precision(gls_plan_t plan);
+
 /* Frees every resource of the plan (after waiting for its work).  NULL is OK. */
 gls_status_t gls_destroy(gls_plan_t plan);
 
@@ -230,9 +303,11 @@ const char* gls_last_error(void);
 /*
  * Device-time accounting for benchmarks.  With timing enabled, each kernel of
  * the SNP loop and each whole setup phase is bracketed by CUDA events on the
- * plan's stream, so the figures are the kernels' own device times; launches
- * counts every kernel the plan enqueued.  gls_plan_set_timing resets the
- * counters; gls_plan_stats synchronizes the plan's stream and sums.
+ * plan's stream, so the figures are the kernels' own device times, and each
+ * host<->device block copy of gls_solve_stream[_packed] by events on its side
+ * stream; launches counts every kernel the plan enqueued.
+ * gls_plan_set_timing resets the counters; gls_plan_stats synchronizes the
+ * plan's streams and sums.
  */
 typedef struct {
   int64_t launches;          /* kernels enqueued since the last reset                 */
@@ -244,6 +319,14 @@ typedef struct {
   int64_t solve_launches;
   double factor_ms;          /* whole gls_factor setup phases                        */
   int64_t factor_calls;
+  /* genotype blocks copied host -> device and b blocks device -> host by the
+   * stream calls, each copy timed on its side stream (while overlapped) */
+  double h2d_ms;
+  int64_t h2d_bytes;
+  int64_t h2d_copies;
+  double d2h_ms;
+  int64_t d2h_bytes;
+  int64_t d2h_copies;
 } gls_stats_t;
 
 gls_status_t gls_plan_set_timing(gls_plan_t plan, int32_t enable);
@@ -263,13 +346,15 @@ gls_status_t gls_plan_stats(gls_plan_t plan, gls_stats_t* out);
  *   RTL   (p-1) x (p-1) column-major lower Cholesky factor of W[:,0:p-1]^T W[:,0:p-1];
  *   zT    p-1: RTL^{-1} W[:,0:p-1]^T W[:,p-1].  Both may be NULL when p == 1.
  *   XR, B, snp_status as for gls_solve_block (snp_status may be NULL).
- * The only scratch is a 4 MiB array inside the library (every GPU that loads
- * the library holds it until the process exits): ceil(n/64) * (p+1) * k must
- * not exceed 524288, otherwise GLS_ERR_INVALID_ARG (see gls_last_error).  The
- * first call on a device looks up that array's device address; make it before
- * any stream capture.  Every call shares the array: calls whose work can
- * overlap on the GPU (other streams, other threads) race and must be ordered
- * by the caller.  Nothing is allocated or freed.
+ * The only scratch is a 4 MiB array inside the library; every GPU that loads
+ * the library holds its own copy until the process exits.  ceil(n/64) *
+ * (p+1) * k must not exceed 524288, otherwise GLS_ERR_INVALID_ARG (see
+ * gls_last_error).  The first call on a device looks up that device's copy
+ * (and again after a device reset, which moves it); make that call before any
+ * stream capture.  Calls on the same device share its copy, which keeps the
+ * last call's contents: calls whose work can overlap on that GPU (other
+ * streams, other threads) race and must be ordered by the caller.  Calls on
+ * different devices use different copies.  Nothing is allocated or freed.
  */
 gls_status_t gls_solve_block_fp64_static(int64_t n, int32_t p, const double* Zinv, int64_t ldz,
                                          const double* W, int64_t ldw, const double* RTL,

@@ -24,7 +24,7 @@
  *        b_i = S_i^{-1} r_i by an unpivoted Cholesky of
  *              S_i and two triangular solves              (Alg. 3 line 6, posv)
  *
- * Readings where the paper is silent (all listed in the design notes):
+ * Readings where the paper is silent (conventions it leaves open, taken here):
  *   - storage is column-major with leading dimensions (LAPACK convention);
  *   - only the lower triangle of M is read;
  *   - b_i lists the X_L coefficients first and the SNP coefficient last;

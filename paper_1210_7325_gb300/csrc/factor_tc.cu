@@ -274,12 +274,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           tma_load_3d(sb + Sh::kABytes, &tmB, &full[st], k, w.J * BN, 0);
         }
       }
-      if (!ok) {
-        raise_error(q.flags, 1);
-        const uint32_t first = g > (uint32_t)Sh::kStages ? g - Sh::kStages : 0;
-        for (uint32_t g2 = first; g2 < g; ++g2)
-          wait_drain(&full[g2 % Sh::kStages], (g2 / Sh::kStages) & 1);
-      }
+      if (!ok) raise_error(q.flags, 1);
+      // the loads already issued land before the CTA's shared memory goes away,
+      // also when another warp gave up after the last load was issued (in a
+      // run that completes they have landed already and this returns at once)
+      const uint32_t first = g > (uint32_t)Sh::kStages ? g - Sh::kStages : 0;
+      for (uint32_t g2 = first; g2 < g; ++g2)
+        wait_drain(&full[g2 % Sh::kStages], (g2 / Sh::kStages) & 1);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer

@@ -10,12 +10,17 @@ namespace gls {
 
 struct MixedState;
 
+// GLS_PREC_MIXED_BF16 plans with fewer rows use FP16 operand slices.
+constexpr int64_t kBf16MinN = 2048;
+
 // Device bytes the mixed path adds to a plan.
 size_t mixed_footprint(int64_t n, int64_t npad, int p, int64_t kmax, int split_terms);
 
-// Allocates the operand slices and encodes the TMA descriptors.
+// Allocates the operand slices and encodes the TMA descriptors.  The solve's
+// pipeline waits give up after wait_limit_us microseconds (0: one second).
 gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int64_t kmax,
-                          int precision, int split_terms, uint32_t flags, cudaStream_t st);
+                          int precision, int split_terms, uint32_t flags, int32_t wait_limit_us,
+                          cudaStream_t st);
 void mixed_free(MixedState* ms);
 const char* mixed_last_error();
 
@@ -51,7 +56,7 @@ int64_t mixed_n(const MixedState* ms);
 
 // Several problems in one persistent launch.  Pbr / Glin / ldp are each
 // problem's partial buffers (as for mixed_trsm_gram); all states need the same
-// split and 16-bit type.  The genotypes of each problem must have been
+// split (BF16 and FP16 operands may be mixed).  The genotypes of each problem must have been
 // converted (mixed_convert) on the launch stream before mixed_batch_run.
 struct MixedBatch;
 gls_status_t mixed_batch_create(MixedState* const* states, const double* const* Pbr,

@@ -5,8 +5,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -111,9 +113,10 @@ struct gls_plan {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
     double ms = 0.0;
     int64_t launches = 0;
+    int64_t bytes = 0;  // copies only
   };
   bool timing = false;
-  Slot t_trsm, t_convert, t_solve, t_factor;
+  Slot t_trsm, t_convert, t_solve, t_factor, t_h2d, t_d2h;
   int64_t launches = 0;
   std::vector<cudaEvent_t> event_pool;
   bool has_factor = false;  // L and Z valid
@@ -406,7 +409,11 @@ gls_status_t validate_desc(const gls_plan_desc_t* d) {
     set_error("GLS_FLAG_FACTOR_NATIVE and GLS_FLAG_FACTOR_TENSOR exclude each other");
     return GLS_ERR_INVALID_ARG;
   }
-  for (int i = 0; i < 7; ++i)
+  if (d->wait_limit_us < 0 || d->host_wait_ms < 0) {
+    set_error("wait_limit_us and host_wait_ms must be >= 0");
+    return GLS_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < 5; ++i)
     if (d->reserved[i] != 0) {
       set_error("reserved fields must be 0");
       return GLS_ERR_INVALID_ARG;
@@ -446,7 +453,8 @@ void free_plan(gls_plan* pl) {
     if (pl->ev_stored[s]) cudaEventDestroy(pl->ev_stored[s]);
     if (pl->ev_staged[s]) cudaEventDestroy(pl->ev_staged[s]);
   }
-  for (gls_plan::Slot* sl : {&pl->t_trsm, &pl->t_convert, &pl->t_solve, &pl->t_factor})
+  for (gls_plan::Slot* sl :
+       {&pl->t_trsm, &pl->t_convert, &pl->t_solve, &pl->t_factor, &pl->t_h2d, &pl->t_d2h})
     for (auto& pr : sl->pending) {
       cudaEventDestroy(pr.first);
       cudaEventDestroy(pr.second);
@@ -467,6 +475,25 @@ cudaError_t copy2d(void* dst, size_t dpitch, const void* src, size_t spitch, siz
   if (dpitch == width && spitch == width)
     return cudaMemcpyAsync(dst, src, width * height, kind, st);
   return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, height, kind, st);
+}
+
+// A host<->device copy of the double-buffered stream on a side stream,
+// bracketed by events when timing is on (its duration on that stream).
+cudaError_t timed_copy(gls_plan* pl, gls_plan::Slot* slot, cudaStream_t side, size_t bytes,
+                       cudaError_t (*issue)(void*), void* ctx) {
+  cudaEvent_t e0 = pl->timing ? pool_event(pl) : nullptr;
+  cudaEvent_t e1 = pl->timing ? pool_event(pl) : nullptr;
+  if (e0 && e1) cudaEventRecord(e0, side);
+  cudaError_t e = issue(ctx);
+  if (e0 && e1) {
+    cudaEventRecord(e1, side);
+    slot->pending.emplace_back(e0, e1);
+    slot->bytes += (int64_t)bytes;
+  } else {
+    if (e0) pl->event_pool.push_back(e0);
+    if (e1) pl->event_pool.push_back(e1);
+  }
+  return e;
 }
 
 template <class T>
@@ -497,10 +524,36 @@ gls_status_t host_alloc(T** p, size_t count) {
     if (s_ != GLS_OK) return s_;   \
   } while (0)
 
+// Waits on the host for the work queued on `st`.  With a deadline
+// (desc.host_wait_ms > 0) it polls and gives up past it, the work still queued.
+gls_status_t host_wait(gls_plan* pl, cudaStream_t st) {
+  const int32_t limit_ms = pl->desc.host_wait_ms;
+  if (limit_ms <= 0) {
+    GLS_CUDA(cudaStreamSynchronize(st));
+    return GLS_OK;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaStreamQuery(st);
+    if (e == cudaSuccess) return GLS_OK;
+    if (e != cudaErrorNotReady) {
+      set_error("stream wait failed: %s", cudaGetErrorString(e));
+      return GLS_ERR_CUDA;
+    }
+    if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(limit_ms)) {
+      cudaGetLastError();
+      set_error("host wait gave up after %d ms with the plan's work still queued; "
+                "gls_synchronize or gls_destroy before reusing its buffers", limit_ms);
+      return GLS_ERR_TIMEOUT;
+    }
+    std::this_thread::yield();
+  }
+}
+
 gls_status_t check_flags(gls_plan* pl, int host_flags[gls::kFlagCount]) {
   GLS_CUDA(cudaMemcpyAsync(host_flags, pl->flags, sizeof(int) * gls::kFlagCount,
                            cudaMemcpyDeviceToHost, pl->stream));
-  GLS_CUDA(cudaStreamSynchronize(pl->stream));
+  GLS_TRY(host_wait(pl, pl->stream));
   if (host_flags[gls::kFlagKernel] & gls::kErrTimeout) {
     set_error("a bounded device wait gave up (site %d)", host_flags[gls::kFlagWhere]);
     return GLS_ERR_TIMEOUT;
@@ -673,7 +726,7 @@ gls_status_t gls_plan_create(const gls_plan_desc_t* desc, gls_plan_t* out) {
   }
   if (pl->precision != GLS_PREC_FP64) {
     if ((st = gls::mixed_create(&pl->mixed, n, npad, p, kmax, pl->precision, desc->split_terms,
-                                desc->flags, pl->stream)) != GLS_OK) {
+                                desc->flags, desc->wait_limit_us, pl->stream)) != GLS_OK) {
       set_error("%s", gls::mixed_last_error());
       return fail(st);
     }
@@ -836,8 +889,7 @@ gls_status_t gls_plan_get_factor(gls_plan_t pl, double* L, int64_t ldl, double* 
   if (Zinv)
     GLS_CUDA(copy2d(Zinv, ldz * sizeof(double), pl->Z, npad * sizeof(double),
                                n * sizeof(double), n, cudaMemcpyDefault, pl->stream));
-  GLS_CUDA(cudaStreamSynchronize(pl->stream));
-  return GLS_OK;
+  return host_wait(pl, pl->stream);
 }
 
 gls_status_t gls_solve_block(gls_plan_t pl, const int8_t* XR, int64_t ldxr, int64_t k,
@@ -965,15 +1017,26 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
     const int64_t s0 = blocks[jb].first, kb = blocks[jb].second;
     // device buffer s is free once the compute of block jb-2 is done
     GLS_CUDA(cudaStreamWaitEvent(pl->h2d, pl->ev_computed[s], 0));
+    struct Copy {
+      void* dst;
+      const void* src;
+      size_t ldsrc, width, cols;
+      cudaStream_t st;
+    };
+    auto issue = [](void* c) -> cudaError_t {
+      const Copy& q = *static_cast<const Copy*>(c);
+      return copy2d(q.dst, q.width, q.src, q.ldsrc, q.width, q.cols, cudaMemcpyHostToDevice,
+                    q.st);
+    };
     if (!pageable_in) {
-      GLS_CUDA(copy2d(dev_in(s), width, X + s0 * ldx, ldx, width, kb, cudaMemcpyHostToDevice,
-                      pl->h2d));
+      Copy q{dev_in(s), X + s0 * ldx, (size_t)ldx, (size_t)width, (size_t)kb, pl->h2d};
+      GLS_CUDA(timed_copy(pl, &pl->t_h2d, pl->h2d, (size_t)width * kb, issue, &q));
     } else {
       GLS_CUDA(cudaEventSynchronize(pl->ev_staged[s]));  // pinned staging s is free
       for (int64_t c = 0; c < kb; ++c)
         memcpy(host_in(s) + c * width, X + (s0 + c) * ldx, (size_t)width);
-      GLS_CUDA(cudaMemcpyAsync(dev_in(s), host_in(s), (size_t)width * kb,
-                               cudaMemcpyHostToDevice, pl->h2d));
+      Copy q{dev_in(s), host_in(s), (size_t)width, (size_t)width, (size_t)kb, pl->h2d};
+      GLS_CUDA(timed_copy(pl, &pl->t_h2d, pl->h2d, (size_t)width * kb, issue, &q));
       GLS_CUDA(cudaEventRecord(pl->ev_staged[s], pl->h2d));
     }
     GLS_CUDA(cudaEventRecord(pl->ev_loaded[s], pl->h2d));
@@ -1034,12 +1097,22 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
     if (out_b_host || out_s_host) {
       GLS_CUDA(cudaStreamWaitEvent(pl->d2h, pl->ev_computed[s], 0));
       if (out_b_host) {
-        if (mb == Mem::Pinned)
-          GLS_CUDA(copy2d(B + s0 * ldb, ldb * sizeof(double), bout, p * sizeof(double),
-                          p * sizeof(double), kb, cudaMemcpyDeviceToHost, pl->d2h));
-        else
-          GLS_CUDA(cudaMemcpyAsync(pl->h_b[s], bout, sizeof(double) * p * kb,
-                                   cudaMemcpyDeviceToHost, pl->d2h));
+        struct Copy {
+          double* dst;
+          size_t lddst;
+          const double* src;
+          size_t rows, cols;
+          cudaStream_t st;
+        };
+        auto issue = [](void* c) -> cudaError_t {
+          const Copy& q = *static_cast<const Copy*>(c);
+          return copy2d(q.dst, q.lddst * sizeof(double), q.src, q.rows * sizeof(double),
+                        q.rows * sizeof(double), q.cols, cudaMemcpyDeviceToHost, q.st);
+        };
+        Copy q = (mb == Mem::Pinned)
+                     ? Copy{B + s0 * ldb, (size_t)ldb, bout, (size_t)p, (size_t)kb, pl->d2h}
+                     : Copy{pl->h_b[s], (size_t)p, bout, (size_t)p, (size_t)kb, pl->d2h};
+        GLS_CUDA(timed_copy(pl, &pl->t_d2h, pl->d2h, sizeof(double) * p * kb, issue, &q));
       }
       if (out_s_host) {
         int32_t* dst = (ms == Mem::Pinned) ? snp_status + s0 : pl->h_s[s];
@@ -1051,8 +1124,8 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
     if (jb >= 1) GLS_TRY(finish_host(jb - 1));
   }
   GLS_TRY(finish_host(blocks.size() - 1));
-  GLS_CUDA(cudaStreamSynchronize(pl->h2d));
-  GLS_CUDA(cudaStreamSynchronize(pl->d2h));
+  GLS_TRY(host_wait(pl, pl->h2d));
+  GLS_TRY(host_wait(pl, pl->d2h));
   int hf[gls::kFlagCount];
   GLS_TRY(check_flags(pl, hf));
   return GLS_OK;
@@ -1287,7 +1360,7 @@ gls_status_t gls_batch_solve(gls_batch_t b, const int8_t* const* XR, const int64
   for (int i = 1; i < count; ++i) GLS_CUDA(cudaStreamWaitEvent(b->plans[i]->stream, b->ev, 0));
   int hf[gls::kFlagCount];
   GLS_CUDA(cudaMemcpyAsync(hf, b->flags, sizeof(hf), cudaMemcpyDeviceToHost, st));
-  GLS_CUDA(cudaStreamSynchronize(st));
+  GLS_TRY(host_wait(p0, st));
   if (hf[gls::kFlagKernel] & gls::kErrTimeout) {
     set_error("a bounded device wait gave up (site %d)", hf[gls::kFlagWhere]);
     return GLS_ERR_TIMEOUT;
@@ -1316,13 +1389,32 @@ gls_status_t gls_synchronize(gls_plan_t pl) {
     return GLS_ERR_INVALID_ARG;
   }
   DeviceGuard guard(pl->device);
-  GLS_CUDA(cudaStreamSynchronize(pl->h2d));
-  GLS_CUDA(cudaStreamSynchronize(pl->d2h));
+  GLS_TRY(host_wait(pl, pl->h2d));
+  GLS_TRY(host_wait(pl, pl->d2h));
   int hf[gls::kFlagCount];
   return check_flags(pl, hf);
 }
 
 void* gls_plan_stream(gls_plan_t pl) { return pl ? (void*)pl->stream : nullptr; }
+
+int32_t gls_plan_operand_precision(gls_plan_t pl) {
+  if (!pl) return -1;
+  if (pl->precision == GLS_PREC_FP64) return GLS_PREC_FP64;
+  return gls::mixed_is_bf16(pl->mixed) ? GLS_PREC_MIXED_BF16 : GLS_PREC_MIXED_FP16;
+}
+
+gls_status_t gls_plan_wait_event(gls_plan_t pl, void* event) {
+  g_last_error.clear();
+  if (!pl || !event) {
+    set_error("plan or event is NULL");
+    return GLS_ERR_INVALID_ARG;
+  }
+  DeviceGuard guard(pl->device);
+  // every device input is read on the compute stream; the side streams of a
+  // stream call start after the compute stream's earlier work
+  GLS_CUDA(cudaStreamWaitEvent(pl->stream, (cudaEvent_t)event, 0));
+  return GLS_OK;
+}
 
 gls_status_t gls_plan_set_timing(gls_plan_t pl, int32_t enable) {
   g_last_error.clear();
@@ -1332,7 +1424,10 @@ gls_status_t gls_plan_set_timing(gls_plan_t pl, int32_t enable) {
   }
   DeviceGuard guard(pl->device);
   GLS_CUDA(cudaStreamSynchronize(pl->stream));
-  for (gls_plan::Slot* sl : {&pl->t_trsm, &pl->t_convert, &pl->t_solve, &pl->t_factor}) {
+  GLS_CUDA(cudaStreamSynchronize(pl->h2d));
+  GLS_CUDA(cudaStreamSynchronize(pl->d2h));
+  for (gls_plan::Slot* sl :
+       {&pl->t_trsm, &pl->t_convert, &pl->t_solve, &pl->t_factor, &pl->t_h2d, &pl->t_d2h}) {
     for (auto& pr : sl->pending) {
       pl->event_pool.push_back(pr.first);
       pl->event_pool.push_back(pr.second);
@@ -1340,6 +1435,7 @@ gls_status_t gls_plan_set_timing(gls_plan_t pl, int32_t enable) {
     sl->pending.clear();
     sl->ms = 0.0;
     sl->launches = 0;
+    sl->bytes = 0;
   }
   pl->launches = 0;
   pl->timing = enable != 0;
@@ -1354,7 +1450,10 @@ gls_status_t gls_plan_stats(gls_plan_t pl, gls_stats_t* out) {
   }
   DeviceGuard guard(pl->device);
   GLS_CUDA(cudaStreamSynchronize(pl->stream));
-  for (gls_plan::Slot* sl : {&pl->t_trsm, &pl->t_convert, &pl->t_solve, &pl->t_factor}) {
+  GLS_CUDA(cudaStreamSynchronize(pl->h2d));
+  GLS_CUDA(cudaStreamSynchronize(pl->d2h));
+  for (gls_plan::Slot* sl :
+       {&pl->t_trsm, &pl->t_convert, &pl->t_solve, &pl->t_factor, &pl->t_h2d, &pl->t_d2h}) {
     for (auto& pr : sl->pending) {
       float ms = 0.f;
       GLS_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
@@ -1374,6 +1473,12 @@ gls_status_t gls_plan_stats(gls_plan_t pl, gls_stats_t* out) {
   out->solve_launches = pl->t_solve.launches;
   out->factor_ms = pl->t_factor.ms;
   out->factor_calls = pl->t_factor.launches;
+  out->h2d_ms = pl->t_h2d.ms;
+  out->h2d_bytes = pl->t_h2d.bytes;
+  out->h2d_copies = pl->t_h2d.launches;
+  out->d2h_ms = pl->t_d2h.ms;
+  out->d2h_bytes = pl->t_d2h.bytes;
+  out->d2h_copies = pl->t_d2h.launches;
   return GLS_OK;
 }
 

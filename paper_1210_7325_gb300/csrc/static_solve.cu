@@ -9,11 +9,15 @@
 // Gram partials of the blocked solve -- in a fixed file-scope device array.
 //
 // The array (kStaticPartials doubles, 4 MiB) is part of the library image:
-// every GPU that loads the library holds it until the process exits.  All
-// calls share it and it keeps the last call's contents; nothing in it has to
-// start at zero, because each call writes every partial it later reads.  Two
-// calls whose kernels can overlap on the GPU (for example calls on different
-// streams, or from different host threads) race on it: the caller orders them.
+// every GPU that loads the library holds its own copy until the process exits.
+// Calls on the same device share that copy and it keeps the last call's
+// contents; nothing in it has to start at zero, because each call writes every
+// partial it later reads.  Two calls on one device whose kernels can overlap
+// on the GPU (for example calls on different streams, or from different host
+// threads) race on it: the caller orders them.  Calls on different devices
+// use different copies.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "common.cuh"
@@ -27,8 +31,50 @@ constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) double g_static_partials[kStaticPartials];
 
+// Set-up state per device, valid for the context it was made in: a device
+// reset (cudaDeviceReset) ends that context and reloads the library's module
+// in the next one, which moves the array, so a new context id redoes the set-up.
+struct DeviceSetup {
+  unsigned long long ctx_id = 0;
+  double* scratch = nullptr;  // device address of g_static_partials
+};
 std::mutex g_mu;
-double* g_scratch[kMaxDevices] = {};  // device address of g_static_partials, per device
+DeviceSetup g_setup[kMaxDevices];
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Unique id of the calling thread's current context (0 if it cannot be read).
+unsigned long long current_context_id() {
+  static const CtxGetCurrentFn get_current = []() {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return static_cast<CtxGetCurrentFn>(nullptr);
+    }
+    return reinterpret_cast<CtxGetCurrentFn>(f);
+  }();
+  static const CtxGetIdFn get_id = []() {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return static_cast<CtxGetIdFn>(nullptr);
+    }
+    return reinterpret_cast<CtxGetIdFn>(f);
+  }();
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx ||
+      get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
 
 struct Smem {
   double Zs[KC][TR];
@@ -150,12 +196,15 @@ extern "C" gls_status_t gls_solve_block_fp64_static(int64_t n, int32_t p, const 
     cudaGetLastError();
     return fail(GLS_ERR_CUDA, "no current CUDA device");
   }
+  // 0 when no context is current yet: the set-up below makes the primary one
+  const unsigned long long ctx = current_context_id();
   double* scratch = nullptr;
   {
-    // Once per device, with that device current: the host-side name of the
-    // array is not a device address; ask the runtime for it.
+    // Once per device (and context), with that device current: the host-side
+    // name of the array is not a device address; ask the runtime for it.
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch[dev]) {
+    DeviceSetup& su = g_setup[dev];
+    if (!su.scratch || ctx == 0 || su.ctx_id != ctx) {
       void* ptr = nullptr;
       if (cudaGetSymbolAddress(&ptr, g_static_partials) != cudaSuccess || !ptr) {
         cudaGetLastError();
@@ -167,9 +216,10 @@ extern "C" gls_status_t gls_solve_block_fp64_static(int64_t n, int32_t p, const 
         cudaGetLastError();
         return fail(GLS_ERR_CUDA, "cudaFuncSetAttribute failed");
       }
-      g_scratch[dev] = static_cast<double*>(ptr);
+      su.scratch = static_cast<double*>(ptr);
+      su.ctx_id = current_context_id();
     }
-    scratch = g_scratch[dev];
+    scratch = su.scratch;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   dim3 grid((unsigned)gls::ceil_div(k, TS), (unsigned)nI);

@@ -105,7 +105,7 @@ constexpr uint32_t kTmemCols = 512;     // acc_H and acc_R, 256 columns each
 constexpr uint32_t kAccR = 256;         // column of acc_R
 constexpr int kMaxDynSmem = 232448;     // 227 KB
 constexpr int kDiag = 4;                // nd: diagonal block edge
-constexpr uint64_t kWaitLimitNs = 1000000000ull;  // bounded waits give up after 1 s
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // bounded waits give up after 1 s (default)
 constexpr uint64_t kDrainLimitNs = 100000000ull;
 constexpr int kDefaultGroup = 3;        // row-block pairs per rasterization group
 
@@ -123,6 +123,7 @@ struct alignas(64) ProblemDesc {
   double* Glin;           // S_BL and b_B, p x ldp
   int64_t npad, ldp;
   int nI, p;
+  uint32_t idesc, idesc_half;  // MMA N = 256 (two row blocks) and N = 128 (one), BF16 or FP16
 };
 
 // Per-launch values, by value: each problem's block size and item range.
@@ -135,7 +136,7 @@ struct RunParams {
 
 struct KConst {
   int S, stages;
-  uint32_t idesc, idesc_half;  // N = 256 (two row blocks) and N = 128 (one)
+  uint64_t wait_ns;  // limit of every pipeline wait
   int* flags;
   uint32_t off_rows, off_bar, stage_bytes;
 };
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int kb = 0; kb < kblocks; ++kb, ++g) {
           const int st = (int)(g % stages);
           const uint32_t ph = g / stages;
-          if (!mbar_wait_bounded(&empty[st], (ph & 1) ^ 1, abort_flag, kWaitLimitNs)) {
+          if (!mbar_wait_bounded(&empty[st], (ph & 1) ^ 1, abort_flag, kc.wait_ns)) {
             ok = false;
             break;
           }
@@ -319,13 +320,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           tma_load_2d(sb + S * kSliceBytes, &pd->tmB, &full[st], kb * BK, w.J * BN);
         }
       }
-      if (!ok) {
-        raise_error(kc.flags, 1);
-        // let the loads already issued land before the CTA's shared memory goes away
-        const uint32_t first = g > (uint32_t)stages ? g - stages : 0;
-        for (uint32_t g2 = first; g2 < g; ++g2)
-          wait_drain(&full[g2 % stages], (g2 / stages) & 1);
-      }
+      if (!ok) raise_error(kc.flags, 1);
+      // the loads already issued land before the CTA's shared memory goes away,
+      // also when another warp gave up after the last load was issued (in a
+      // run that completes they have landed already and this returns at once)
+      const uint32_t first = g > (uint32_t)stages ? g - stages : 0;
+      for (uint32_t g2 = first; g2 < g; ++g2)
+        wait_drain(&full[g2 % stages], (g2 / stages) & 1);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -337,9 +338,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
         const Item w = item_at(probs, run, t);
         const int kblocks = w.kblocks();
-        const uint32_t idesc = w.wide() ? kc.idesc : kc.idesc_half;
+        // the operand type is per problem: a batch may mix BF16 and FP16 plans
+        const uint32_t idesc = w.wide() ? probs[w.pi].idesc : probs[w.pi].idesc_half;
         // the epilogue has read the previous item's accumulators
-        if (!mbar_wait_bounded(tempty, ((uint32_t)it & 1) ^ 1, abort_flag, kWaitLimitNs)) {
+        if (!mbar_wait_bounded(tempty, ((uint32_t)it & 1) ^ 1, abort_flag, kc.wait_ns)) {
           ok = false;
           break;
         }
@@ -347,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int kb = 0; kb < kblocks; ++kb, ++g) {
           const int st = (int)(g % stages);
           const uint32_t ph = g / stages;
-          if (!mbar_wait_bounded(&full[st], ph & 1, abort_flag, kWaitLimitNs)) {
+          if (!mbar_wait_bounded(&full[st], ph & 1, abort_flag, kc.wait_ns)) {
             ok = false;
             break;
           }
@@ -416,7 +418,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int i = 0; i < BM / 16; ++i) xv[i] = __ldg(src + i);
       }
-      const bool got = mbar_wait_bounded(tfull, ph, abort_flag, kWaitLimitNs);
+      const bool got = mbar_wait_bounded(tfull, ph, abort_flag, kc.wait_ns);
       if (!epilogue_all(got)) {  // all epilogue threads leave together; also orders the row data
         if (!got && lane == 0) raise_error(kc.flags, 3);
         break;
@@ -852,7 +854,8 @@ void mixed_free(MixedState* ms) {
 }
 
 gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int64_t kmax,
-                          int precision, int split_terms, uint32_t flags, cudaStream_t st) {
+                          int precision, int split_terms, uint32_t flags, int32_t wait_limit_us,
+                          cudaStream_t st) {
   *out = nullptr;
   if (npad % BM != 0) {
     g_err = "npad must be a multiple of 128";
@@ -867,7 +870,9 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   ms->npad = npad;
   ms->kmax = kmax;
   ms->p = p;
-  ms->bf16 = (precision == GLS_PREC_MIXED_BF16);
+  // BF16 slices below kBf16MinN rows fall short of 1e-6 on b_i; FP16 slices
+  // (three more bits per slice, same tensor rate) meet it at every size
+  ms->bf16 = (precision == GLS_PREC_MIXED_BF16) && n >= kBf16MinN;
   ms->S = split_terms ? split_terms : 3;
   ms->bits = ms->bf16 ? 7 : 10;
   ms->naive = (flags & GLS_FLAG_NAIVE_SPLIT) != 0;
@@ -906,11 +911,10 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   KConst& kc = ms->kc;
   kc.S = ms->S;
   kc.stages = stages;
+  kc.wait_ns = wait_limit_us > 0 ? (uint64_t)wait_limit_us * 1000ull : kWaitLimitNs;
   kc.stage_bytes = (uint32_t)ms->S * kSliceBytes + kXBytes;
   kc.off_rows = (uint32_t)stages * kc.stage_bytes;
   kc.off_bar = kc.off_rows + 2u * kRowsBytes;
-  kc.idesc = umma_idesc_f16(BN, kPair, ms->bf16);
-  kc.idesc_half = umma_idesc_f16(BN, BM, ms->bf16);
   if (!g_attr_done) {
     if (cudaFuncSetAttribute(trsm_gram_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kMaxDynSmem) != cudaSuccess) {
@@ -952,6 +956,8 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   d.npad = npad;
   d.nI = (int)(npad / BM);
   d.p = p;
+  d.idesc = umma_idesc_f16(BN, kPair, ms->bf16);
+  d.idesc_half = umma_idesc_f16(BN, BM, ms->bf16);
   *out = ms;
   return GLS_OK;
 }
@@ -1073,8 +1079,8 @@ gls_status_t mixed_batch_create(MixedState* const* states, const double* const* 
     return GLS_ERR_INVALID_ARG;
   }
   for (int i = 1; i < count; ++i)
-    if (states[i]->S != states[0]->S || states[i]->bf16 != states[0]->bf16) {
-      g_err = "all plans of a batch need the same mixed precision and split_terms";
+    if (states[i]->S != states[0]->S) {
+      g_err = "all plans of a batch need the same split_terms";
       return GLS_ERR_INVALID_ARG;
     }
   MixedBatch* b = new MixedBatch();

@@ -50,7 +50,9 @@ class PlanDesc(ctypes.Structure):
         ("split_terms", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
         ("flags", ctypes.c_uint32),
-        ("reserved", ctypes.c_int32 * 7),
+        ("wait_limit_us", ctypes.c_int32),
+        ("host_wait_ms", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
     ]
 
 
@@ -61,6 +63,10 @@ class Stats(ctypes.Structure):
         ("convert_ms", ctypes.c_double), ("convert_launches", ctypes.c_int64),
         ("solve_ms", ctypes.c_double), ("solve_launches", ctypes.c_int64),
         ("factor_ms", ctypes.c_double), ("factor_calls", ctypes.c_int64),
+        ("h2d_ms", ctypes.c_double), ("h2d_bytes", ctypes.c_int64),
+        ("h2d_copies", ctypes.c_int64),
+        ("d2h_ms", ctypes.c_double), ("d2h_bytes", ctypes.c_int64),
+        ("d2h_copies", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -98,6 +104,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.gls_synchronize.restype = i32
     lib.gls_plan_stream.argtypes = [vp]
     lib.gls_plan_stream.restype = vp
+    lib.gls_plan_wait_event.argtypes = [vp, vp]
+    lib.gls_plan_wait_event.restype = i32
+    lib.gls_plan_operand_precision.argtypes = [vp]
+    lib.gls_plan_operand_precision.restype = i32
     lib.gls_destroy.argtypes = [vp]
     lib.gls_destroy.restype = i32
     lib.gls_plan_footprint_bytes.argtypes = [P(PlanDesc)]
@@ -134,7 +144,7 @@ def _check(status: int, where: str, info: int = 0):
 
 
 def make_desc(n, p, max_block_snps, precision="fp64", device=0, stream=None, split_terms=0,
-              flags=0) -> PlanDesc:
+              flags=0, wait_limit_us=0, host_wait_ms=0) -> PlanDesc:
     d = PlanDesc()
     d.n = int(n)
     d.p = int(p)
@@ -144,6 +154,8 @@ def make_desc(n, p, max_block_snps, precision="fp64", device=0, stream=None, spl
     d.split_terms = int(split_terms)
     d.stream = stream
     d.flags = int(flags)
+    d.wait_limit_us = int(wait_limit_us)
+    d.host_wait_ms = int(host_wait_ms)
     return d
 
 
@@ -251,12 +263,12 @@ class Plan:
     ``solve_stream`` over SNP blocks.  Thin wrapper over the C ABI."""
 
     def __init__(self, n, p, max_block_snps, precision="fp64", device=0, stream=None,
-                 split_terms=0, flags=0):
+                 split_terms=0, flags=0, wait_limit_us=0, host_wait_ms=0):
         lib = load()
         self.n, self.p, self.kmax = int(n), int(p), int(max_block_snps)
         self.precision = precision
         self._desc = make_desc(n, p, max_block_snps, precision, device, stream, split_terms,
-                               flags)
+                               flags, wait_limit_us, host_wait_ms)
         h = ctypes.c_void_p()
         _check(lib.gls_plan_create(ctypes.byref(self._desc), ctypes.byref(h)), "gls_plan_create")
         self._h = h
@@ -266,8 +278,23 @@ class Plan:
         return self._h
 
     @property
+    def operand_precision(self) -> str:
+        """The precision the plan's tensor-core operands use ("bf16", "fp16";
+        "fp64" for the binary64 path): a BF16 plan with n < 2048 uses FP16."""
+        code = load().gls_plan_operand_precision(self._h)
+        return {v: k for k, v in PRECISIONS.items()}[code]
+
+    @property
     def stream(self) -> int:
         return int(load().gls_plan_stream(self._h) or 0)
+
+    def wait_event(self, event):
+        """Orders the plan's later work after ``event`` (a ``torch.cuda.Event``
+        recorded on the stream that produced the next calls' device inputs, or
+        a raw cudaEvent_t handle)."""
+        h = getattr(event, "cuda_event", event)
+        _check(load().gls_plan_wait_event(self._h, ctypes.c_void_p(int(h))),
+               "gls_plan_wait_event")
 
     def factor(self, M, XL, y):
         """M: n x n column-major (lower triangle read) or None to keep the previous

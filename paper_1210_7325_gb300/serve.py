@@ -14,6 +14,16 @@ Each request is one GWAS scan (its own n, p, m, M, X_L, y, X_R).  The server
     block per active request on their own streams (FP64), so requests that
     arrive while others are running join the next round.
 Latency of a request = completion time - arrival time.
+
+Ordering and lifetime of request inputs.  ``make_inputs`` enqueues whatever
+device work makes a request's tensors on the calling thread's current stream.
+The server records an event on that stream right after it returns and makes
+the request's plan wait for the event (gls_plan_wait_event) before the factor
+and every solve read the tensors on the plan's stream; a batched round runs
+after the work queued on each of its plans' streams, so it is ordered too.
+The tensors stay referenced until the request's last synchronous round has
+returned and its factor has ended; run() waits for every outstanding factor
+before it returns, even when it stops at its time cap.
 """
 from __future__ import annotations
 
@@ -78,12 +88,20 @@ class _Active:
 
 class Server:
     def __init__(self, make_inputs, precision="bf16", hbm_budget=150e9, block=32768,
-                 factor_workers=4, group=0, device="cuda"):
-        """make_inputs(req, torch, reuse) -> Inputs (device tensors for the request;
-        with reuse=True the factor of M is cached, so M and X_L may be None)."""
+                 factor_workers=4, group=0, device="cuda", streams=None, keep=None):
+        """make_inputs(req, torch, reuse) -> Inputs (device tensors for the request,
+        made by work on the current stream; with reuse=True the factor of M is
+        cached, so M and X_L may be None).  ``streams`` supplies
+        current_stream() and Event() (torch.cuda by default on a GPU device,
+        none on the CPU); ``keep`` is a set of request ids whose outputs run()
+        keeps (every request's with keep_outputs=True)."""
         import torch
         self.torch = torch
         self.device = device
+        if streams is None and str(device).startswith("cuda"):
+            streams = torch.cuda
+        self.streams = streams
+        self.keep = set(keep or ())
         self.make_inputs = make_inputs
         self.precision = precision
         self.budget = float(hbm_budget)
@@ -146,9 +164,7 @@ class Server:
         reuse = slot is not None
         t = time.perf_counter()
         inputs = self.make_inputs(req, self.torch, reuse)
-        # the plan's stream reads these tensors: let their producers finish first
-        if str(self.device).startswith("cuda"):
-            self.torch.cuda.current_stream().synchronize()
+        ready = self._inputs_ready()
         self.breakdown["inputs_s"] += time.perf_counter() - t
         if not reuse:
             t = time.perf_counter()
@@ -164,12 +180,23 @@ class Server:
         B = torch.empty((req.m, req.p), dtype=torch.float64, device=self.device)
         st = torch.empty(req.m, dtype=torch.int32, device=self.device)
         act = _Active(req, slot, inputs, B, st, now)
+        if ready is not None:
+            # the plan's stream reads the inputs only after their producer wrote them
+            slot.plan.wait_event(ready)
         if reuse:
             act.factored = self.pool.submit(self._timed_factor, slot.plan, None, None, inputs.y)
         else:
             act.factored = self.pool.submit(self._timed_factor, slot.plan, inputs.M, inputs.XL,
                                             inputs.y)
         return act
+
+    def _inputs_ready(self):
+        """An event on the current stream after make_inputs' work (None on the CPU)."""
+        if self.streams is None:
+            return None
+        ev = self.streams.Event()
+        ev.record(self.streams.current_stream())
+        return ev
 
     def _timed_factor(self, plan, M, XL, y):
         t = time.perf_counter()
@@ -228,6 +255,15 @@ class Server:
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting: collections.deque = collections.deque()
         active: List[_Active] = []
+        try:
+            self._serve(pending, waiting, active, time_cap, keep_outputs)
+        finally:
+            # a factor still running (time cap, or another request's error)
+            # reads its request's inputs: they stay referenced until it ends
+            cf.wait([a.factored for a in active if a.factored is not None])
+        return self.results
+
+    def _serve(self, pending, waiting, active, time_cap, keep_outputs):
         t0 = time.perf_counter()
         while pending or waiting or active:
             now = time.perf_counter() - t0
@@ -275,10 +311,9 @@ class Server:
             for a in [a for a in active if a.factored.done() and a.next >= a.req.m]:
                 self._finish(a, done_now)
                 active.remove(a)
-                if not keep_outputs:
+                if not keep_outputs and a.req.rid not in self.keep:
                     self.results[a.req.rid].pop("B")
                     self.results[a.req.rid].pop("status")
-        return self.results
 
     def close(self):
         # a run cut off by its time cap can leave factors running on the

@@ -82,6 +82,15 @@ def kinship_M_torch(n: int, h: float, seed: int, n_markers: int = 5000, device="
     marker draws use torch's generator, so the matrix differs from
     ``kinship_M`` for the same seed.  Returns an (n, n) float64 tensor
     (symmetric, so row- and column-major storage coincide)."""
+    M = kinship_phi_torch(n, seed, n_markers, device)
+    M.mul_(h)
+    M.diagonal().add_(1.0 - h)
+    return M
+
+
+def kinship_phi_torch(n: int, seed: int, n_markers: int = 5000, device="cuda"):
+    """Phi (unit diagonal, n x n float64 tensor) of the kinship recipe, drawn
+    with torch on ``device`` (see kinship_M_torch)."""
     import torch
     dev = torch.device(device)
     if n < 2:  # one sample: Phi = [1]
@@ -113,9 +122,7 @@ def kinship_M_torch(n: int, h: float, seed: int, n_markers: int = 5000, device="
     Phi = (K / d[:, None] / d[None, :]).double()
     Phi = 0.5 * (Phi + Phi.T)
     Phi.fill_diagonal_(1.0)
-    M = h * Phi
-    M.diagonal().add_(1.0 - h)
-    return M
+    return Phi
 
 
 def covariates(n: int, p: int, seed: int) -> np.ndarray:
@@ -153,8 +160,6 @@ def genotypes_torch(n: int, m: int, seed: int, device="cpu", chunk: int = 8192, 
     P(0) = (1-f)^2, P(1) = 2 f (1-f) and P(2) = f^2."""
     import torch
     dev = torch.device(device)
-    if n < 2:  # one sample: Phi = [1]
-        return torch.ones((n, n), dtype=torch.float64, device=dev)
     gen = torch.Generator(device=dev)
     gen.manual_seed(int(seed) * 1000003 + _STREAM_GENOTYPES)
     if out is None:
@@ -178,3 +183,58 @@ def problem(n: int, p: int, m: int, h: float, seed: int, n_markers: int = 5000,
         y=phenotype(n, seed),
         XR=genotypes_np(n, m, seed),
     )
+
+
+_STREAM_BANK = 5
+
+
+class ServingBank:
+    """Request inputs for a serving run, drawn once before the requests arrive
+    so that admitting a request costs a slice and one elementwise kernel, not
+    a fresh synthesis (which would make the measured latency that of the input
+    generator rather than of the server).
+
+    Two device-resident banks, for N = the largest n of the stream:
+      * Phi_bank: the kinship recipe's Phi for N individuals (N x N float64);
+      * X_bank: m_max SNPs of N individuals (m_max x N int8, SNP-major),
+        SNP i ~ Binomial(2, f_i), f_i ~ U(0.05, 0.5).
+    Request (n, p, m, h) with seed s draws offsets o ~ U{0..N-n} and
+    c ~ U{0..m_max-m} from s; then
+      M   = h Phi_bank[o:o+n, o:o+n] + (1 - h) I  (a principal submatrix of a
+            correlation matrix: unit diagonal and SPD, so M is SPD for h < 1),
+      X_R = X_bank[c:c+m, o:o+n]^T  (column-major n x m view, leading dim N),
+      X_L = covariates(n, p, s), y = phenotype(n, y_seed).
+    Equal seeds give equal (M, X_L, X_R), so a request that repeats an earlier
+    scan with a new phenotype sees the same factor inputs."""
+
+    def __init__(self, n_max: int, m_max: int, seed: int, n_markers: int = 5000,
+                 device="cuda"):
+        import torch
+        self.N, self.m_max = int(n_max), int(m_max)
+        self.device = torch.device(device)
+        self.phi = kinship_phi_torch(self.N, seed, n_markers, device)
+        self.X = genotypes_torch(self.N, self.m_max, seed + 1, device=device)
+
+    def offsets(self, n: int, m: int, seed: int):
+        g = rng(seed, _STREAM_BANK)
+        o = int(g.integers(0, self.N - n + 1))
+        c = int(g.integers(0, self.m_max - m + 1))
+        return o, c
+
+    def request(self, n: int, p: int, m: int, h: float, seed: int, y_seed: int,
+                with_factor_inputs: bool = True):
+        """(M, X_L, y, X_R) as device tensors (M, X_L None without factor inputs)."""
+        import torch
+        if n > self.N or m > self.m_max:
+            raise ValueError(f"request n={n}, m={m} exceeds the bank ({self.N}, {self.m_max})")
+        o, c = self.offsets(n, m, seed)
+        M = XL = None
+        if with_factor_inputs:
+            M = self.phi[o:o + n, o:o + n] * h
+            M.diagonal().add_(1.0 - h)
+            if p > 1:
+                XL = torch.from_numpy(np.ascontiguousarray(covariates(n, p, seed).T))
+                XL = XL.to(self.device).t()
+        y = torch.from_numpy(phenotype(n, y_seed)).to(self.device)
+        XR = self.X[c:c + m, o:o + n]  # (m, n) view: X_R^T, row stride N
+        return M, XL, y, XR

@@ -70,7 +70,19 @@ def test_invalid_descriptions_rejected_without_gpu(lib):
     assert lib.gls_plan_create(ctypes.byref(d), ctypes.byref(h)) == 1
     assert "flag" in gls.last_error()
     assert lib.gls_plan_create(None, ctypes.byref(h)) == 1
+    d = gls.make_desc(10, 3, 10, wait_limit_us=-1)
+    assert lib.gls_plan_create(ctypes.byref(d), ctypes.byref(h)) == 1
+    d = gls.make_desc(10, 3, 10, host_wait_ms=-5)
+    assert lib.gls_plan_create(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert "host_wait_ms" in gls.last_error()
     assert lib.gls_destroy(None) == 0
+
+
+def test_desc_layout_matches_header():
+    # 8 + 4 + 4 + 8 + 4 + 4 + 8 + 4 + 4 + 4 + 5 * 4 bytes, 8-aligned
+    assert ctypes.sizeof(gls.PlanDesc) == 72
+    assert gls.PlanDesc.wait_limit_us.offset == 44 and gls.PlanDesc.reserved.offset == 52
+    assert ctypes.sizeof(gls.Stats) == 15 * 8
 
 
 def test_null_plan_calls_are_errors(lib):
@@ -79,6 +91,8 @@ def test_null_plan_calls_are_errors(lib):
     assert lib.gls_solve_stream(None, None, 0, 0, None, 0, None) == 1
     assert lib.gls_synchronize(None) == 1
     assert lib.gls_plan_stream(None) is None
+    assert lib.gls_plan_wait_event(None, None) == 1
+    assert lib.gls_plan_operand_precision(None) == -1
 
 
 def test_no_device_reports_unsupported(lib):

@@ -50,10 +50,9 @@ def test_batch_matches_single_and_oracle(prec):
                 Bs_single, st_single = run_gpu(pr, prec)
                 assert np.array_equal(Bb, Bs_single), f"scan {i} group {group}"
                 assert np.array_equal(sts[i].cpu().numpy(), st_single)
+    if prec == "bf16":  # n = 2048 keeps BF16 slices, the rest run on FP16 ones
+        assert [pl.operand_precision for pl in plans] == ["fp16"] * 2 + ["bf16"] + ["fp16"] * 2
     for i, pr in enumerate(probs):
-        n = pr["M"].shape[0]
-        if prec == "bf16" and n < 1000:
-            continue  # the BF16 split is held to 1e-6 from n = 1000 up
         Bref, sref = oracle_ref(pr, oracle.TAU_MIXED)
         ok = sref == 0
         assert relerr(Bs[i].cpu().numpy().T[:, ok], Bref[:, ok]).max() <= 1e-6
@@ -63,11 +62,13 @@ def test_batch_matches_single_and_oracle(prec):
 
 def test_batch_rejects_mixed_configurations():
     a = gls.Plan(200, 3, 10, precision="fp16")
-    b = gls.Plan(200, 3, 10, precision="bf16")
+    b = gls.Plan(200, 3, 10, precision="fp16", split_terms=2)
     c = gls.Plan(200, 3, 10, precision="fp64")
+    d = gls.Plan(2100, 3, 10, precision="bf16")
     with pytest.raises(gls.GlsError):
         gls.Batch([a, b])
     with pytest.raises(gls.GlsError):
         gls.Batch([a, c])
-    for pl in (a, b, c):
+    gls.Batch([a, d]).close()  # BF16 and FP16 operands share a launch
+    for pl in (a, b, c, d):
         pl.close()

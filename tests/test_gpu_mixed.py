@@ -4,10 +4,9 @@ relative, singular-SNP decisions identical.  Sizes span several 128-row /
 checked on sampled SNPs.
 
 The FP16 split carries about 33 bits of each row of L^{-1} and meets 1e-6 at
-every size; the BF16 split carries about 24 bits, which meets 1e-6 from
-n of about 1000 up (at n = 100, p = 2 the coefficient vector's own
-conditioning turns 2^-26 per-row truncation into ~1e-6), so the BF16 cases
-use n >= 1000."""
+every size; the BF16 split carries about 24 bits, which falls short of 1e-6
+at small n (about 1e-6 at n = 100, p = 2).  A BF16 plan below n = 2048
+therefore runs on FP16 slices; the tests check both sides of that boundary."""
 import numpy as np
 import pytest
 
@@ -56,16 +55,33 @@ def test_ragged_shapes(n, p, m, kmax):
     check(pr, B, st)
 
 
-@pytest.mark.parametrize("n,p,m,kmax", [(1025, 7, 300, 129), (1500, 4, 700, 700)])
+@pytest.mark.parametrize("n,p,m,kmax", [(1025, 7, 300, 129), (1500, 4, 700, 700),
+                                         (2100, 5, 400, 400)])
 def test_ragged_shapes_bf16(n, p, m, kmax):
     pr = synth.problem(n, p, m, 0.5, seed=300 + n + p)
     B, st = run_gpu(pr, "bf16", kmax=kmax)
     check(pr, B, st)
 
 
+@pytest.mark.parametrize("n,p,h,expect", [
+    (500, 2, 0.9, "fp16"), (687, 11, 0.5, "fp16"), (1000, 3, 0.1, "fp16"),
+    (2047, 20, 0.5, "fp16"), (2048, 20, 0.5, "bf16"), (2600, 2, 0.9, "bf16")])
+def test_bf16_plans_meet_the_bound_at_every_n(n, p, h, expect):
+    """A BF16 plan below n = 2048 runs on FP16 slices; on both sides of the
+    boundary b_i meets 1e-6 against the oracle (the smallest scan of the
+    batched workload has n = 687)."""
+    pr = synth.problem(n, p, 600, h, seed=400 + n, n_markers=max(2 * n, 400))
+    with gls.Plan(n, p, 600, precision="bf16") as plan:
+        assert plan.operand_precision == expect
+    B, st = run_gpu(pr, "bf16")
+    e = check(pr, B, st)
+    print(f"bf16 plan n={n} p={p} h={h} ({expect} slices): max {e.max():.3e} "
+          f"p99 {np.quantile(e, .99):.3e}")
+
+
 def test_split_variants_reported():
-    """Error of each operand split on the same problem (printed for the design
-    notes); the 3-term splits must meet 1e-6."""
+    """Error of each operand split on the same problem (printed side by side);
+    the 3-term splits must meet 1e-6."""
     pr = synth.problem(2048, 8, 2048, 0.5, seed=31)
     Bref, sref = oracle_ref(pr, oracle.TAU_MIXED)
     rows = []
@@ -156,8 +172,9 @@ def test_full_size_sampled():
             plan.synchronize()
             out[tag] = (B.cpu().numpy().T, st.cpu().numpy())
     assert np.abs(out["planted"][0][:, planted] - beta).max() <= 1e-6
+    rs = np.random.Generator(np.random.Philox(77)).choice(k, size=200, replace=False)
     idx = np.unique(np.concatenate([np.arange(16), np.linspace(16, k - 1, 32).astype(np.int64),
-                                    [kmax - 1, kmax, k - 1]]))
+                                    [kmax - 1, kmax, k - 1], rs]))
     XR_host = np.asfortranarray(XRt.cpu().numpy().T)
     Bref, sref, info = oracle.gls_sampled(M, XL, y, XR_host, idx, tau=oracle.TAU_MIXED,
                                           nthreads=oracle.default_threads())
@@ -166,6 +183,7 @@ def test_full_size_sampled():
         B, st = out[tag]
         assert np.array_equal(st[idx], sref)
         e = relerr(B[:, idx], Bref)
+        p99 = np.quantile(e, 0.99)
         print(f"full size {'bf16' if tag == 'y' else 'fp16'} S=3: max {e.max():.3e} "
-              f"over {idx.size} sampled SNPs")
-        assert e.max() <= TOL
+              f"p99 {p99:.3e} over {idx.size} sampled SNPs")
+        assert e.max() <= TOL and p99 <= TOL

@@ -53,7 +53,8 @@ def alone(req, prec, block):
     return B, st, (M, XL, y, XR)
 
 
-@pytest.mark.parametrize("prec,budget", [("fp16", 100e9), ("fp16", 2.5e8), ("fp64", 100e9)])
+@pytest.mark.parametrize("prec,budget", [("fp16", 100e9), ("fp16", 2.5e8), ("bf16", 100e9),
+                                         ("fp64", 100e9)])
 def test_served_equals_alone(prec, budget):
     reqs = serve.poisson_requests(10, 60.0, 1234, (150, 1400), (2, 6), (300, 2500), 0.3)
     assert any(r.reuse for r in reqs)

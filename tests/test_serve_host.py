@@ -12,12 +12,50 @@ import torch
 from paper_1210_7325_gb300 import serve
 
 
+class FakeStreams:
+    """current_stream() / Event() of a fake device.  Work is not run, only
+    logged: make_inputs tags each tensor with the stream it was made on and the
+    position of that work in the log, and an event remembers where it was
+    recorded."""
+
+    def __init__(self):
+        self.lock = threading.Lock()
+        self.log = []
+        self.current = "s0"
+
+    def current_stream(self):
+        return self.current
+
+    def produce(self, *tensors):
+        with self.lock:
+            self.log.append(("produce", self.current))
+            pos = len(self.log)
+        for t in tensors:
+            if t is not None:
+                t.made_on, t.made_at = self.current, pos
+
+    def Event(self):
+        streams = self
+
+        class Event:
+            stream = at = None
+
+            def record(self, stream):
+                with streams.lock:
+                    streams.log.append(("record", stream))
+                    self.stream, self.at = stream, len(streams.log)
+        return Event()
+
+
 class FakeGls:
     def __init__(self):
         self.lock = threading.Lock()
         self.factors = []      # (plan id, with_M)
         self.batches = []      # number of plans per batched launch
         self.closed_use = 0
+        self.inflight = 0      # factors running now
+        self.factor_s = 0.002
+        self.unordered = []    # reads of inputs the plan was not ordered after
 
     def footprint_bytes(self, n, p, block, precision):
         return 8 * n * n + 1000
@@ -33,10 +71,28 @@ class FakeGls:
                 self.id = next(Plan.ids)
                 self.closed = False
                 self.yv = None
+                self.waited = None
+
+            def wait_event(self, ev):
+                self.waited = ev
+
+            def check_ordered(self, *tensors):
+                # every input was made before an event that this plan waited
+                # for, on the stream that made it
+                for t in tensors:
+                    if t is None or not hasattr(t, "made_on"):
+                        continue
+                    ev = self.waited
+                    if ev is None or ev.stream != t.made_on or ev.at <= t.made_at:
+                        fake.unordered.append((self.id, getattr(t, "made_on", None)))
 
             def factor(self, M, XL, y):
-                time.sleep(0.002)
                 with fake.lock:
+                    fake.inflight += 1
+                self.check_ordered(M, XL, y)
+                time.sleep(fake.factor_s)
+                with fake.lock:
+                    fake.inflight -= 1
                     if self.closed:
                         fake.closed_use += 1
                         raise RuntimeError("factor on a closed plan")
@@ -53,6 +109,7 @@ class FakeGls:
             def solve_block(self, XR, B, st, k=None):
                 if self.closed:
                     fake.closed_use += 1
+                self.check_ordered(XR._base if XR._base is not None else XR)
                 self._fill(XR, B, st)
 
             def synchronize(self):
@@ -70,6 +127,7 @@ class FakeGls:
                 for pl, X, B, s in zip(self.plans, XRs, Bs, sts):
                     if pl.closed:
                         fake.closed_use += 1
+                    pl.check_ordered(X._base if X._base is not None else X)
                     pl._fill(X, B, s)
 
             def close(self):
@@ -144,3 +202,61 @@ def test_latency_summary():
     assert s["completed"] == 100 and s["reused"] == 50
     assert s["p50_s"] == pytest.approx(50.5) and s["p99_s"] == pytest.approx(99.01)
     assert s["solves_per_s"] == pytest.approx(1000 / 101)
+
+
+def tagged_inputs(streams):
+    """make_inputs that logs its work on the current fake stream."""
+    def make(req, torch_mod, reuse):
+        inp = make_inputs(req, torch_mod, reuse)
+        streams.produce(inp.M, inp.XL, inp.y, inp.XR)
+        return inp
+    return make
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp64"])
+def test_inputs_ordered_before_the_plan_reads_them(fake, prec):
+    """The invariant whose absence let a plan's stream read request inputs made
+    on another stream: after make_inputs the server records an event on the
+    stream that made them, and the plan waits for it before its factor and
+    every solve read them (checked for reused factors too)."""
+    streams = FakeStreams()
+    streams.current = "side"   # inputs made on a stream other than the default
+    reqs = serve.poisson_requests(30, 400.0, 9, (100, 300), (2, 5), (50, 700), 0.4)
+    assert any(r.reuse for r in reqs)
+    srv = serve.Server(tagged_inputs(streams), prec, hbm_budget=1e9, block=128,
+                       device="cpu", streams=streams)
+    res = srv.run(reqs, time_cap=60.0)
+    srv.close()
+    assert sorted(res) == [r.rid for r in reqs]
+    assert fake.unordered == []
+    # and a server that forgets the event is caught by the same check
+    fake.unordered.clear()
+    bad = serve.Server(tagged_inputs(streams), prec, hbm_budget=1e9, block=128, device="cpu",
+                       streams=None)
+    bad.run(reqs[:3], time_cap=60.0)
+    bad.close()
+    assert fake.unordered
+
+
+def test_time_cap_waits_for_running_factors(fake):
+    """run() stopped by its time cap returns only after every factor it started
+    has ended, so no factor reads inputs that were already released."""
+    fake.factor_s = 0.3
+    reqs = serve.poisson_requests(6, 1000.0, 3, (100, 200), (2, 4), (50, 100), 0.0)
+    srv = serve.Server(make_inputs, "bf16", hbm_budget=1e9, block=128, device="cpu",
+                       factor_workers=6)
+    t0 = time.perf_counter()
+    srv.run(reqs, time_cap=0.02)
+    assert fake.inflight == 0
+    assert time.perf_counter() - t0 >= 0.25
+    srv.close()
+
+
+def test_kept_outputs(fake):
+    reqs = serve.poisson_requests(8, 400.0, 4, (100, 200), (2, 4), (50, 300), 0.0)
+    srv = serve.Server(make_inputs, "bf16", hbm_budget=1e9, block=128, device="cpu",
+                       keep={0, 3})
+    res = srv.run(reqs, time_cap=60.0)
+    srv.close()
+    assert "B" in res[0] and "B" in res[3] and "B" not in res[1]
+    assert torch.equal(res[3]["B"][:, 0], expected(reqs[3]))
