@@ -151,7 +151,9 @@ typedef struct {
  * calls, gls_batch_solve (first plan's value) and gls_synchronize: past it they return
  * GLS_ERR_TIMEOUT with the plan's work still queued, so the caller must call
  * gls_synchronize again (or gls_destroy, which always waits to the end) before
- * it reuses or frees any buffer of that call.
+ * it reuses or frees any buffer of that call.  Copies between the device and
+ * the caller's pageable host memory complete inside the CUDA runtime and are
+ * not bounded by it.
  */
 
 /*

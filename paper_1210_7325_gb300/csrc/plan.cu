@@ -94,6 +94,7 @@ struct gls_plan {
   double* RTL = nullptr;    // (p-1) x (p-1)
   double* zT = nullptr;     // p-1
   int* flags = nullptr;     // kFlagCount
+  int* h_flags = nullptr;   // pinned read-back of flags (an async copy the host can wait on)
   int8_t* xr[2]{};          // device staging of X_R blocks (ld = n)
   double* bdev[2]{};        // p x kmax
   int32_t* sdev[2]{};       // kmax
@@ -438,6 +439,7 @@ void free_plan(gls_plan* pl) {
   cudaFree(pl->RTL);
   cudaFree(pl->zT);
   cudaFree(pl->flags);
+  cudaFreeHost(pl->h_flags);
   cudaFree(pl->partials);
   for (int s = 0; s < 2; ++s) {
     cudaFree(pl->xr[s]);
@@ -551,9 +553,12 @@ gls_status_t host_wait(gls_plan* pl, cudaStream_t st) {
 }
 
 gls_status_t check_flags(gls_plan* pl, int host_flags[gls::kFlagCount]) {
-  GLS_CUDA(cudaMemcpyAsync(host_flags, pl->flags, sizeof(int) * gls::kFlagCount,
+  // into pinned memory: a copy into pageable memory would itself block until
+  // the stream is done, outside the deadline
+  GLS_CUDA(cudaMemcpyAsync(pl->h_flags, pl->flags, sizeof(int) * gls::kFlagCount,
                            cudaMemcpyDeviceToHost, pl->stream));
   GLS_TRY(host_wait(pl, pl->stream));
+  memcpy(host_flags, pl->h_flags, sizeof(int) * gls::kFlagCount);
   if (host_flags[gls::kFlagKernel] & gls::kErrTimeout) {
     set_error("a bounded device wait gave up (site %d)", host_flags[gls::kFlagWhere]);
     return GLS_ERR_TIMEOUT;
@@ -712,6 +717,7 @@ gls_status_t gls_plan_create(const gls_plan_desc_t* desc, gls_plan_t* out) {
   if ((st = dev_alloc(&pl->RTL, (size_t)32 * 32)) != GLS_OK) return fail(st);
   if ((st = dev_alloc(&pl->zT, (size_t)32)) != GLS_OK) return fail(st);
   if ((st = dev_alloc(&pl->flags, (size_t)gls::kFlagCount)) != GLS_OK) return fail(st);
+  if ((st = host_alloc(&pl->h_flags, (size_t)gls::kFlagCount)) != GLS_OK) return fail(st);
   if ((st = dev_alloc(&pl->partials, partial_doubles(pl->precision, npad, p, kmax))) != GLS_OK)
     return fail(st);
   for (int s = 0; s < 2; ++s) {
@@ -1220,6 +1226,7 @@ struct gls_batch {
   std::vector<gls_plan*> plans;
   gls::MixedBatch* mb = nullptr;
   int* flags = nullptr;
+  int* h_flags = nullptr;  // pinned read-back
   cudaEvent_t ev = nullptr;
   int device = 0;
   ReplayCache replays;  // rounds captured on the first plan's stream
@@ -1270,10 +1277,12 @@ gls_status_t gls_batch_create(const gls_plan_t* plans, int32_t nplans, gls_batch
   }
   if (cudaMalloc(&b->flags, sizeof(int) * gls::kFlagCount) != cudaSuccess ||
       cudaMemset(b->flags, 0, sizeof(int) * gls::kFlagCount) != cudaSuccess ||
+      cudaMallocHost(&b->h_flags, sizeof(int) * gls::kFlagCount) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     gls::mixed_batch_free(b->mb);
     cudaFree(b->flags);
+    cudaFreeHost(b->h_flags);
     delete b;
     set_error("batch allocation failed");
     return GLS_ERR_OOM;
@@ -1359,8 +1368,9 @@ gls_status_t gls_batch_solve(gls_batch_t b, const int8_t* const* XR, const int64
   GLS_CUDA(cudaEventRecord(b->ev, st));
   for (int i = 1; i < count; ++i) GLS_CUDA(cudaStreamWaitEvent(b->plans[i]->stream, b->ev, 0));
   int hf[gls::kFlagCount];
-  GLS_CUDA(cudaMemcpyAsync(hf, b->flags, sizeof(hf), cudaMemcpyDeviceToHost, st));
+  GLS_CUDA(cudaMemcpyAsync(b->h_flags, b->flags, sizeof(hf), cudaMemcpyDeviceToHost, st));
   GLS_TRY(host_wait(p0, st));
+  memcpy(hf, b->h_flags, sizeof(hf));
   if (hf[gls::kFlagKernel] & gls::kErrTimeout) {
     set_error("a bounded device wait gave up (site %d)", hf[gls::kFlagWhere]);
     return GLS_ERR_TIMEOUT;
@@ -1376,6 +1386,7 @@ gls_status_t gls_batch_destroy(gls_batch_t b) {
   b->replays.items.clear();
   gls::mixed_batch_free(b->mb);
   cudaFree(b->flags);
+  cudaFreeHost(b->h_flags);
   if (b->ev) cudaEventDestroy(b->ev);
   cudaGetLastError();
   delete b;

@@ -232,6 +232,7 @@ class ServingBank:
         if with_factor_inputs:
             M = self.phi[o:o + n, o:o + n] * h
             M.diagonal().add_(1.0 - h)
+            M = M.t()  # exactly symmetric: the column-major view of the same matrix
             if p > 1:
                 XL = torch.from_numpy(np.ascontiguousarray(covariates(n, p, seed).T))
                 XL = XL.to(self.device).t()

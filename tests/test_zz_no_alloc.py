@@ -10,6 +10,7 @@ was.  This file is collected last so that a failure here leaves every other
 test already run; it also passes on its own in a fresh process.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -74,6 +75,7 @@ def test_static_entry_point_matches_plan_and_oracle_twice(lib, n, p, k):
     for call, (B, st) in enumerate(outs):
         B.fill_(-1.0)
         st.fill_(-1)
+        gc.collect()  # so that no unrelated tensor is freed during the call
         torch.cuda.synchronize()
         free0 = torch.cuda.mem_get_info()[0]
         held0 = torch.cuda.memory_allocated()
@@ -85,7 +87,7 @@ def test_static_entry_point_matches_plan_and_oracle_twice(lib, n, p, k):
         torch.cuda.synchronize()
         if call == 1:  # the first call may load the kernels' module; later ones allocate nothing
             assert torch.cuda.mem_get_info()[0] == free0
-            assert torch.cuda.memory_allocated() == held0
+            assert torch.cuda.memory_allocated() <= held0  # nothing from torch's pool either
         Bh = B.cpu().numpy().T
         sh = st.cpu().numpy()
         assert np.array_equal(sh, splan) and np.array_equal(sh, sora)
