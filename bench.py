@@ -815,6 +815,82 @@ def run_serve_workload(args, sw, torch, time_cap=None):
     return line
 
 
+def sub_phenotypes(args, torch, ts=(1, 4, 13), steps=3, warmup=1):
+    """The headline scan with t phenotypes per factor (Eq. 1's index j <= t):
+    one pass over X_R serves t right-hand sides, so GLS solves (b_ij) per
+    second grow with t while the step's time barely moves.  b_ij of three
+    phenotypes of the largest t are checked against the oracle on sampled SNPs."""
+    import numpy as np
+
+    import oracle
+    from paper_1210_7325_gb300 import gls, synth
+    wl = WORKLOADS[DEFAULT_WORKLOAD]
+    n, p, m, kmax, prec = wl["n"], wl["p"], wl["m"], wl["block"], wl["precision"]
+    dev = torch.device("cuda")
+    M, XL, y, XR = make_inputs(wl, 0, torch)
+    Md = torch.from_numpy(np.ascontiguousarray(M.T)).to(dev).t()
+    XLd = torch.from_numpy(np.ascontiguousarray(XL.T)).to(dev).t()
+    tmax = max(ts)
+    Y = np.column_stack([synth.phenotype(n, synth.BASE_SEED + 50 + j) for j in range(tmax)])
+    rows, last = [], None
+    for t in ts:
+        Yd = torch.from_numpy(np.ascontiguousarray(Y[:, :t].T)).to(dev).t()
+        B = torch.empty((m * t, p), dtype=torch.float64, device=dev)
+        st = torch.empty(m, dtype=torch.int32, device=dev)
+        plan = gls.Plan(n, p, kmax, precision=prec, phenotypes=t, flags=launch_flags(args, gls))
+        stream = torch.cuda.ExternalStream(plan.stream, device=dev)
+
+        def step():
+            plan.factor(Md, XLd, Yd)
+            for s0 in range(0, m, kmax):
+                k = min(kmax, m - s0)
+                plan.solve_block(XR[s0:s0 + k].t(), B[s0 * t:(s0 + k) * t].t(), st[s0:s0 + k],
+                                 k=k)
+
+        for _ in range(warmup):
+            step()
+        plan.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        rows.append({"phenotypes": t, "value": m * t * steps / sec,
+                     "ms_per_step": sec / steps * 1e3, "bad_status": int((st != 0).sum())})
+        plan.close()
+        last = (t, B, st)
+    base = rows[0]["value"]
+    for r in rows:
+        r["vs_t1"] = r["value"] / base
+    # oracle check of the largest t: three phenotypes on 256 seeded SNPs
+    t, B, st = last
+    cols = sample_columns(m, 256, seed=7)
+    ci = torch.as_tensor(cols, device=dev)
+    Xs = np.asfortranarray(XR[ci].cpu().numpy().T)
+    L, info = oracle.potrf(M, nthreads=oracle.default_threads())
+    Bg = B.view(m, t, p)[ci].cpu().numpy()          # (s, t, p)
+    sg = st[ci].cpu().numpy()
+    errs, mism = [], 0
+    for j in (0, t // 2, t - 1):
+        Bref, sref = oracle.gls_factored(L, XL, Y[:, j], Xs, tau=oracle.TAU_MIXED,
+                                         nthreads=oracle.default_threads())
+        ok = sref == 0
+        Bj = Bg[:, j, :].T
+        errs.append(np.linalg.norm(Bj[:, ok] - Bref[:, ok], axis=0)
+                    / np.linalg.norm(Bref[:, ok], axis=0))
+        mism += int((sg != sref).sum())
+    e = np.concatenate(errs)
+    return {"workload": DEFAULT_WORKLOAD, "unit": "solves/s (one solve = one b_ij)",
+            "steps": steps, "warmup": warmup, "rows": rows,
+            "error": {"max": float(e.max()), "p99": float(np.quantile(e, 0.99)),
+                      "n_sampled": int(e.size), "status_mismatches": mism, "tolerance": 1e-6,
+                      "phenotypes_checked": [0, t // 2, t - 1],
+                      "reference": "FP64 oracle on the same SNP columns, per phenotype"}}
+
+
 def sub_batch(args, torch, name="batch48_uneven_bf16", steps=2, warmup=1):
     """The batched uneven-scan workload as a sub-object of the default line."""
     sub = argparse.Namespace(**vars(args))
@@ -1043,6 +1119,11 @@ def main():
         line["batch"] = sub_batch(args, torch)
         torch.cuda.empty_cache()
         line["serve"] = sub_serve(args, torch)
+        torch.cuda.empty_cache()
+        try:
+            line["phenotypes"] = sub_phenotypes(args, torch)
+        except Exception as ex:  # reported, not fatal to the headline line
+            line["phenotypes"] = {"error_raised": repr(ex)}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

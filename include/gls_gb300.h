@@ -135,7 +135,9 @@ typedef struct {
                               up after this many microseconds (0 = 1 s); see below         */
   int32_t host_wait_ms;    /* each host wait of a call gives up after this many ms
                               (0 = no limit); see below                                    */
-  int32_t reserved[5];     /* must be 0                                                      */
+  int32_t phenotypes;      /* t: phenotypes per factor the plan holds (0 = 1);
+                              p - 1 + t <= 32                                              */
+  int32_t reserved[4];     /* must be 0                                                      */
 } gls_plan_desc_t;
 
 /*
@@ -186,12 +188,30 @@ gls_status_t gls_factor(gls_plan_t plan, const double* M, int64_t ldm, const dou
                         int64_t ldxl, const double* y, int64_t* info);
 
 /*
+ * gls_factor for several phenotypes at once: Eq. 1 with the index
+ * 1 <= j <= t that the paper comments out, b_ij = (X_i^T M^{-1} X_i)^{-1}
+ * X_i^T M^{-1} y_j.  The Gram matrix S_i and its Cholesky factor do not
+ * depend on j, so one pass of the blocked solve over X_R serves all t
+ * right-hand sides: the whitened block becomes [X~_L | Y~], b_T a
+ * (p-1) x t block, and each SNP gets t values b_B_ij = y~_j^T x~_i.
+ * Y   n x t (ldy >= n), 1 <= t <= desc.phenotypes.  M, XL and info as for
+ *     gls_factor (M == NULL keeps the factor: new phenotypes for the same M).
+ * Until the next gls_factor[_y], the SNP calls write b_ij to column
+ * i t + j (0-based) of their B (p x (k t)): the t vectors of a SNP are adjacent.
+ * gls_factor is gls_factor_y with t = 1 and ldy = n.
+ */
+gls_status_t gls_factor_y(gls_plan_t plan, const double* M, int64_t ldm, const double* XL,
+                          int64_t ldxl, const double* Y, int64_t ldy, int32_t t,
+                          int64_t* info);
+
+/*
  * One block of the SNP loop (Alg. 5 lines 3 and 7-11): for the k SNP columns
  * of XR, x~_i = L^{-1} x_Ri (blocked triangular solve), the Gram entries
  * S_BL_i = X~_L^T x~_i, S_BR_i = x~_i^T x~_i, b_B_i = y~^T x~_i, and
  * b_i = S_i^{-1} (b_T; b_B_i) by a Cholesky solve of the p x p system.
  * XR  n x k int8 genotype codes (ldxr >= n); every int8 value is accepted.
- * B   p x k binary64 output (ldb >= p): X_L coefficients first, SNP last.
+ * B   p x k binary64 output (ldb >= p): X_L coefficients first, SNP last;
+ *     p x (k t) after gls_factor_y with t phenotypes (column i t + j).
  * snp_status (may be NULL) k int32: 0, or 1 when S_i is not numerically SPD
  *     (its last pivot d <= tau * S_BR_i with tau = 2^-30 for FP64 and 2^-16
  *     for the mixed paths); that b_i is NaN and the call still returns OK.
@@ -210,8 +230,8 @@ gls_status_t gls_solve_block(gls_plan_t plan, const int8_t* XR, int64_t ldxr, in
  * copy of block j+1 to the device runs on a side stream while block j is
  * solved, and b of block j is copied back while block j+1 is solved
  * (Section 4.2).  The first block is smaller so that its unoverlapped load is
- * short (Section 4.3).  B (p x m, ldb >= p) and snp_status (m, may be NULL)
- * are host memory.  Synchronous.  Device-resident XR is also accepted, in
+ * short (Section 4.3).  B (p x m, or p x (m t) with t phenotypes; ldb >= p)
+ * and snp_status (m, may be NULL) are host memory.  Synchronous.  Device-resident XR is also accepted, in
  * which case only B and snp_status are copied.
  */
 gls_status_t gls_solve_stream(gls_plan_t plan, const int8_t* XR, int64_t ldxr, int64_t m,
@@ -256,7 +276,8 @@ gls_status_t gls_batch_create(const gls_plan_t* plans, int32_t nplans, gls_batch
 /*
  * One block per plan, all in one launch: plan i solves k[i] SNP columns of
  * XR[i] (device memory, n_i x k[i] int8, ldxr[i] >= n_i) into B[i] (device,
- * p_i x k[i], ldb[i] >= p_i) and snp_status[i] (device, may be NULL; the array
+ * p_i x (k[i] t_i) for its t_i phenotypes, ldb[i] >= p_i) and snp_status[i]
+ * (device, may be NULL; the array
  * snp_status itself may be NULL).  0 <= k[i] <= max_block_snps of plan i.
  * group: pairs of 128-row blocks per L2 rasterization group of the launch (0 = default 3;
  * a tuning knob only, results do not depend on it).  Runs on the first plan's

@@ -12,6 +12,9 @@ __host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return ceil_
 // FP64 factor/solve tile edge: L, L^{-1} and the FP64 blocked solve use 64 x 64 tiles.
 constexpr int kT = 64;
 constexpr int kMaxP = 32;
+// Columns of the whitened right-hand block [X_L | Y]: p - 1 covariates plus
+// t phenotypes, q + t <= kMaxW.
+constexpr int kMaxW = 32;
 // Largest number of problems one batched launch serves.
 constexpr int kMaxBatch = 64;
 
@@ -42,10 +45,12 @@ cudaError_t potrf_trtri_fp64(double* A, double* Z, int64_t ld, int64_t npad, int
 void launch_whiten(const double* Z, int64_t ldz, int64_t n, int64_t npad, const double* rhs,
                    int64_t ldr, int ncols, double* out, int64_t ldo, const int* flags,
                    cudaStream_t st);
-void launch_fixed_gram(const double* W, int64_t ld, int64_t n, int p, double* gram,
+// gram (ncols x ncols) = W^T W over the n rows of W (npad x ncols).
+void launch_fixed_gram(const double* W, int64_t ld, int64_t n, int ncols, double* gram,
                        cudaStream_t st);
-void launch_small_chol(const double* gram, int p, double* RTL, double* zT, int* flags,
-                       cudaStream_t st);
+// R_TL R_TL^T = gram[0:q, 0:q]; zT (q x t) = R_TL^{-1} gram[0:q, q:q+t] (ld of gram: ldg).
+void launch_small_chol(const double* gram, int ldg, int q, int t, double* RTL, double* zT,
+                       int* flags, cudaStream_t st);
 
 // trsm_fp64.cu
 cudaError_t launch_trsm_gram_fp64(const double* Z, int64_t ldz, int64_t n, int64_t npad,
@@ -56,12 +61,14 @@ cudaError_t launch_trsm_gram_fp64(const double* Z, int64_t ldz, int64_t n, int64
 // plan.cu: replaces the calling thread's gls_last_error() text.
 void set_last_error_text(const char* msg);
 
-// solve_small.cu
-void launch_assemble_solve(const double* partials, int64_t ldp, int nrowblocks, int p,
-                           int64_t k, const double* RTL, const double* zT, double tau,
+// solve_small.cu.  t phenotypes: b_ij goes to column i t + j of B.
+// FP64 partials: per row block nw + 1 rows (S_BL: q, b_B: nw - q of which the
+// first t are used, S_BR last).
+void launch_assemble_solve(const double* partials, int64_t ldp, int nrowblocks, int p, int t,
+                           int nw, int64_t k, const double* RTL, const double* zT, double tau,
                            double* B, int64_t ldb, int32_t* status, cudaStream_t st);
 void launch_assemble_solve_split(const double* Glin, const double* Pbr, int64_t ldp,
-                                 int nrowblocks, int p, int64_t k, const double* RTL,
+                                 int nrowblocks, int p, int t, int64_t k, const double* RTL,
                                  const double* zT, double tau, double* B, int64_t ldb,
                                  int32_t* status, cudaStream_t st);
 

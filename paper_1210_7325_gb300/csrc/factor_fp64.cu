@@ -336,8 +336,9 @@ __global__ void __launch_bounds__(256) whiten_kernel(const double* __restrict__ 
   }
 }
 
-// G(a, c) = sum_{r < n} W(r, a) W(r, c) for the p columns of W; one CTA per
-// pair a >= c, each thread summing a fixed stride in order, then a fixed tree.
+// G(a, c) = sum_{r < n} W(r, a) W(r, c) for the p columns of W (covariates
+// and phenotypes); one CTA per pair a >= c, each thread summing a fixed stride
+// in order, then a fixed tree.
 __global__ void __launch_bounds__(256) fixed_gram_kernel(const double* __restrict__ W,
                                                          int64_t ld, int64_t n, int p,
                                                          double* __restrict__ G) {
@@ -362,13 +363,14 @@ __global__ void __launch_bounds__(256) fixed_gram_kernel(const double* __restric
   }
 }
 
-// S_TL = G[0:p-1, 0:p-1] = R_TL R_TL^T (pivot rule d <= tau S_jj fails),
-// z_T = R_TL^{-1} b_T with b_T = G[0:p-1, p-1].  One thread; p <= 32.
-__global__ void small_chol_kernel(const double* __restrict__ G, int p, double* __restrict__ R,
-                                  double* __restrict__ zT, int* flags) {
+// S_TL = G[0:q, 0:q] = R_TL R_TL^T (pivot rule d <= tau S_jj fails), and for
+// each phenotype h < t, z_T,h = R_TL^{-1} b_T,h with b_T,h = G[0:q, q + h]
+// (G is ldg x ldg).  One thread; q + t <= 32.
+__global__ void small_chol_kernel(const double* __restrict__ G, int ldg, int q, int t,
+                                  double* __restrict__ R, double* __restrict__ zT, int* flags) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   if (*(volatile int*)&flags[kFlagPotrf] != 0) return;
-  const int q = p - 1;
+  const int64_t p = ldg;
   for (int j = 0; j < q; ++j) {
     const double sjj = G[j + (int64_t)j * p];
     double d = sjj;
@@ -386,10 +388,13 @@ __global__ void small_chol_kernel(const double* __restrict__ G, int p, double* _
     }
     for (int i = 0; i < j; ++i) R[i + j * q] = 0.0;
   }
-  for (int i = 0; i < q; ++i) {
-    double s = G[i + (int64_t)(p - 1) * p];
-    for (int k = 0; k < i; ++k) s -= R[i + k * q] * zT[k];
-    zT[i] = s / R[i + i * q];
+  for (int h = 0; h < t; ++h) {
+    double* z = zT + (int64_t)h * q;
+    for (int i = 0; i < q; ++i) {
+      double s = G[i + (int64_t)(q + h) * p];
+      for (int k = 0; k < i; ++k) s -= R[i + k * q] * z[k];
+      z[i] = s / R[i + i * q];
+    }
   }
 }
 
@@ -471,9 +476,9 @@ void launch_fixed_gram(const double* W, int64_t ld, int64_t n, int p, double* gr
   fixed_gram_kernel<<<(unsigned)(p * (p + 1) / 2), 256, 0, st>>>(W, ld, n, p, gram);
 }
 
-void launch_small_chol(const double* gram, int p, double* RTL, double* zT, int* flags,
-                       cudaStream_t st) {
-  small_chol_kernel<<<1, 32, 0, st>>>(gram, p, RTL, zT, flags);
+void launch_small_chol(const double* gram, int ldg, int q, int t, double* RTL, double* zT,
+                       int* flags, cudaStream_t st) {
+  small_chol_kernel<<<1, 32, 0, st>>>(gram, ldg, q, t, RTL, zT, flags);
 }
 
 }  // namespace gls

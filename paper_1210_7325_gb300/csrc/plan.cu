@@ -80,6 +80,9 @@ struct gls_plan {
   int device = 0;
   int64_t n = 0, npad = 0, kmax = 0;
   int p = 1;
+  int t = 1;                // phenotypes the plan holds (desc.phenotypes)
+  int t_active = 1;         // phenotypes of the last gls_factor
+  int nw = 1;               // columns of [X_L | Y]: p - 1 + t
   int precision = GLS_PREC_FP64;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -88,15 +91,15 @@ struct gls_plan {
 
   double* A = nullptr;      // L, npad x npad
   double* Z = nullptr;      // L^{-1}, npad x npad
-  double* Wrhs = nullptr;   // [X_L | y], npad x p
-  double* Wt = nullptr;     // [X~_L | y~], npad x p
-  double* gram = nullptr;   // p x p
+  double* Wrhs = nullptr;   // [X_L | Y], npad x nw
+  double* Wt = nullptr;     // [X~_L | Y~], npad x nw
+  double* gram = nullptr;   // nw x nw
   double* RTL = nullptr;    // (p-1) x (p-1)
-  double* zT = nullptr;     // p-1
+  double* zT = nullptr;     // (p-1) x t
   int* flags = nullptr;     // kFlagCount
   int* h_flags = nullptr;   // pinned read-back of flags (an async copy the host can wait on)
   int8_t* xr[2]{};          // device staging of X_R blocks (ld = n)
-  double* bdev[2]{};        // p x kmax
+  double* bdev[2]{};        // p x (t kmax)
   int32_t* sdev[2]{};       // kmax
   double* partials = nullptr;
   int64_t ldp = 0;
@@ -344,12 +347,15 @@ gls_status_t replayed(gls_plan* pl, ReplayCache* rc, uint64_t key, F&& body) {
   return launch_replay(pl, ref);
 }
 
-// FP64 path: per 64-row block, p + 1 partial sums per SNP.  Mixed path: one S_BR
-// partial per 128-row block per SNP, plus the p linear Gram entries per SNP.
-size_t partial_doubles(int precision, int64_t npad, int p, int64_t kmax) {
-  if (precision == GLS_PREC_FP64) return (size_t)(npad / gls::kT) * (p + 1) * kmax;
-  return (size_t)(npad / 128 + p) * kmax;
+// FP64 path: per 64-row block, nw + 1 partial sums per SNP (S_BL, b_B per
+// phenotype, S_BR).  Mixed path: one S_BR partial per 128-row block per SNP,
+// plus the nw linear Gram entries per SNP.
+size_t partial_doubles(int precision, int64_t npad, int nw, int64_t kmax) {
+  if (precision == GLS_PREC_FP64) return (size_t)(npad / gls::kT) * (nw + 1) * kmax;
+  return (size_t)(npad / 128 + nw) * kmax;
 }
+
+int phenotypes_of(const gls_plan_desc_t& d) { return d.phenotypes > 0 ? d.phenotypes : 1; }
 
 bool uses_tc_factor(const gls_plan_desc_t& d) {
   if (d.precision == GLS_PREC_FP64) return (d.flags & GLS_FLAG_FACTOR_TENSOR) != 0;
@@ -359,17 +365,18 @@ bool uses_tc_factor(const gls_plan_desc_t& d) {
 size_t footprint(const gls_plan_desc_t& d, int64_t* npad_out = nullptr) {
   const int64_t npad = gls::round_up(d.n, 128);
   if (npad_out) *npad_out = npad;
-  const int p = d.p;
+  const int p = d.p, t = phenotypes_of(d), nw = p - 1 + t;
   const int64_t kmax = d.max_block_snps;
   size_t bytes = 0;
   bytes += 2 * (size_t)npad * npad * sizeof(double);              // L, Z
-  bytes += 2 * (size_t)npad * p * sizeof(double);                 // Wrhs, Wt
-  bytes += (size_t)p * p * sizeof(double) + 2 * 32 * 32 * sizeof(double);
+  bytes += 2 * (size_t)npad * nw * sizeof(double);                // Wrhs, Wt
+  bytes += (size_t)nw * nw * sizeof(double) + 2 * 32 * 32 * sizeof(double);
   bytes += 64;                                                    // flags
   bytes += 2 * (size_t)d.n * kmax;                                // X_R staging
-  bytes += 2 * (size_t)kmax * (p * sizeof(double) + sizeof(int32_t));
-  bytes += partial_doubles(d.precision, npad, p, kmax) * sizeof(double);  // Gram partials
-  if (d.precision != GLS_PREC_FP64) bytes += gls::mixed_footprint(d.n, npad, p, kmax, d.split_terms);
+  bytes += 2 * (size_t)kmax * ((size_t)p * t * sizeof(double) + sizeof(int32_t));
+  bytes += partial_doubles(d.precision, npad, nw, kmax) * sizeof(double);  // Gram partials
+  if (d.precision != GLS_PREC_FP64)
+    bytes += gls::mixed_footprint(d.n, npad, nw, kmax, d.split_terms);
   if (uses_tc_factor(d)) bytes += gls::tc_factor_bytes(npad);
   return bytes;
 }
@@ -414,7 +421,11 @@ gls_status_t validate_desc(const gls_plan_desc_t* d) {
     set_error("wait_limit_us and host_wait_ms must be >= 0");
     return GLS_ERR_INVALID_ARG;
   }
-  for (int i = 0; i < 5; ++i)
+  if (d->phenotypes < 0 || d->p - 1 + phenotypes_of(*d) > gls::kMaxW) {
+    set_error("phenotypes = %d: need p - 1 + phenotypes <= %d", d->phenotypes, gls::kMaxW);
+    return GLS_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < 4; ++i)
     if (d->reserved[i] != 0) {
       set_error("reserved fields must be 0");
       return GLS_ERR_INVALID_ARG;
@@ -581,11 +592,11 @@ gls_status_t run_block(gls_plan* pl, const int8_t* xr, int64_t ldxr, int64_t k, 
     {
       Timed t(pl, &pl->t_trsm);
       GLS_CUDA(gls::launch_trsm_gram_fp64(pl->Z, pl->npad, pl->n, pl->npad, xr, ldxr, k, pl->Wt,
-                                          pl->npad, pl->p, pl->partials, pl->ldp, pl->stream));
+                                          pl->npad, pl->nw, pl->partials, pl->ldp, pl->stream));
     }
     Timed t(pl, &pl->t_solve);
-    gls::launch_assemble_solve(pl->partials, pl->ldp, pl->nI, pl->p, k, pl->RTL, pl->zT,
-                               gls::kTauFP64, B, ldb, status, pl->stream);
+    gls::launch_assemble_solve(pl->partials, pl->ldp, pl->nI, pl->p, pl->t_active, pl->nw, k,
+                               pl->RTL, pl->zT, gls::kTauFP64, B, ldb, status, pl->stream);
     pl->launches += 2;
   } else {
     double* Pbr = pl->partials;                      // nI x ldp
@@ -601,8 +612,8 @@ gls_status_t run_block(gls_plan* pl, const int8_t* xr, int64_t ldxr, int64_t k, 
                                     pl->stream));
     }
     Timed t(pl, &pl->t_solve);
-    gls::launch_assemble_solve_split(Glin, Pbr, pl->ldp, pl->nI, pl->p, k, pl->RTL, pl->zT,
-                                     gls::kTauMixed, B, ldb, status, pl->stream);
+    gls::launch_assemble_solve_split(Glin, Pbr, pl->ldp, pl->nI, pl->p, pl->t_active, k, pl->RTL,
+                                     pl->zT, gls::kTauMixed, B, ldb, status, pl->stream);
     pl->launches += 3;
   }
   GLS_CUDA(cudaGetLastError());
@@ -674,9 +685,11 @@ gls_status_t gls_plan_create(const gls_plan_desc_t* desc, gls_plan_t* out) {
   pl->p = desc->p;
   pl->kmax = desc->max_block_snps;
   pl->precision = desc->precision;
+  pl->t = pl->t_active = phenotypes_of(*desc);
+  pl->nw = desc->p - 1 + pl->t;
   footprint(*desc, &pl->npad);
   const int64_t npad = pl->npad, n = pl->n, kmax = pl->kmax;
-  const int p = pl->p;
+  const int p = pl->p, nw = pl->nw;
   pl->nI = (int)((pl->precision == GLS_PREC_FP64) ? npad / gls::kT : npad / 128);
   pl->ldp = kmax;
 
@@ -711,27 +724,27 @@ gls_status_t gls_plan_create(const gls_plan_desc_t* desc, gls_plan_t* out) {
   gls_status_t st;
   if ((st = dev_alloc(&pl->A, (size_t)npad * npad)) != GLS_OK) return fail(st);
   if ((st = dev_alloc(&pl->Z, (size_t)npad * npad)) != GLS_OK) return fail(st);
-  if ((st = dev_alloc(&pl->Wrhs, (size_t)npad * p)) != GLS_OK) return fail(st);
-  if ((st = dev_alloc(&pl->Wt, (size_t)npad * p)) != GLS_OK) return fail(st);
-  if ((st = dev_alloc(&pl->gram, (size_t)p * p)) != GLS_OK) return fail(st);
+  if ((st = dev_alloc(&pl->Wrhs, (size_t)npad * nw)) != GLS_OK) return fail(st);
+  if ((st = dev_alloc(&pl->Wt, (size_t)npad * nw)) != GLS_OK) return fail(st);
+  if ((st = dev_alloc(&pl->gram, (size_t)nw * nw)) != GLS_OK) return fail(st);
   if ((st = dev_alloc(&pl->RTL, (size_t)32 * 32)) != GLS_OK) return fail(st);
-  if ((st = dev_alloc(&pl->zT, (size_t)32)) != GLS_OK) return fail(st);
+  if ((st = dev_alloc(&pl->zT, (size_t)32 * 32)) != GLS_OK) return fail(st);
   if ((st = dev_alloc(&pl->flags, (size_t)gls::kFlagCount)) != GLS_OK) return fail(st);
   if ((st = host_alloc(&pl->h_flags, (size_t)gls::kFlagCount)) != GLS_OK) return fail(st);
-  if ((st = dev_alloc(&pl->partials, partial_doubles(pl->precision, npad, p, kmax))) != GLS_OK)
+  if ((st = dev_alloc(&pl->partials, partial_doubles(pl->precision, npad, nw, kmax))) != GLS_OK)
     return fail(st);
   for (int s = 0; s < 2; ++s) {
     if ((st = dev_alloc(&pl->xr[s], (size_t)n * kmax)) != GLS_OK) return fail(st);
-    if ((st = dev_alloc(&pl->bdev[s], (size_t)p * kmax)) != GLS_OK) return fail(st);
+    if ((st = dev_alloc(&pl->bdev[s], (size_t)p * pl->t * kmax)) != GLS_OK) return fail(st);
     if ((st = dev_alloc(&pl->sdev[s], (size_t)kmax)) != GLS_OK) return fail(st);
   }
-  if (cudaMemsetAsync(pl->Wrhs, 0, sizeof(double) * npad * p, pl->stream) != cudaSuccess ||
+  if (cudaMemsetAsync(pl->Wrhs, 0, sizeof(double) * npad * nw, pl->stream) != cudaSuccess ||
       cudaMemsetAsync(pl->flags, 0, sizeof(int) * gls::kFlagCount, pl->stream) != cudaSuccess) {
     set_error("cudaMemset failed");
     return fail(GLS_ERR_CUDA);
   }
   if (pl->precision != GLS_PREC_FP64) {
-    if ((st = gls::mixed_create(&pl->mixed, n, npad, p, kmax, pl->precision, desc->split_terms,
+    if ((st = gls::mixed_create(&pl->mixed, n, npad, nw, kmax, pl->precision, desc->split_terms,
                                 desc->flags, desc->wait_limit_us, pl->stream)) != GLS_OK) {
       set_error("%s", gls::mixed_last_error());
       return fail(st);
@@ -754,14 +767,24 @@ gls_status_t gls_plan_create(const gls_plan_desc_t* desc, gls_plan_t* out) {
 
 gls_status_t gls_factor(gls_plan_t pl, const double* M, int64_t ldm, const double* XL,
                         int64_t ldxl, const double* y, int64_t* info) {
+  return gls_factor_y(pl, M, ldm, XL, ldxl, y, pl ? pl->n : 1, 1, info);
+}
+
+gls_status_t gls_factor_y(gls_plan_t pl, const double* M, int64_t ldm, const double* XL,
+                          int64_t ldxl, const double* Y, int64_t ldy, int32_t t,
+                          int64_t* info) {
   g_last_error.clear();
   if (info) *info = 0;
   if (!pl) {
     set_error("plan is NULL");
     return GLS_ERR_INVALID_ARG;
   }
-  if (!y) {
-    set_error("y is NULL");
+  if (!Y) {
+    set_error("Y is NULL");
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (t < 1 || t > pl->t || ldy < pl->n) {
+    set_error("t = %d outside [1, phenotypes = %d], or ldy < n", t, pl->t);
     return GLS_ERR_INVALID_ARG;
   }
   if (M && ldm < pl->n) {
@@ -785,7 +808,7 @@ gls_status_t gls_factor(gls_plan_t pl, const double* M, int64_t ldm, const doubl
   DeviceGuard guard(pl->device);
   pl->factored = false;
   const int64_t n = pl->n, npad = pl->npad;
-  const int p = pl->p;
+  const int p = pl->p, q = p - 1, nw = pl->nw;
   cudaStream_t st = pl->stream;
   Timed phase(pl, &pl->t_factor);
   GLS_CUDA(cudaMemsetAsync(pl->flags, 0, sizeof(int) * gls::kFlagCount, st));
@@ -820,10 +843,13 @@ gls_status_t gls_factor(gls_plan_t pl, const double* M, int64_t ldm, const doubl
                                n * sizeof(double), p - 1, cudaMemcpyDefault, st));
     pl->has_xl = true;
   }
-  GLS_CUDA(cudaMemcpyAsync(pl->Wrhs + (int64_t)(p - 1) * npad, y, n * sizeof(double),
-                           cudaMemcpyDefault, st));
+  GLS_CUDA(copy2d(pl->Wrhs + (int64_t)q * npad, npad * sizeof(double), Y, ldy * sizeof(double),
+                  n * sizeof(double), t, cudaMemcpyDefault, st));
+  if (q + t < nw)  // columns of phenotypes this call does not use: zero
+    GLS_CUDA(cudaMemsetAsync(pl->Wrhs + (int64_t)(q + t) * npad, 0,
+                             sizeof(double) * npad * (nw - q - t), st));
   if (pl->tc) {
-    cudaError_t e = gls::tc_lower_times(pl->tcf, pl->Z, npad, npad, pl->Wrhs, npad, p, pl->Wt,
+    cudaError_t e = gls::tc_lower_times(pl->tcf, pl->Z, npad, npad, pl->Wrhs, npad, nw, pl->Wt,
                                         npad, pl->flags, st);
     if (e != cudaSuccess) {
       set_error("tensor-core whitening: %s %s", cudaGetErrorString(e),
@@ -831,10 +857,10 @@ gls_status_t gls_factor(gls_plan_t pl, const double* M, int64_t ldm, const doubl
       return GLS_ERR_CUDA;
     }
   } else {
-    gls::launch_whiten(pl->Z, npad, n, npad, pl->Wrhs, npad, p, pl->Wt, npad, pl->flags, st);
+    gls::launch_whiten(pl->Z, npad, n, npad, pl->Wrhs, npad, nw, pl->Wt, npad, pl->flags, st);
   }
-  gls::launch_fixed_gram(pl->Wt, npad, n, p, pl->gram, st);
-  if (p > 1) gls::launch_small_chol(pl->gram, p, pl->RTL, pl->zT, pl->flags, st);
+  gls::launch_fixed_gram(pl->Wt, npad, n, nw, pl->gram, st);
+  if (p > 1) gls::launch_small_chol(pl->gram, nw, q, t, pl->RTL, pl->zT, pl->flags, st);
   pl->launches += (p > 1) ? 3 : 2;
   GLS_CUDA(cudaGetLastError());
   int hf[gls::kFlagCount];
@@ -854,7 +880,7 @@ gls_status_t gls_factor(gls_plan_t pl, const double* M, int64_t ldm, const doubl
     double* W = nullptr;  // M^{-1} [X_L | y] = Z^T [X~_L | y~]
     if (pl->tc) {
       W = gls::mixed_w_buffer(pl->mixed);
-      cudaError_t e = gls::tc_lower_t_times(pl->tcf, pl->Z, npad, npad, pl->Wt, npad, p, W, npad,
+      cudaError_t e = gls::tc_lower_t_times(pl->tcf, pl->Z, npad, npad, pl->Wt, npad, nw, W, npad,
                                             pl->flags, st);
       if (e != cudaSuccess) {
         set_error("tensor-core W: %s %s", cudaGetErrorString(e), gls::tc_factor_last_error());
@@ -868,6 +894,7 @@ gls_status_t gls_factor(gls_plan_t pl, const double* M, int64_t ldm, const doubl
   phase.finish();
   if (pl->tc) pl->launches += gls::tc_launches(pl->tcf) - tc_before;
   if (pl->precision != GLS_PREC_FP64) GLS_TRY(check_flags(pl, hf));
+  pl->t_active = t;
   pl->factored = true;
   return GLS_OK;
 }
@@ -933,12 +960,14 @@ gls_status_t gls_solve_block(gls_plan_t pl, const int8_t* XR, int64_t ldxr, int6
   const int64_t ldout = (mb == Mem::Device) ? ldb : pl->p;
   int32_t* sout = snp_status ? ((ms == Mem::Device) ? snp_status : pl->sdev[0]) : nullptr;
   GLS_TRY(replayed(pl, pl->replays,
-                   (KeyHash() << 2u << xin << ldin << k << bout << ldout << sout).h,
+                   (KeyHash() << 2u << xin << ldin << k << bout << ldout << sout
+                    << (uint64_t)pl->t_active).h,
                    [&]() { return run_block(pl, xin, ldin, k, bout, ldout, sout); }));
   const bool sync = (mx != Mem::Device) || (mb != Mem::Device) || (ms != Mem::Device);
   if (mb != Mem::Device)
     GLS_CUDA(copy2d(B, ldb * sizeof(double), bout, pl->p * sizeof(double),
-                               pl->p * sizeof(double), k, cudaMemcpyDeviceToHost, st));
+                               pl->p * sizeof(double), k * pl->t_active, cudaMemcpyDeviceToHost,
+                               st));
   if (snp_status && ms != Mem::Device)
     GLS_CUDA(cudaMemcpyAsync(snp_status, sout, k * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   if (sync) {
@@ -969,7 +998,7 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
                          double* B, int64_t ldb, int32_t* snp_status) {
   DeviceGuard guard(pl->device);
   const int64_t n = pl->n, kmax = pl->kmax;
-  const int p = pl->p;
+  const int p = pl->p, t = pl->t_active;  // b_ij of SNP i, phenotype j: column i t + j of B
   const int64_t width = packed ? gls::ceil_div(n, 4) : n;  // bytes per column
   const Mem mx = classify(X), mb = classify(B);
   const Mem ms = snp_status ? classify(snp_status) : Mem::Device;
@@ -995,7 +1024,7 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
     if (!packed && pageable_in && !pl->h_xr[s])
       GLS_TRY(host_alloc(&pl->h_xr[s], (size_t)n * kmax));
     if (pageable_out && !pl->h_b[s]) {
-      GLS_TRY(host_alloc(&pl->h_b[s], (size_t)p * kmax));
+      GLS_TRY(host_alloc(&pl->h_b[s], (size_t)p * pl->t * kmax));
       GLS_TRY(host_alloc(&pl->h_s[s], (size_t)kmax));
     }
   }
@@ -1054,8 +1083,8 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
     const int64_t s0 = blocks[jb].first, kb = blocks[jb].second;
     GLS_CUDA(cudaEventSynchronize(pl->ev_stored[s]));
     if (mb == Mem::Pageable)
-      for (int64_t c = 0; c < kb; ++c)
-        memcpy(B + (s0 + c) * ldb, pl->h_b[s] + c * p, sizeof(double) * p);
+      for (int64_t c = 0; c < kb * t; ++c)
+        memcpy(B + (s0 * t + c) * ldb, pl->h_b[s] + c * p, sizeof(double) * p);
     if (snp_status && ms == Mem::Pageable)
       memcpy(snp_status + s0, pl->h_s[s], sizeof(int32_t) * kb);
     return GLS_OK;
@@ -1068,7 +1097,7 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
     if (mx != Mem::Device && jb + 1 < blocks.size()) GLS_TRY(issue_load(jb + 1));
     if (mx != Mem::Device) GLS_CUDA(cudaStreamWaitEvent(cs, pl->ev_loaded[s], 0));
     GLS_CUDA(cudaStreamWaitEvent(cs, pl->ev_stored[s], 0));  // output slot s copied out
-    double* bout = out_b_host ? pl->bdev[s] : B + s0 * ldb;
+    double* bout = out_b_host ? pl->bdev[s] : B + s0 * t * ldb;
     const int64_t ldout = out_b_host ? p : ldb;
     int32_t* sout = snp_status ? (out_s_host ? pl->sdev[s] : snp_status + s0) : nullptr;
     if (packed && pl->precision != GLS_PREC_FP64) {
@@ -1076,7 +1105,8 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
       const uint8_t* src = (mx == Mem::Device) ? X + s0 * ldx : pl->xp[s];
       const int64_t ld = (mx == Mem::Device) ? ldx : width;
       GLS_TRY(replayed(pl, pl->replays,
-                       (KeyHash() << 3u << src << ld << kb << bout << ldout << sout).h,
+                       (KeyHash() << 3u << src << ld << kb << bout << ldout << sout
+                        << (uint64_t)t).h,
                        [&]() {
                          return run_block(pl, nullptr, 0, kb, bout, ldout, sout, src, ld);
                        }));
@@ -1096,7 +1126,8 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
         ldin = (mx == Mem::Device) ? ldx : n;
       }
       GLS_TRY(replayed(pl, pl->replays,
-                       (KeyHash() << 2u << xin << ldin << kb << bout << ldout << sout).h,
+                       (KeyHash() << 2u << xin << ldin << kb << bout << ldout << sout
+                        << (uint64_t)t).h,
                        [&]() { return run_block(pl, xin, ldin, kb, bout, ldout, sout); }));
     }
     GLS_CUDA(cudaEventRecord(pl->ev_computed[s], cs));
@@ -1115,10 +1146,11 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
           return copy2d(q.dst, q.lddst * sizeof(double), q.src, q.rows * sizeof(double),
                         q.rows * sizeof(double), q.cols, cudaMemcpyDeviceToHost, q.st);
         };
-        Copy q = (mb == Mem::Pinned)
-                     ? Copy{B + s0 * ldb, (size_t)ldb, bout, (size_t)p, (size_t)kb, pl->d2h}
-                     : Copy{pl->h_b[s], (size_t)p, bout, (size_t)p, (size_t)kb, pl->d2h};
-        GLS_CUDA(timed_copy(pl, &pl->t_d2h, pl->d2h, sizeof(double) * p * kb, issue, &q));
+        Copy q = (mb == Mem::Pinned) ? Copy{B + s0 * t * ldb, (size_t)ldb, bout, (size_t)p,
+                                            (size_t)(kb * t), pl->d2h}
+                                     : Copy{pl->h_b[s], (size_t)p, bout, (size_t)p,
+                                            (size_t)(kb * t), pl->d2h};
+        GLS_CUDA(timed_copy(pl, &pl->t_d2h, pl->d2h, sizeof(double) * p * kb * t, issue, &q));
       }
       if (out_s_host) {
         int32_t* dst = (ms == Mem::Pinned) ? snp_status + s0 : pl->h_s[s];
@@ -1333,7 +1365,7 @@ gls_status_t gls_batch_solve(gls_batch_t b, const int8_t* const* XR, const int64
   key << 3u << (uint64_t)group;
   for (int i = 0; i < count; ++i)
     key << XR[i] << ldxr[i] << k[i] << B[i] << ldb[i]
-        << (snp_status ? (const void*)snp_status[i] : nullptr);
+        << (snp_status ? (const void*)snp_status[i] : nullptr) << (uint64_t)b->plans[i]->t_active;
   // one round: every conversion, the persistent solve over all scans, every
   // p x p assembly; captured as one graph when the same round repeats
   GLS_TRY(replayed(p0, &b->replays, key.h, [&]() -> gls_status_t {
@@ -1356,8 +1388,8 @@ gls_status_t gls_batch_solve(gls_batch_t b, const int8_t* const* XR, const int64
       if (k[i] == 0) continue;
       gls_plan* pl = b->plans[i];
       gls::launch_assemble_solve_split(pl->partials + (int64_t)pl->nI * pl->ldp, pl->partials,
-                                       pl->ldp, pl->nI, pl->p, k[i], pl->RTL, pl->zT,
-                                       gls::kTauMixed, B[i], ldb[i],
+                                       pl->ldp, pl->nI, pl->p, pl->t_active, k[i], pl->RTL,
+                                       pl->zT, gls::kTauMixed, B[i], ldb[i],
                                        snp_status ? snp_status[i] : nullptr, st);
       p0->launches += 1;
     }

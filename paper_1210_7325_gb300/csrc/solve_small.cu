@@ -12,6 +12,9 @@
 //   z_B = (b_B_i - r^T z_T) / delta,  b_SNP = z_B / delta,
 //   b_cov = R_TL^{-T} (z_T - r b_SNP),   with z_T = R_TL^{-1} b_T (fixed).
 // A pivot delta^2 <= tau * S_BR_i marks S_i as not SPD: b_i = NaN, status 1.
+// With t phenotypes (Eq. 1's index j <= t), S_i and its factor are shared and
+// only b_B_ij and z_T,j differ: one factor per SNP, t pairs of triangular
+// solves, b_ij written to column i t + j of B.
 //
 // The Gram entries arrive as per-row-block partials P[I][q][j] and are summed
 // over I in ascending order (deterministic, independent of the launch shape).
@@ -22,13 +25,12 @@
 namespace gls {
 namespace {
 
-// The per-SNP part of the Cholesky solve of S_i, given s = S_BL_i (length q),
-// rho = b_B_i and sigma = S_BR_i.  R (q x q) and z (q) are R_TL and z_T.
-__device__ __forceinline__ void solve_one(double (&s)[kMaxP], double rho, double sigma, int p,
-                                          const double* R, const double* z, double tau,
-                                          double* out, int32_t* status_j) {
-  const int q = p - 1;
-  // r = R_TL^{-1} S_BL (in place in s)
+// Shared by the t phenotypes of one SNP: the per-SNP part of the Cholesky of
+// S_i (which does not depend on the phenotype).  s = S_BL_i (length q) becomes
+// r = R_TL^{-1} S_BL_i in place; returns delta = sqrt(S_BR_i - r^T r), or 0
+// when the pivot fails (delta^2 <= tau S_BR_i).
+__device__ __forceinline__ double factor_one(double (&s)[kMaxW], double sigma, int q,
+                                             const double* R, double tau) {
   for (int a = 0; a < q; ++a) {
     double t = s[a];
     for (int c = 0; c < a; ++c) t -= R[a + c * q] * s[c];
@@ -36,18 +38,20 @@ __device__ __forceinline__ void solve_one(double (&s)[kMaxP], double rho, double
   }
   double d = sigma;
   for (int a = 0; a < q; ++a) d -= s[a] * s[a];
-  if (!(d > tau * sigma)) {
-    for (int a = 0; a < p; ++a) out[a] = __longlong_as_double(0x7ff8000000000000ll);
-    if (status_j) *status_j = 1;
-    return;
-  }
-  const double delta = sqrt(d);
+  if (!(d > tau * sigma)) return 0.0;
+  return sqrt(d);
+}
+
+// One right-hand side: rho = b_B_ij = y~_j^T x~_i, z = z_T of phenotype j;
+// writes the p = q + 1 entries of b_ij (X_L coefficients, then the SNP's).
+__device__ __forceinline__ void solve_rhs(const double (&r)[kMaxW], double delta, double rho,
+                                          int q, const double* R, const double* z, double* out) {
   double zb = rho;
-  for (int a = 0; a < q; ++a) zb -= s[a] * z[a];
+  for (int a = 0; a < q; ++a) zb -= r[a] * z[a];
   zb /= delta;
   const double bsnp = zb / delta;
-  double bt[kMaxP];
-  for (int a = 0; a < q; ++a) bt[a] = z[a] - s[a] * bsnp;
+  double bt[kMaxW];
+  for (int a = 0; a < q; ++a) bt[a] = z[a] - r[a] * bsnp;
   for (int a = q - 1; a >= 0; --a) {
     double t = bt[a];
     for (int c = a + 1; c < q; ++c) t -= R[c + a * q] * bt[c];
@@ -55,74 +59,95 @@ __device__ __forceinline__ void solve_one(double (&s)[kMaxP], double rho, double
   }
   for (int a = 0; a < q; ++a) out[a] = bt[a];
   out[q] = bsnp;
+}
+
+// The whole SNP: one factor, t solves into columns j t + jj of B; a failed
+// pivot gives NaN for every phenotype and status 1.
+__device__ __forceinline__ void solve_snp(double (&s)[kMaxW], const double* rho, int64_t rho_ld,
+                                          double sigma, int p, int t, const double* R,
+                                          const double* z, double tau, double* Bj, int64_t ldb,
+                                          int32_t* status_j) {
+  const int q = p - 1;
+  const double delta = factor_one(s, sigma, q, R, tau);
+  if (delta == 0.0) {
+    for (int jj = 0; jj < t; ++jj)
+      for (int a = 0; a < p; ++a) Bj[a + jj * ldb] = __longlong_as_double(0x7ff8000000000000ll);
+    if (status_j) *status_j = 1;
+    return;
+  }
+  for (int jj = 0; jj < t; ++jj)
+    solve_rhs(s, delta, rho[jj * rho_ld], q, R, z + jj * q, Bj + jj * ldb);
   if (status_j) *status_j = 0;
 }
 
-// FP64 path: partials P[I][a][j] for a <= p (S_BL..., b_B, S_BR), summed over I
-// in ascending order.
+// FP64 path: partials P[I][a][j] for a <= nw (S_BL, the b_B, S_BR last),
+// summed over I in ascending order; the first t b_B rows are used.
 __global__ void __launch_bounds__(128) assemble_solve_kernel(
-    const double* __restrict__ P, int64_t ldp, int nI, int p, int64_t k,
+    const double* __restrict__ P, int64_t ldp, int nI, int p, int t, int nw, int64_t k,
     const double* __restrict__ RTL, const double* __restrict__ zT, double tau,
     double* __restrict__ B, int64_t ldb, int32_t* __restrict__ status) {
-  __shared__ double R[kMaxP * kMaxP];
-  __shared__ double z[kMaxP];
+  __shared__ double R[kMaxW * kMaxW];
+  __shared__ double z[kMaxW * kMaxW];
   const int q = p - 1;
-  for (int t = threadIdx.x; t < q * q; t += blockDim.x) R[t] = RTL[t];
-  for (int t = threadIdx.x; t < q; t += blockDim.x) z[t] = zT[t];
+  for (int i = threadIdx.x; i < q * q; i += blockDim.x) R[i] = RTL[i];
+  for (int i = threadIdx.x; i < q * t; i += blockDim.x) z[i] = zT[i];
   __syncthreads();
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= k) return;
-  double s[kMaxP];
-  double rho = 0.0, sigma = 0.0;
+  double s[kMaxW];
+  double rho[kMaxW];
+  double sigma = 0.0;
   for (int a = 0; a < q; ++a) s[a] = 0.0;
+  for (int a = 0; a < t; ++a) rho[a] = 0.0;
   for (int I = 0; I < nI; ++I) {
-    const double* pi = P + (int64_t)I * (p + 1) * ldp + j;
+    const double* pi = P + (int64_t)I * (nw + 1) * ldp + j;
     for (int a = 0; a < q; ++a) s[a] += pi[(int64_t)a * ldp];
-    rho += pi[(int64_t)q * ldp];
-    sigma += pi[(int64_t)p * ldp];
+    for (int a = 0; a < t; ++a) rho[a] += pi[(int64_t)(q + a) * ldp];
+    sigma += pi[(int64_t)nw * ldp];
   }
-  solve_one(s, rho, sigma, p, R, z, tau, B + j * ldb, status ? status + j : nullptr);
+  solve_snp(s, rho, 1, sigma, p, t, R, z, tau, B + j * t * ldb, ldb,
+            status ? status + j : nullptr);
 }
 
-// Mixed path: S_BL and b_B arrive whole in Glin[a][j]; S_BR as row-block
-// partials Pbr[I][j], summed over I in ascending order.
+// Mixed path: S_BL and the t b_B arrive whole in Glin[a][j]; S_BR as
+// row-block partials Pbr[I][j], summed over I in ascending order.
 __global__ void __launch_bounds__(128) assemble_solve_split_kernel(
     const double* __restrict__ Glin, const double* __restrict__ Pbr, int64_t ldp, int nI, int p,
-    int64_t k, const double* __restrict__ RTL, const double* __restrict__ zT, double tau,
+    int t, int64_t k, const double* __restrict__ RTL, const double* __restrict__ zT, double tau,
     double* __restrict__ B, int64_t ldb, int32_t* __restrict__ status) {
-  __shared__ double R[kMaxP * kMaxP];
-  __shared__ double z[kMaxP];
+  __shared__ double R[kMaxW * kMaxW];
+  __shared__ double z[kMaxW * kMaxW];
   const int q = p - 1;
-  for (int t = threadIdx.x; t < q * q; t += blockDim.x) R[t] = RTL[t];
-  for (int t = threadIdx.x; t < q; t += blockDim.x) z[t] = zT[t];
+  for (int i = threadIdx.x; i < q * q; i += blockDim.x) R[i] = RTL[i];
+  for (int i = threadIdx.x; i < q * t; i += blockDim.x) z[i] = zT[i];
   __syncthreads();
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= k) return;
-  double s[kMaxP];
+  double s[kMaxW];
   for (int a = 0; a < q; ++a) s[a] = Glin[(int64_t)a * ldp + j];
-  const double rho = Glin[(int64_t)q * ldp + j];
   double sigma = 0.0;
   for (int I = 0; I < nI; ++I) sigma += Pbr[(int64_t)I * ldp + j];
-  solve_one(s, rho, sigma, p, R, z, tau, B + j * ldb, status ? status + j : nullptr);
+  solve_snp(s, Glin + (int64_t)q * ldp + j, ldp, sigma, p, t, R, z, tau, B + j * t * ldb, ldb,
+            status ? status + j : nullptr);
 }
 
 }  // namespace
 
-void launch_assemble_solve(const double* partials, int64_t ldp, int nI, int p, int64_t k,
-                           const double* RTL, const double* zT, double tau, double* B,
-                           int64_t ldb, int32_t* status, cudaStream_t st) {
+void launch_assemble_solve(const double* partials, int64_t ldp, int nI, int p, int t, int nw,
+                           int64_t k, const double* RTL, const double* zT, double tau,
+                           double* B, int64_t ldb, int32_t* status, cudaStream_t st) {
   if (k <= 0) return;
   assemble_solve_kernel<<<(unsigned)ceil_div(k, 128), 128, 0, st>>>(
-      partials, ldp, nI, p, k, RTL, zT, tau, B, ldb, status);
+      partials, ldp, nI, p, t, nw, k, RTL, zT, tau, B, ldb, status);
 }
 
 void launch_assemble_solve_split(const double* Glin, const double* Pbr, int64_t ldp, int nI,
-                                 int p, int64_t k, const double* RTL, const double* zT,
+                                 int p, int t, int64_t k, const double* RTL, const double* zT,
                                  double tau, double* B, int64_t ldb, int32_t* status,
                                  cudaStream_t st) {
   if (k <= 0) return;
   assemble_solve_split_kernel<<<(unsigned)ceil_div(k, 128), 128, 0, st>>>(
-      Glin, Pbr, ldp, nI, p, k, RTL, zT, tau, B, ldb, status);
+      Glin, Pbr, ldp, nI, p, t, k, RTL, zT, tau, B, ldb, status);
 }
 
 }  // namespace gls

@@ -225,8 +225,8 @@ extern "C" gls_status_t gls_solve_block_fp64_static(int64_t n, int32_t p, const 
   dim3 grid((unsigned)gls::ceil_div(k, TS), (unsigned)nI);
   trsm_gram_fp64_static_kernel<<<grid, 256, sizeof(Smem), st>>>(Zinv, ldz, n, nI, XR, ldxr, k, W,
                                                                 ldw, p, scratch, k);
-  gls::launch_assemble_solve(scratch, k, nI, p, k, RTL, zT, gls::kTauFP64, B, ldb, snp_status,
-                             st);
+  gls::launch_assemble_solve(scratch, k, nI, p, 1, p, k, RTL, zT, gls::kTauFP64, B, ldb,
+                             snp_status, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(GLS_ERR_CUDA, cudaGetErrorString(e));
   return GLS_OK;

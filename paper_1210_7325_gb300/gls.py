@@ -52,7 +52,8 @@ class PlanDesc(ctypes.Structure):
         ("flags", ctypes.c_uint32),
         ("wait_limit_us", ctypes.c_int32),
         ("host_wait_ms", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("phenotypes", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 
@@ -92,6 +93,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.gls_plan_create.restype = i32
     lib.gls_factor.argtypes = [vp, vp, i64, vp, i64, vp, P(i64)]
     lib.gls_factor.restype = i32
+    lib.gls_factor_y.argtypes = [vp, vp, i64, vp, i64, vp, i64, i32, P(i64)]
+    lib.gls_factor_y.restype = i32
     lib.gls_solve_block.argtypes = [vp, vp, i64, i64, vp, i64, vp]
     lib.gls_solve_block.restype = i32
     lib.gls_solve_stream.argtypes = [vp, vp, i64, i64, vp, i64, vp]
@@ -144,7 +147,7 @@ def _check(status: int, where: str, info: int = 0):
 
 
 def make_desc(n, p, max_block_snps, precision="fp64", device=0, stream=None, split_terms=0,
-              flags=0, wait_limit_us=0, host_wait_ms=0) -> PlanDesc:
+              flags=0, wait_limit_us=0, host_wait_ms=0, phenotypes=1) -> PlanDesc:
     d = PlanDesc()
     d.n = int(n)
     d.p = int(p)
@@ -156,13 +159,15 @@ def make_desc(n, p, max_block_snps, precision="fp64", device=0, stream=None, spl
     d.flags = int(flags)
     d.wait_limit_us = int(wait_limit_us)
     d.host_wait_ms = int(host_wait_ms)
+    d.phenotypes = int(phenotypes)
     return d
 
 
-def footprint_bytes(n, p, max_block_snps, precision="fp64", split_terms=0, flags=0) -> int:
+def footprint_bytes(n, p, max_block_snps, precision="fp64", split_terms=0, flags=0,
+                    phenotypes=1) -> int:
     return int(load().gls_plan_footprint_bytes(
         ctypes.byref(make_desc(n, p, max_block_snps, precision, split_terms=split_terms,
-                               flags=flags))))
+                               flags=flags, phenotypes=phenotypes))))
 
 
 # ------------------------------------------------------------------ marshalling
@@ -263,12 +268,14 @@ class Plan:
     ``solve_stream`` over SNP blocks.  Thin wrapper over the C ABI."""
 
     def __init__(self, n, p, max_block_snps, precision="fp64", device=0, stream=None,
-                 split_terms=0, flags=0, wait_limit_us=0, host_wait_ms=0):
+                 split_terms=0, flags=0, wait_limit_us=0, host_wait_ms=0, phenotypes=1):
         lib = load()
         self.n, self.p, self.kmax = int(n), int(p), int(max_block_snps)
         self.precision = precision
+        self.phenotypes = int(phenotypes)  # capacity t of the plan
+        self.t = 1                         # phenotypes of the last factor
         self._desc = make_desc(n, p, max_block_snps, precision, device, stream, split_terms,
-                               flags, wait_limit_us, host_wait_ms)
+                               flags, wait_limit_us, host_wait_ms, phenotypes)
         h = ctypes.c_void_p()
         _check(lib.gls_plan_create(ctypes.byref(self._desc), ctypes.byref(h)), "gls_plan_create")
         self._h = h
@@ -298,14 +305,18 @@ class Plan:
 
     def factor(self, M, XL, y):
         """M: n x n column-major (lower triangle read) or None to keep the previous
-        factor; XL: n x (p-1) column-major or None; y: n vector."""
+        factor; XL: n x (p-1) column-major or None; y: an n vector, or an n x t
+        column-major matrix of t <= phenotypes phenotypes (gls_factor_y; then B
+        holds p x t values per SNP, column i t + j)."""
         lib = load()
         pm, ldm = _colmajor(M, self.n, 8, "M")
         px, ldx = _colmajor(XL, self.n, 8, "XL")
-        py, _ = _colmajor(y, self.n, 8, "y")
+        t = 1 if (y.ndim == 1 or y.shape[1] == 1) else int(y.shape[1])
+        py, ldy = _colmajor(y, self.n, 8, "y")
         info = ctypes.c_int64(0)
-        st = lib.gls_factor(self._h, pm, ldm, px, ldx, py, ctypes.byref(info))
-        _check(st, "gls_factor", info.value)
+        st = lib.gls_factor_y(self._h, pm, ldm, px, ldx, py, ldy, t, ctypes.byref(info))
+        _check(st, "gls_factor_y", info.value)
+        self.t = t
 
     def solve_block(self, XR, B, status=None, k=None):
         """XR: n x k int8 column-major; B: p x k float64 column-major (output);

@@ -9,6 +9,9 @@ Each request is one GWAS scan (its own n, p, m, M, X_L, y, X_R).  The server
     covariates and a new phenotype only re-whitens y (gls_factor with M = NULL);
   * factors newly admitted requests on worker threads (each plan has its own
     stream) while the main loop keeps the GPU busy with solves;
+  * admits waiting requests that share one M (and X_L, X_R) together, up to
+    the plans' phenotype capacity: their phenotypes join one factor call
+    (gls_factor_y) and every solve pass over X_R serves all of them;
   * solves in rounds: every round runs ONE batched launch (gls_batch_solve)
     over the next block of every active request (mixed precision), or one
     block per active request on their own streams (FP64), so requests that
@@ -75,8 +78,13 @@ class _Slot:
 
 
 class _Active:
-    def __init__(self, req, slot, inputs, B, st, t_admit):
-        self.req = req
+    """Requests being served on one plan: the leader and the requests that
+    share its M and joined as further phenotypes (b_ij of phenotype j in
+    row i t + j of B)."""
+
+    def __init__(self, reqs, slot, inputs, B, st, t_admit):
+        self.reqs = reqs
+        self.req = reqs[0]
         self.slot = slot
         self.inputs = inputs
         self.B = B
@@ -88,7 +96,8 @@ class _Active:
 
 class Server:
     def __init__(self, make_inputs, precision="bf16", hbm_budget=150e9, block=32768,
-                 factor_workers=4, group=0, device="cuda", streams=None, keep=None):
+                 factor_workers=4, group=0, device="cuda", streams=None, keep=None,
+                 phenotypes=4):
         """make_inputs(req, torch, reuse) -> Inputs (device tensors for the request,
         made by work on the current stream; with reuse=True the factor of M is
         cached, so M and X_L may be None).  ``streams`` supplies
@@ -107,6 +116,7 @@ class Server:
         self.budget = float(hbm_budget)
         self.block = int(block)
         self.group = int(group)
+        self.phenotypes = max(1, int(phenotypes))  # phenotype capacity of every plan
         self.slots: Dict[int, _Slot] = {}
         self.used = 0.0
         self.pool = cf.ThreadPoolExecutor(max_workers=factor_workers)
@@ -123,7 +133,8 @@ class Server:
 
     # ------------------------------------------------------------ memory
     def _plan_bytes(self, n, p):
-        return gls.footprint_bytes(n, p, self.block, self.precision)
+        return gls.footprint_bytes(n, p, self.block, self.precision,
+                                   phenotypes=min(self.phenotypes, 33 - p))
 
     def _input_bytes(self, req):
         return req.n * req.m + req.m * req.p * 8 + req.m * 4 + req.n * req.n * 8
@@ -145,11 +156,14 @@ class Server:
             self.batches.pop(key).close()
 
     # ------------------------------------------------------------ admission
-    def _try_admit(self, req, now):
+    def _try_admit(self, req, now, companions=()):
+        """Admits req and, as further phenotypes of the same factor, the waiting
+        requests in `companions` (same mkey) that fit the plan's capacity."""
         slot = self.slots.get(req.mkey)
         if slot is not None and slot.busy:
             return None  # the resident factor is serving another phenotype
-        in_bytes = self._input_bytes(req)
+        reqs = [req] + list(companions)[:min(self.phenotypes, 33 - req.p) - 1]
+        in_bytes = sum(self._input_bytes(r) for r in reqs)
         need = in_bytes + (0 if slot is not None else self._plan_bytes(req.n, req.p))
         if need > self.budget:
             raise MemoryError(f"request {req.rid} needs {need:.3g} B, above the HBM budget")
@@ -164,11 +178,15 @@ class Server:
         reuse = slot is not None
         t = time.perf_counter()
         inputs = self.make_inputs(req, self.torch, reuse)
+        if len(reqs) > 1:  # the companions' phenotypes: Y = [y_1 ... y_g], column-major
+            ys = [inputs.y] + [self.make_inputs(r, self.torch, True).y for r in reqs[1:]]
+            inputs.y = self.torch.stack(ys, dim=0).t()
         ready = self._inputs_ready()
         self.breakdown["inputs_s"] += time.perf_counter() - t
         if not reuse:
             t = time.perf_counter()
-            plan = gls.Plan(req.n, req.p, self.block, precision=self.precision)
+            plan = gls.Plan(req.n, req.p, self.block, precision=self.precision,
+                            phenotypes=min(self.phenotypes, 33 - req.p))
             self.breakdown["plan_create_s"] += time.perf_counter() - t
             slot = _Slot(plan, req.mkey, req.n, req.p, self._plan_bytes(req.n, req.p))
             self.slots[req.mkey] = slot
@@ -177,9 +195,11 @@ class Server:
         self.used += in_bytes
         self.peak_used = max(self.peak_used, self.used)
         torch = self.torch
-        B = torch.empty((req.m, req.p), dtype=torch.float64, device=self.device)
+        B = torch.empty((req.m * len(reqs), req.p), dtype=torch.float64, device=self.device)
         st = torch.empty(req.m, dtype=torch.int32, device=self.device)
-        act = _Active(req, slot, inputs, B, st, now)
+        act = _Active(reqs, slot, inputs, B, st, now)
+        if len(reqs) > 1:
+            self.breakdown["grouped"] = self.breakdown.get("grouped", 0) + len(reqs) - 1
         if ready is not None:
             # the plan's stream reads the inputs only after their producer wrote them
             slot.plan.wait_event(ready)
@@ -226,15 +246,16 @@ class Server:
             parts.append((a, s0, k))
         if self.precision == "fp64":
             for a, s0, k in parts:
-                a.slot.plan.solve_block(a.inputs.XR[s0:s0 + k].t(), a.B[s0:s0 + k].t(),
-                                        a.st[s0:s0 + k], k=k)
+                g = len(a.reqs)
+                a.slot.plan.solve_block(a.inputs.XR[s0:s0 + k].t(),
+                                        a.B[s0 * g:(s0 + k) * g].t(), a.st[s0:s0 + k], k=k)
             for a, s0, k in parts:
                 a.slot.plan.synchronize()
         else:
             acts = [a for a, _, _ in parts]
             batch = self._batch_for(acts)
             batch.solve([a.inputs.XR[s0:s0 + k].t() for a, s0, k in parts],
-                        [a.B[s0:s0 + k].t() for a, s0, k in parts],
+                        [a.B[s0 * len(a.reqs):(s0 + k) * len(a.reqs)].t() for a, s0, k in parts],
                         [a.st[s0:s0 + k] for a, s0, k in parts],
                         [k for _, _, k in parts], group=self.group)
         for a, s0, k in parts:
@@ -243,11 +264,14 @@ class Server:
     def _finish(self, a, now):
         a.slot.busy = False
         a.slot.last_used = now
-        self.used -= self._input_bytes(a.req)
-        self.results[a.req.rid] = dict(
-            rid=a.req.rid, arrival=a.req.arrival, admitted=a.t_admit, done=now,
-            latency=now - a.req.arrival, n=a.req.n, p=a.req.p, m=a.req.m, reuse=a.req.reuse,
-            B=a.B, status=a.st)
+        g = len(a.reqs)
+        Bg = a.B.view(a.req.m, g, a.req.p)
+        for j, r in enumerate(a.reqs):
+            self.used -= self._input_bytes(r)
+            self.results[r.rid] = dict(
+                rid=r.rid, arrival=r.arrival, admitted=a.t_admit, done=now,
+                latency=now - r.arrival, n=r.n, p=r.p, m=r.m, reuse=r.reuse,
+                B=Bg[:, j, :] if g > 1 else a.B, status=a.st, phenotypes_in_call=g)
 
     # ------------------------------------------------------------ main loop
     def run(self, requests: List[Request], time_cap: float = float("inf"), keep_outputs=False):
@@ -279,8 +303,9 @@ class Server:
                 if len(active) >= MAX_BATCH:
                     still.append(req)
                     continue
+                same = [r for r in waiting if r.mkey == req.mkey]
                 try:
-                    act = self._try_admit(req, time.perf_counter() - t0)
+                    act = self._try_admit(req, time.perf_counter() - t0, same)
                 except MemoryError as e:
                     self.rejected.append((req.rid, str(e)))
                     continue
@@ -288,6 +313,8 @@ class Server:
                     still.append(req)
                 else:
                     active.append(act)
+                    for r in act.reqs[1:]:
+                        waiting.remove(r)
             waiting = still
             self.breakdown["admit_s"] += time.perf_counter() - t_adm
             self.queue_depth.append((now, len(waiting), len(active)))
@@ -311,9 +338,10 @@ class Server:
             for a in [a for a in active if a.factored.done() and a.next >= a.req.m]:
                 self._finish(a, done_now)
                 active.remove(a)
-                if not keep_outputs and a.req.rid not in self.keep:
-                    self.results[a.req.rid].pop("B")
-                    self.results[a.req.rid].pop("status")
+                for r in a.reqs:
+                    if not keep_outputs and r.rid not in self.keep:
+                        self.results[r.rid].pop("B")
+                        self.results[r.rid].pop("status")
 
     def close(self):
         # a run cut off by its time cap can leave factors running on the

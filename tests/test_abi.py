@@ -75,13 +75,19 @@ def test_invalid_descriptions_rejected_without_gpu(lib):
     d = gls.make_desc(10, 3, 10, host_wait_ms=-5)
     assert lib.gls_plan_create(ctypes.byref(d), ctypes.byref(h)) == 1
     assert "host_wait_ms" in gls.last_error()
+    d = gls.make_desc(10, 20, 10, phenotypes=14)       # p - 1 + t = 33 > 32
+    assert lib.gls_plan_create(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert "phenotypes" in gls.last_error()
+    d = gls.make_desc(10, 20, 10, phenotypes=13)
+    assert gls.footprint_bytes(10, 20, 10, phenotypes=13) > gls.footprint_bytes(10, 20, 10)
     assert lib.gls_destroy(None) == 0
 
 
 def test_desc_layout_matches_header():
     # 8 + 4 + 4 + 8 + 4 + 4 + 8 + 4 + 4 + 4 + 5 * 4 bytes, 8-aligned
     assert ctypes.sizeof(gls.PlanDesc) == 72
-    assert gls.PlanDesc.wait_limit_us.offset == 44 and gls.PlanDesc.reserved.offset == 52
+    assert gls.PlanDesc.wait_limit_us.offset == 44 and gls.PlanDesc.phenotypes.offset == 52
+    assert gls.PlanDesc.reserved.offset == 56
     assert ctypes.sizeof(gls.Stats) == 15 * 8
 
 

@@ -54,10 +54,11 @@ class FakeGls:
         self.batches = []      # number of plans per batched launch
         self.closed_use = 0
         self.inflight = 0      # factors running now
+        self.groups = []       # phenotypes per factor call
         self.factor_s = 0.002
         self.unordered = []    # reads of inputs the plan was not ordered after
 
-    def footprint_bytes(self, n, p, block, precision):
+    def footprint_bytes(self, n, p, block, precision, phenotypes=1):
         return 8 * n * n + 1000
 
     def make(self):
@@ -66,8 +67,9 @@ class FakeGls:
         class Plan:
             ids = iter(range(10**6))
 
-            def __init__(self, n, p, block, precision="fp64"):
+            def __init__(self, n, p, block, precision="fp64", phenotypes=1):
                 self.n, self.p, self.block, self.precision = n, p, block, precision
+                self.capacity = phenotypes
                 self.id = next(Plan.ids)
                 self.closed = False
                 self.yv = None
@@ -97,13 +99,16 @@ class FakeGls:
                         fake.closed_use += 1
                         raise RuntimeError("factor on a closed plan")
                     fake.factors.append((self.id, M is not None))
-                self.yv = float(y.sum())
+                    fake.groups.append(1 if y.dim() == 1 else y.shape[1])
+                assert (1 if y.dim() == 1 else y.shape[1]) <= self.capacity
+                self.yv = y.sum(dim=0).reshape(-1)  # one sum per phenotype
 
             def _fill(self, XR, B, st):
-                # b_i := (sum of the SNP column + y sum) in every row: a function of
-                # the request's own data only
-                v = XR.t().double().sum(dim=1) + self.yv
-                B.t()[:] = v[:, None]
+                # b_ij := (sum of the SNP column + sum of phenotype j) in every row of
+                # column i t + j: a function of the request's own data only
+                t = self.yv.numel()
+                v = XR.t().double().sum(dim=1)[:, None] + self.yv[None, :]   # (k, t)
+                B.t()[:] = v.reshape(-1)[:, None]
                 st[:] = 0
 
             def solve_block(self, XR, B, st, k=None):
@@ -174,14 +179,15 @@ def test_every_request_served_once_within_budget(fake, prec, budget):
         B = res[r.rid]["B"]
         assert torch.equal(B[:, 0], expected(r)), r.rid
         assert torch.equal(B[:, -1], expected(r))
-    # each resident factor serves a new phenotype with M = None
-    reused = sum(1 for r in reqs if r.reuse)
+    # every phenotype is in exactly one factor call; a resident factor serves
+    # new phenotypes with M = None
+    assert sum(fake.groups) == len(reqs)
+    distinct = len({r.mkey for r in reqs})
     with_m = sum(1 for _, m in fake.factors if m)
-    assert with_m + sum(1 for _, m in fake.factors if not m) == len(reqs)
     if budget >= 1e9:
-        assert with_m == len(reqs) - reused       # nothing evicted
+        assert with_m == distinct                 # nothing evicted: one factor per M
     else:
-        assert with_m > len(reqs) - reused        # evictions forced re-factoring
+        assert with_m > distinct                  # evictions forced re-factoring
     if prec != "fp64":
         assert max(fake.batches) > 1               # requests shared launches
 
@@ -260,3 +266,24 @@ def test_kept_outputs(fake):
     srv.close()
     assert "B" in res[0] and "B" in res[3] and "B" not in res[1]
     assert torch.equal(res[3]["B"][:, 0], expected(reqs[3]))
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp64"])
+def test_requests_sharing_an_m_join_one_factor(fake, prec):
+    """A burst of requests on one M (new phenotypes) waiting together is
+    served by factor calls with several phenotypes, up to the capacity, and
+    every request still gets its own b."""
+    base = serve.Request(0, 0.0, 150, 3, 200, 7, 100)
+    reqs = [base] + [serve.Request(i, 0.0, 150, 3, 200, 7, 100 + i, reuse=True)
+                     for i in range(1, 7)]
+    reqs += [serve.Request(7, 0.0, 120, 2, 100, 8, 300)]
+    srv = serve.Server(make_inputs, prec, hbm_budget=1e9, block=64, device="cpu", phenotypes=4)
+    res = srv.run(reqs, time_cap=60.0, keep_outputs=True)
+    srv.close()
+    assert sorted(res) == list(range(8))
+    assert max(fake.groups) == 4 and sum(fake.groups) == 8
+    assert srv.breakdown["grouped"] >= 3
+    for r in reqs:
+        B = res[r.rid]["B"]
+        assert torch.equal(B[:, 0], expected(r)), r.rid
+        assert torch.equal(B[:, -1], expected(r))
