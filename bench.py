@@ -286,6 +286,25 @@ def run_gpu(args, wl, rank, world, torch, dist):
                                             if sd["d2h_ms"] > 0 else None)}
         res["e2e_diag"] = diag(e2e_step)
         res["e2e_int8_diag"] = diag(e2e_int8)
+        # the int8 stream through the copy engine (the pre-existing staged path) on a
+        # plan of its own, for comparison with the in-place reads above
+        plan_st = gls.Plan(n, p, kmax, precision=prec, device=dev.index, split_terms=split,
+                           flags=launch_flags(args, gls) | gls.GLS_FLAG_STAGED_INPUT)
+
+        def e2e_int8_staged():
+            plan_st.factor(Mh, XLh, yh)
+            plan_st.solve_stream(XRh.t(), Bh.t(), sh, m=m)
+
+        e2e_int8_staged()  # warm-up
+        steps_st = min(args.steps, 3)
+        marks = [time.perf_counter()]
+        for _ in range(steps_st):
+            e2e_int8_staged()
+            marks.append(time.perf_counter())
+        res["e2e_int8_staged"] = {
+            "steps": steps_st, "value": m * steps_st / (marks[-1] - marks[0]),
+            "step_ms": [round((b - a) * 1e3, 2) for a, b in zip(marks, marks[1:])]}
+        plan_st.close()
         # context for the end-to-end figure: this box's pinned host -> device copy rate
         # ... over every block of the pinned genotype buffer (placement of its
         # pages can differ along the buffer), best of 3 per block
@@ -779,7 +798,8 @@ def run_serve_workload(args, sw, torch, time_cap=None):
     srv.run(warm)
     srv.close()
     kept = serve_kept(reqs)
-    srv = serve.Server(make, sw["precision"], sw["budget"], sw["block"], keep=kept)
+    srv = serve.Server(make, sw["precision"], sw["budget"], sw["block"], keep=kept,
+                       trace=getattr(args, "serve_trace", None))
     cap = time_cap or getattr(args, "time_cap", 0) or sw["time_cap"]
     t0 = time.perf_counter()
     results = srv.run(reqs, time_cap=cap)
@@ -913,7 +933,8 @@ def sub_batch(args, torch, name="batch48_uneven_bf16", steps=2, warmup=1):
 def sub_serve(args, torch, name="serve2000_bf16", time_cap=180.0):
     """The serving workload as a sub-object of the default line (time-capped)."""
     try:
-        ln = run_serve_workload(argparse.Namespace(workload=name, requests=0, time_cap=0),
+        ln = run_serve_workload(argparse.Namespace(workload=name, requests=0, time_cap=0,
+                                                   serve_trace=args.serve_trace),
                                 SERVE_WORKLOADS[name], torch, time_cap=time_cap)
     except Exception as ex:  # reported, not fatal to the headline line
         return {"workload": name, "error_raised": repr(ex)}
@@ -977,6 +998,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-sub", action="store_true",
                     help="default workload: skip the batched-scan and serving legs")
+    ap.add_argument("--serve-trace", default=None,
+                    help="serving: append one line per admission, round and eviction to this file")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--cpu-snps", type=int, default=2048)
@@ -1092,9 +1115,11 @@ def main():
             line["e2e_int8"] = {"value": whole_job_rate(world, m, K, e8_max), "unit": UNIT,
                                 "h2d_bytes_per_step": res["e2e_int8_h2d"],
                                 "d2h_bytes_per_step": res["e2e_d2h"],
-                                "genotype_input": "int8 (gls_solve_stream)",
+                                "genotype_input": "int8 (gls_solve_stream), pinned blocks "
+                                                  "read in place by the conversion kernel",
                                 "step_ms": res.get("e2e_int8_step_ms"),
-                                "diagnostic_step": res.get("e2e_int8_diag")}
+                                "diagnostic_step": res.get("e2e_int8_diag"),
+                                "staged_copy_engine": res.get("e2e_int8_staged")}
     if not args.skip_fp64 and wl["precision"] != "fp64":
         try:
             line["fp64"] = fp64_sample(wl, torch)
@@ -1115,15 +1140,15 @@ def main():
                                       1e-10 if wl["precision"] == "fp64" else 1e-6)
     del res
     if world == 1 and not args.skip_sub and args.workload == DEFAULT_WORKLOAD:
-        torch.cuda.empty_cache()
-        line["batch"] = sub_batch(args, torch)
-        torch.cuda.empty_cache()
-        line["serve"] = sub_serve(args, torch)
-        torch.cuda.empty_cache()
-        try:
-            line["phenotypes"] = sub_phenotypes(args, torch)
-        except Exception as ex:  # reported, not fatal to the headline line
-            line["phenotypes"] = {"error_raised": repr(ex)}
+        # each leg reports its own failure; the headline line is printed regardless
+        for key, leg in (("batch", lambda: sub_batch(args, torch)),
+                         ("serve", lambda: sub_serve(args, torch)),
+                         ("phenotypes", lambda: sub_phenotypes(args, torch))):
+            try:
+                torch.cuda.empty_cache()
+                line[key] = leg()
+            except Exception as ex:
+                line[key] = {"error_raised": repr(ex)}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

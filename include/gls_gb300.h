@@ -120,6 +120,13 @@ typedef enum {
  * While such a call runs, nothing else may enqueue work on the plan's stream
  * (gls_plan_stream) from another thread: a capture would take it in. */
 #define GLS_FLAG_EAGER 8u
+/* Mixed paths: gls_solve_stream copies pinned int8 blocks to the device with
+ * the copy engine (double-buffered on a side stream) instead of reading them
+ * in place.  By default the conversion kernel reads each pinned block over the
+ * host link itself: the copy engine's rate on this part falls several-fold
+ * while kernels run, reading in place does not depend on it.  Results are the
+ * same either way. */
+#define GLS_FLAG_STAGED_INPUT 16u
 
 /* Plan description.  Zero-initialise and fill the fields that matter. */
 typedef struct {
@@ -229,7 +236,8 @@ gls_status_t gls_solve_block(gls_plan_t plan, const int8_t* XR, int64_t ldxr, in
  * buffers).  Blocks of up to max_block_snps columns are double-buffered: the
  * copy of block j+1 to the device runs on a side stream while block j is
  * solved, and b of block j is copied back while block j+1 is solved
- * (Section 4.2).  The first block is smaller so that its unoverlapped load is
+ * (Section 4.2).  Mixed plans read pinned int8 input in place instead (see
+ * GLS_FLAG_STAGED_INPUT).  The first block is smaller so that its unoverlapped load is
  * short (Section 4.3).  B (p x m, or p x (m t) with t phenotypes; ldb >= p)
  * and snp_status (m, may be NULL) are host memory.  Synchronous.  Device-resident XR is also accepted, in
  * which case only B and snp_status are copied.

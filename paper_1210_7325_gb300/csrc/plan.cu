@@ -53,14 +53,20 @@ struct DeviceGuard {
 
 enum class Mem { Device, Pinned, Pageable };
 
-Mem classify(const void* p) {
+// Where p lives; for pinned host memory *dev (if given) receives the address
+// kernels use for it (the runtime's device pointer of the mapping).
+Mem classify(const void* p, const void** dev = nullptr) {
+  if (dev) *dev = nullptr;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return Mem::Pageable;
   }
   if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return Mem::Device;
-  if (a.type == cudaMemoryTypeHost) return Mem::Pinned;
+  if (a.type == cudaMemoryTypeHost) {
+    if (dev) *dev = a.devicePointer;
+    return Mem::Pinned;
+  }
   return Mem::Pageable;
 }
 
@@ -407,8 +413,8 @@ gls_status_t validate_desc(const gls_plan_desc_t* d) {
     set_error("split_terms must be 0, 2 or 3");
     return GLS_ERR_INVALID_ARG;
   }
-  const uint32_t known =
-      GLS_FLAG_NAIVE_SPLIT | GLS_FLAG_FACTOR_NATIVE | GLS_FLAG_FACTOR_TENSOR | GLS_FLAG_EAGER;
+  const uint32_t known = GLS_FLAG_NAIVE_SPLIT | GLS_FLAG_FACTOR_NATIVE | GLS_FLAG_FACTOR_TENSOR |
+                         GLS_FLAG_EAGER | GLS_FLAG_STAGED_INPUT;
   if ((d->flags & ~known) != 0) {
     set_error("unknown flag bits 0x%x", d->flags);
     return GLS_ERR_INVALID_ARG;
@@ -1000,8 +1006,15 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
   const int64_t n = pl->n, kmax = pl->kmax;
   const int p = pl->p, t = pl->t_active;  // b_ij of SNP i, phenotype j: column i t + j of B
   const int64_t width = packed ? gls::ceil_div(n, 4) : n;  // bytes per column
-  const Mem mx = classify(X), mb = classify(B);
+  const void* Xdev = nullptr;
+  const Mem mx = classify(X, &Xdev), mb = classify(B);
   const Mem ms = snp_status ? classify(snp_status) : Mem::Device;
+  // Mixed plans read pinned int8 blocks in place: the conversion kernel loads
+  // them over the host link through the mapping's device address, and the
+  // copy engine (whose rate falls several-fold while kernels run) is idle.
+  const bool direct = !packed && pl->precision != GLS_PREC_FP64 && mx == Mem::Pinned && Xdev &&
+                      !(pl->desc.flags & GLS_FLAG_STAGED_INPUT);
+  const bool staged = (mx != Mem::Device) && !direct;
 
   // Block schedule: a short first block (its load is not overlapped), then
   // doubling up to max_block_snps (Section 4.3).
@@ -1090,12 +1103,12 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
     return GLS_OK;
   };
 
-  if (mx != Mem::Device) GLS_TRY(issue_load(0));
+  if (staged) GLS_TRY(issue_load(0));
   for (size_t jb = 0; jb < blocks.size(); ++jb) {
     const int s = (int)(jb % 2);
     const int64_t s0 = blocks[jb].first, kb = blocks[jb].second;
-    if (mx != Mem::Device && jb + 1 < blocks.size()) GLS_TRY(issue_load(jb + 1));
-    if (mx != Mem::Device) GLS_CUDA(cudaStreamWaitEvent(cs, pl->ev_loaded[s], 0));
+    if (staged && jb + 1 < blocks.size()) GLS_TRY(issue_load(jb + 1));
+    if (staged) GLS_CUDA(cudaStreamWaitEvent(cs, pl->ev_loaded[s], 0));
     GLS_CUDA(cudaStreamWaitEvent(cs, pl->ev_stored[s], 0));  // output slot s copied out
     double* bout = out_b_host ? pl->bdev[s] : B + s0 * t * ldb;
     const int64_t ldout = out_b_host ? p : ldb;
@@ -1121,9 +1134,12 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
         pl->launches += 1;
         xin = pl->xr[s];
         ldin = n;
+      } else if (mx == Mem::Device || direct) {
+        xin = reinterpret_cast<const int8_t*>(direct ? Xdev : X) + s0 * ldx;
+        ldin = ldx;
       } else {
-        xin = (mx == Mem::Device) ? reinterpret_cast<const int8_t*>(X) + s0 * ldx : pl->xr[s];
-        ldin = (mx == Mem::Device) ? ldx : n;
+        xin = pl->xr[s];
+        ldin = n;
       }
       GLS_TRY(replayed(pl, pl->replays,
                        (KeyHash() << 2u << xin << ldin << kb << bout << ldout << sout

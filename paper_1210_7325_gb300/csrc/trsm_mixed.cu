@@ -299,6 +299,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const Item w = item_at(probs, run, t);
         const ProblemDesc* pd = probs + w.pi;
         if (w.pi != last_pi) {
+          // the maps live in global memory written by the host: fence before
+          // this thread's first TMA with them (see tensormap_acquire_sys)
+          tensormap_acquire_sys(&pd->tmA);
+          tensormap_acquire_sys(&pd->tmB);
           tma_prefetch_desc(&pd->tmA);
           tma_prefetch_desc(&pd->tmB);
           last_pi = w.pi;
@@ -544,6 +548,49 @@ __global__ void convert_x_kernel(const int8_t* __restrict__ x8, int64_t ldx, int
     bb.x = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
     bb.y = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
     *reinterpret_cast<uint2*>(x8a + j * npad + c0) = bb;
+  }
+}
+
+// The same outputs with 16 rows per thread and one 16-byte load of codes, for
+// sources whose columns start on 16-byte boundaries.  Used for HBM sources
+// and for pinned host memory read in place over the host link (the stream's
+// direct path), where wide requests keep enough bytes in flight.
+template <bool kBF16>
+__global__ void __launch_bounds__(256) convert_x_wide_kernel(
+    const int8_t* __restrict__ x8, int64_t ldx, int64_t n, int64_t k, int64_t npad,
+    uint16_t* __restrict__ x16, uint8_t* __restrict__ x8a) {
+  const int64_t per_col = npad / 16;
+  const int64_t total = k * per_col;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = idx / per_col;
+    const int64_t c0 = (idx - j * per_col) * 16;
+    const int8_t* col = x8 + j * ldx;
+    uint4 raw = make_uint4(0, 0, 0, 0);
+    if (c0 + 16 <= n) {
+      raw = *reinterpret_cast<const uint4*>(col + c0);
+    } else if (c0 < n) {  // ragged end of the column: bytes, rows >= n stay zero
+      uint32_t w[4] = {0, 0, 0, 0};
+      for (int e = 0; e < 16 && c0 + e < n; ++e)
+        w[e / 4] |= (uint32_t)(uint8_t)col[c0 + e] << (8 * (e % 4));
+      raw = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    const uint32_t wv[4] = {raw.x, raw.y, raw.z, raw.w};
+    uint32_t o[8];
+#pragma unroll
+    for (int e = 0; e < 16; e += 2) {
+      const float a = (float)(int8_t)(wv[e / 4] >> (8 * (e % 4)));
+      const float b = (float)(int8_t)(wv[e / 4] >> (8 * (e % 4 + 1)));
+      const uint32_t va = kBF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(a))
+                                : __half_as_ushort(__float2half_rn(a));
+      const uint32_t vb = kBF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(b))
+                                : __half_as_ushort(__float2half_rn(b));
+      o[e / 2] = va | (vb << 16);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(x16 + j * npad + c0);
+    dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+    dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    *reinterpret_cast<uint4*>(x8a + j * npad + c0) = raw;
   }
 }
 
@@ -995,6 +1042,18 @@ gls_status_t mixed_prepare(MixedState* ms, const double* Z, int64_t ldz, const d
 cudaError_t mixed_convert(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,
                           cudaStream_t st) {
   if (k <= 0) return cudaSuccess;
+  if (((uintptr_t)xr % 16) == 0 && (ldxr % 16) == 0) {
+    const int64_t work = k * (ms->npad / 16);
+    const unsigned grid =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 256), ms->num_sms * 8));
+    if (ms->bf16)
+      convert_x_wide_kernel<true><<<grid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, ms->x16,
+                                                        ms->x8a);
+    else
+      convert_x_wide_kernel<false><<<grid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, ms->x16,
+                                                         ms->x8a);
+    return cudaGetLastError();
+  }
   const int64_t work = k * (ms->npad / 8);
   const unsigned cgrid = (unsigned)std::min<int64_t>(ceil_div(work, 256), 65535 * 4);
   if (ms->bf16)

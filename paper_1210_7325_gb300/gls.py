@@ -29,6 +29,7 @@ GLS_FLAG_NAIVE_SPLIT = 1
 GLS_FLAG_FACTOR_NATIVE = 2
 GLS_FLAG_FACTOR_TENSOR = 4
 GLS_FLAG_EAGER = 8
+GLS_FLAG_STAGED_INPUT = 16
 
 
 class GlsError(RuntimeError):

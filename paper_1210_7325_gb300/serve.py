@@ -97,13 +97,14 @@ class _Active:
 class Server:
     def __init__(self, make_inputs, precision="bf16", hbm_budget=150e9, block=32768,
                  factor_workers=4, group=0, device="cuda", streams=None, keep=None,
-                 phenotypes=4):
+                 phenotypes=4, trace=None):
         """make_inputs(req, torch, reuse) -> Inputs (device tensors for the request,
         made by work on the current stream; with reuse=True the factor of M is
         cached, so M and X_L may be None).  ``streams`` supplies
         current_stream() and Event() (torch.cuda by default on a GPU device,
         none on the CPU); ``keep`` is a set of request ids whose outputs run()
-        keeps (every request's with keep_outputs=True)."""
+        keeps (every request's with keep_outputs=True); ``trace`` a file that
+        gets one flushed line per admission, round, eviction and batch."""
         import torch
         self.torch = torch
         self.device = device
@@ -117,6 +118,8 @@ class Server:
         self.block = int(block)
         self.group = int(group)
         self.phenotypes = max(1, int(phenotypes))  # phenotype capacity of every plan
+        self._trace = open(trace, "a", buffering=1) if trace else None
+        self._t0 = time.perf_counter()
         self.slots: Dict[int, _Slot] = {}
         self.used = 0.0
         self.pool = cf.ThreadPoolExecutor(max_workers=factor_workers)
@@ -130,6 +133,11 @@ class Server:
         self.breakdown = {"admit_s": 0.0, "rounds_s": 0.0, "idle_s": 0.0, "rounds": 0,
                           "round_requests": 0, "factor_s": 0.0, "factors": 0,
                           "plan_create_s": 0.0, "evict_s": 0.0, "inputs_s": 0.0}
+
+    def _log(self, *fields):
+        if self._trace:
+            self._trace.write(f"{time.perf_counter() - self._t0:.4f} " +
+                              " ".join(str(f) for f in fields) + "\n")
 
     # ------------------------------------------------------------ memory
     def _plan_bytes(self, n, p):
@@ -145,6 +153,7 @@ class Server:
             if self.used + need <= self.budget:
                 break
             t = time.perf_counter()
+            self._log("evict", s.key, id(s.plan), s.n, s.p)
             self._drop_batches_with(s.plan)
             s.plan.close()
             self.breakdown["evict_s"] += time.perf_counter() - t
@@ -153,6 +162,7 @@ class Server:
 
     def _drop_batches_with(self, plan):
         for key in [k for k in self.batches if id(plan) in k]:
+            self._log("batch_close", key)
             self.batches.pop(key).close()
 
     # ------------------------------------------------------------ admission
@@ -200,6 +210,8 @@ class Server:
         act = _Active(reqs, slot, inputs, B, st, now)
         if len(reqs) > 1:
             self.breakdown["grouped"] = self.breakdown.get("grouped", 0) + len(reqs) - 1
+        self._log("admit", [r.rid for r in reqs], req.mkey, id(slot.plan), req.n, req.p, req.m,
+                  "reuse" if reuse else "new")
         if ready is not None:
             # the plan's stream reads the inputs only after their producer wrote them
             slot.plan.wait_event(ready)
@@ -231,9 +243,12 @@ class Server:
         b = self.batches.get(key)
         if b is None:
             b = gls.Batch([a.slot.plan for a in acts])
+            self._log("batch_new", key)
             self.batches[key] = b
             while len(self.batches) > 32:
-                self.batches.popitem(last=False)[1].close()
+                old_key, old = self.batches.popitem(last=False)
+                self._log("batch_close", old_key)
+                old.close()
         else:
             self.batches.move_to_end(key)
         return b
@@ -244,6 +259,8 @@ class Server:
             s0 = a.next
             k = min(self.block, a.req.m - s0)
             parts.append((a, s0, k))
+        # logged before the launch, so that a trace cut short by a failure names it
+        self._log("round", [(a.req.rid, id(a.slot.plan), s0, k, len(a.reqs)) for a, s0, k in parts])
         if self.precision == "fp64":
             for a, s0, k in parts:
                 g = len(a.reqs)
@@ -347,6 +364,9 @@ class Server:
         # a run cut off by its time cap can leave factors running on the
         # workers: they finish before any plan is destroyed
         self.pool.shutdown(wait=True)
+        if self._trace:
+            self._trace.close()
+            self._trace = None
         for b in self.batches.values():
             b.close()
         self.batches.clear()

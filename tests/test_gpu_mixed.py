@@ -128,11 +128,16 @@ def test_mixed_matches_fp64_and_is_block_independent(prec, n):
     assert relerr(B1, Bf).max() <= TOL
 
 
-def test_stream_mixed():
+@pytest.mark.parametrize("n", [500, 512])   # columns on 16-byte boundaries or not
+@pytest.mark.parametrize("flags", [0, gls.GLS_FLAG_STAGED_INPUT])
+def test_stream_mixed(n, flags):
+    """Pinned int8 input read in place by the conversion kernel (default) or
+    copied by the copy engine (GLS_FLAG_STAGED_INPUT): both equal the block
+    solve of device-resident input bit for bit."""
     import torch
-    pr = synth.problem(500, 4, 2500, 0.5, seed=14, n_markers=700)
+    pr = synth.problem(n, 4, 2500, 0.5, seed=14, n_markers=700)
     Bb, sb = run_gpu(pr, "fp16", kmax=1000)
-    with gls.Plan(500, 4, 1000, precision="fp16") as plan:
+    with gls.Plan(n, 4, 1000, precision="fp16", flags=flags) as plan:
         plan.factor(np.asfortranarray(pr["M"]), np.asfortranarray(pr["XL"]), pr["y"])
         XR = torch.from_numpy(np.ascontiguousarray(pr["XR"].T)).pin_memory()
         B = np.zeros((4, 2500), order="F")
