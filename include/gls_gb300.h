@@ -252,7 +252,9 @@ gls_status_t gls_solve_stream(gls_plan_t plan, const int8_t* XR, int64_t ldxr, i
  * paper's, which reads binary64 blocks).  Column j of XP holds ceil(n/4)
  * bytes (ldxp >= ceil(n/4)); genotype i is the 2-bit code in bits
  * 2 (i mod 4) .. 2 (i mod 4) + 1 of byte floor(i/4) of its column (the first
- * sample in the lowest bits), read as the value 0, 1, 2 or 3.  The mixed
+ * sample in the lowest bits), read as the value 0, 1, 2 or 3 (no code means
+ * "missing": 2-bit files whose codes mean something else, such as formats
+ * with a missing-call code, must be recoded first).  The mixed
  * paths of the stream convert the packed codes straight to their tensor-core
  * operand; otherwise a block is unpacked on the device into the plan's int8
  * staging and solved as an int8 block.  Either way the results equal those of

@@ -208,12 +208,16 @@ def packed_rows(n: int) -> int:
     return (int(n) + 3) // 4
 
 
-def pack_genotypes(X):
-    """Packs n x k genotype codes 0..3 (int8 or uint8, numpy or torch) four to a
+def pack_genotypes(X, allow_code3=False):
+    """Packs n x k genotype codes 0..2 (int8 or uint8, numpy or torch) four to a
     byte: column j -> ceil(n/4) bytes, genotype i in bits 2 (i mod 4) ..
     2 (i mod 4) + 1 of byte i // 4 (the layout of gls_solve_*_packed).  The
     result is column-major uint8 in the same library (and device) as X.  Works
-    on byte views: the temporaries are about n x k / 4 bytes each."""
+    on byte views: the temporaries are about n x k / 4 bytes each.
+    The library reads code 3 as the value 3; it is refused here unless
+    allow_code3, because 2-bit genotype files of other tools give the codes
+    other meanings (one of them often marks a missing call)."""
+    top = 3 if allow_code3 else 2
     n = X.shape[0]
     k = X.shape[1] if X.ndim == 2 else 1
     nb = packed_rows(n)
@@ -223,8 +227,8 @@ def pack_genotypes(X):
             if X.dtype not in (torch.int8, torch.uint8):
                 raise TypeError("packed genotype codes must be int8 or uint8")
             x = X.reshape(n, k)
-            if x.numel() and (int(x.min()) < 0 or int(x.max()) > 3):
-                raise ValueError("packed genotype codes must be in 0..3")
+            if x.numel() and (int(x.min()) < 0 or int(x.max()) > top):
+                raise ValueError(f"packed genotype codes must be in 0..{top}")
             x = x.view(torch.uint8)  # same bits for 0..3
             if n % 4:
                 pad = torch.zeros((4 * nb, k), dtype=torch.uint8, device=X.device)
@@ -242,8 +246,8 @@ def pack_genotypes(X):
     if x.dtype not in (np.int8, np.uint8):
         raise TypeError("packed genotype codes must be int8 or uint8")
     x = x.reshape(n, k, order="F")
-    if x.size and (int(x.min()) < 0 or int(x.max()) > 3):
-        raise ValueError("packed genotype codes must be in 0..3")
+    if x.size and (int(x.min()) < 0 or int(x.max()) > top):
+        raise ValueError(f"packed genotype codes must be in 0..{top}")
     x = x.view(np.uint8)
     pad = np.zeros((4 * nb, k), dtype=np.uint8)  # row-major: row 4 b + q -> q[b, q]
     pad[:n] = x
