@@ -911,6 +911,56 @@ def sub_phenotypes(args, torch, ts=(1, 4, 13), steps=3, warmup=1):
                       "reference": "FP64 oracle on the same SNP columns, per phenotype"}}
 
 
+def run_variants(torch, n=2000, p=4, h=0.5):
+    """Table 2 on GB300: the marginal cost per GLS problem of the paper's four
+    algorithms (binary64), each timed at two numbers of SNPs so that its
+    one-time setup (Cholesky, inverse) drops out, and its ratio to Alg. 5
+    beside the table's asymptotic ratio.  b_i of every algorithm is compared
+    with Alg. 5's on the SNPs both solved."""
+    import numpy as np
+    from paper_1210_7325_gb300 import gls, synth
+    sizes = {"black_box": (2, 6), "seq_gls": (64, 320), "hp_gwas": (16384, 65536),
+             "gwfgls": (4096, 16384)}
+    table2 = {"black_box": n, "seq_gls": p, "hp_gwas": 1, "gwfgls": 2}
+    mmax = max(m2 for _, m2 in sizes.values())
+    seed = synth.BASE_SEED + 5
+    dev = torch.device("cuda")
+    M = torch.from_numpy(synth.kinship_M(n, h, seed)).to(dev).t()  # symmetric: column-major view
+    XL = torch.from_numpy(np.ascontiguousarray(synth.covariates(n, p, seed).T)).to(dev).t()
+    y = torch.from_numpy(synth.phenotype(n, seed)).to(dev)
+    XR = synth.genotypes_torch(n, mmax, seed, device=dev)          # (m, n)
+    B = torch.empty((mmax, p), dtype=torch.float64, device=dev)
+    st = torch.empty(mmax, dtype=torch.int32, device=dev)
+    rows, ref = {}, None
+    with gls.Plan(n, p, 16384, precision="fp64") as plan:
+        plan.solve_variant("hp_gwas", M, XL, y, XR[:256].t(), B[:256].t(), st[:256], k=256)
+        for alg in ("hp_gwas", "black_box", "seq_gls", "gwfgls"):
+            times = []
+            for m in sizes[alg]:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                plan.solve_variant(alg, M, XL, y, XR[:m].t(), B[:m].t(), st[:m], k=m)
+                torch.cuda.synchronize()
+                times.append(time.perf_counter() - t0)
+            (m1, m2), (t1, t2) = sizes[alg], times
+            per = (t2 - t1) / (m2 - m1)
+            got = B[:sizes["black_box"][1]].cpu().numpy().T.copy()
+            if alg == "hp_gwas":
+                ref = got
+            diff = float(np.max(np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)))
+            rows[alg] = {"m": [m1, m2], "seconds": [round(t1, 4), round(t2, 4)],
+                         "per_problem_us": per * 1e6,
+                         "setup_ms": max(t1 - m1 * per, 0.0) * 1e3,
+                         "max_rel_diff_vs_hp_gwas": diff}
+    for alg, r in rows.items():
+        r["ratio_vs_hp_gwas"] = r["per_problem_us"] / rows["hp_gwas"]["per_problem_us"]
+        r["table2_ratio"] = table2[alg]
+    return {"workload": f"variants_n{n}_p{p}", "n": n, "p": p, "precision": "fp64",
+            "algorithms": rows,
+            "note": "per_problem_us = marginal cost (two sizes); Table 2 gives the asymptotic "
+                    "ratios n, p, 1, 2 for Alg. 3, 4, 5, 6"}
+
+
 def sub_batch(args, torch, name="batch48_uneven_bf16", steps=2, warmup=1):
     """The batched uneven-scan workload as a sub-object of the default line."""
     sub = argparse.Namespace(**vars(args))
@@ -1143,7 +1193,8 @@ def main():
         # each leg reports its own failure; the headline line is printed regardless
         for key, leg in (("batch", lambda: sub_batch(args, torch)),
                          ("serve", lambda: sub_serve(args, torch)),
-                         ("phenotypes", lambda: sub_phenotypes(args, torch))):
+                         ("phenotypes", lambda: sub_phenotypes(args, torch)),
+                         ("variants", lambda: run_variants(torch))):
             try:
                 torch.cuda.empty_cache()
                 line[key] = leg()

@@ -404,6 +404,41 @@ gls_status_t gls_solve_block_fp64_static(int64_t n, int32_t p, const double* Zin
 gls_status_t gls_plan_get_factor(gls_plan_t plan, double* L, int64_t ldl, double* Zinv,
                                  int64_t ldz);
 
+/*
+ * The paper's comparison algorithms for a sequence of GLS problems
+ * (Section 2), as binary64 GPU paths for the cost comparison of Table 2:
+ *   GLS_ALG_BLACK_BOX (Alg. 3): each problem solved on its own (Cholesky of M,
+ *     whitening of X_i = (X_L | x_Ri) and y, X_i^T X_i, X_i^T y, posv):
+ *     about n^3 / 3 flops per problem;
+ *   GLS_ALG_SEQ_GLS (Alg. 4): the Cholesky of M and y~ once, then per problem
+ *     the whitening of the whole X_i: about n^2 p flops per problem;
+ *   GLS_ALG_HP_GWAS (Alg. 5): this library's path (gls_factor +
+ *     gls_solve_block in blocks of max_block_snps): about n^2 per problem;
+ *   GLS_ALG_GWFGLS (Alg. 6, GenABEL's gwfgls): the explicit inverse M^{-1} and
+ *     W_L = M^{-1} X_L once, then per problem w = M^{-1} x_Ri with the full
+ *     inverse, S_i = (W_L | w)^T X_i formed without its symmetry, and an LU
+ *     solve (gesv): about 2 n^2 per problem.
+ * Triangular solves with L are applied as products with L^{-1}, which costs
+ * the same.  Every path gives b_i of Eq. 1 (B p x k, ldb >= p; snp_status k,
+ * may be NULL, 1 where S_i is singular and b_i NaN).  The plan must be a
+ * binary64 plan with one phenotype and, except for Alg. 5, p <= 8.  All
+ * pointers are device memory (M n x n, X_L n x (p-1), y n, X_R n x k int8).
+ * The call is synchronous, allocates its own workspace (cudaMalloc) and
+ * leaves the plan without a factor (gls_factor again before gls_solve_block).
+ * Errors: INVALID_ARG, NOT_SPD, OOM, CUDA.
+ */
+typedef enum {
+  GLS_ALG_BLACK_BOX = 3,
+  GLS_ALG_SEQ_GLS = 4,
+  GLS_ALG_HP_GWAS = 5,
+  GLS_ALG_GWFGLS = 6
+} gls_algorithm_t;
+
+gls_status_t gls_solve_variant(gls_plan_t plan, int32_t algorithm, const double* M, int64_t ldm,
+                               const double* XL, int64_t ldxl, const double* y,
+                               const int8_t* XR, int64_t ldxr, int64_t k, double* B,
+                               int64_t ldb, int32_t* snp_status);
+
 /* Library version as major*10000 + minor*100 + patch. */
 int32_t gls_version(void);
 

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libgls_gb300.so")
 SOURCES = ["plan.cu", "factor_fp64.cu", "trsm_fp64.cu", "solve_small.cu", "trsm_mixed.cu",
-           "static_solve.cu", "factor_tc.cu", "genotypes.cu"]
+           "static_solve.cu", "factor_tc.cu", "genotypes.cu", "variants.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

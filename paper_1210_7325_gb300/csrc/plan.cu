@@ -15,6 +15,7 @@
 #include "factor_tc.cuh"
 #include "gls_gb300.h"
 #include "mixed.cuh"
+#include "variants.cuh"
 
 namespace {
 
@@ -1550,3 +1551,139 @@ gls_status_t gls_destroy(gls_plan_t pl) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ Alg. 3, 4, 6
+namespace {
+
+// Device workspace of one gls_solve_variant call, freed when it goes out of scope.
+struct DevBuf {
+  double* p = nullptr;
+  ~DevBuf() { cudaFree(p); }
+};
+
+}  // namespace
+
+extern "C" gls_status_t gls_solve_variant(gls_plan_t pl, int32_t algorithm, const double* M,
+                                          int64_t ldm, const double* XL, int64_t ldxl,
+                                          const double* y, const int8_t* XR, int64_t ldxr,
+                                          int64_t k, double* B, int64_t ldb,
+                                          int32_t* snp_status) {
+  g_last_error.clear();
+  if (!pl) {
+    set_error("plan is NULL");
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (pl->precision != GLS_PREC_FP64 || pl->t != 1) {
+    set_error("the comparison algorithms run on binary64 plans with one phenotype");
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (algorithm != GLS_ALG_BLACK_BOX && algorithm != GLS_ALG_SEQ_GLS &&
+      algorithm != GLS_ALG_HP_GWAS && algorithm != GLS_ALG_GWFGLS) {
+    set_error("unknown algorithm %d", algorithm);
+    return GLS_ERR_INVALID_ARG;
+  }
+  const int64_t n = pl->n, npad = pl->npad;
+  const int p = pl->p, q = p - 1;
+  if (algorithm != GLS_ALG_HP_GWAS && p > gls::kVarMaxP) {
+    set_error("the comparison algorithms take p <= %d", gls::kVarMaxP);
+    return GLS_ERR_INVALID_ARG;
+  }
+  if (k < 0 || !M || !y || (q > 0 && !XL) || (k > 0 && (!XR || !B)) || ldm < n ||
+      (q > 0 && ldxl < n) || ldxr < n || ldb < p) {
+    set_error("bad size, pointer or leading dimension");
+    return GLS_ERR_INVALID_ARG;
+  }
+  DeviceGuard guard(pl->device);
+  for (const void* ptr : {(const void*)M, (const void*)XL, (const void*)y, (const void*)XR,
+                          (const void*)B, (const void*)snp_status})
+    if (ptr && classify(ptr) != Mem::Device) {
+      set_error("the comparison algorithms take device buffers only");
+      return GLS_ERR_INVALID_ARG;
+    }
+  if (k == 0) return GLS_OK;
+  if (algorithm == GLS_ALG_HP_GWAS) {  // the library's own path, block by block
+    GLS_TRY(gls_factor(pl, M, ldm, XL, ldxl, y, nullptr));
+    for (int64_t j0 = 0; j0 < k; j0 += pl->kmax) {
+      const int64_t kb = std::min(pl->kmax, k - j0);
+      GLS_TRY(gls_solve_block(pl, XR + j0 * ldxr, ldxr, kb, B + j0 * ldb, ldb,
+                              snp_status ? snp_status + j0 : nullptr));
+    }
+    return gls_synchronize(pl);
+  }
+  cudaStream_t st = pl->stream;
+  pl->factored = pl->has_factor = false;  // A and Z are overwritten below
+  GLS_CUDA(cudaMemsetAsync(pl->flags, 0, sizeof(int) * gls::kFlagCount, st));
+  auto factor = [&]() -> gls_status_t {
+    GLS_CUDA(copy2d(pl->A, npad * sizeof(double), M, ldm * sizeof(double), n * sizeof(double), n,
+                    cudaMemcpyDeviceToDevice, st));
+    gls::launch_pad_lower(pl->A, npad, n, npad, st);
+    gls::launch_identity(pl->Z, npad, npad, st);
+    GLS_CUDA(gls::potrf_trtri_fp64(pl->A, pl->Z, npad, npad, pl->flags, st));
+    return GLS_OK;
+  };
+  auto alloc = [&](DevBuf& b, size_t count) -> gls_status_t {
+    return dev_alloc(&b.p, count);
+  };
+  DevBuf R, Ws, yt, Mi, WL, F, bT, P;
+  if (algorithm == GLS_ALG_BLACK_BOX) {
+    // every problem from scratch: potrf of M, [X_L | x_j | y] whitened, syrk, gemv, posv
+    GLS_TRY(alloc(R, (size_t)npad * (p + 1)));
+    GLS_TRY(alloc(Ws, (size_t)npad * (p + 1)));
+    for (int64_t j = 0; j < k; ++j) {
+      GLS_TRY(factor());
+      gls::launch_variant_rhs(XL, ldxl, y, XR, ldxr, j, 1, n, npad, p, 0, R.p, npad, st);
+      gls::launch_whiten(pl->Z, npad, n, npad, R.p, npad, p + 1, Ws.p, npad, pl->flags, st);
+      gls::launch_gram_posv(Ws.p, npad, n, p, 0, 1, Ws.p + (int64_t)p * npad, gls::kTauFP64,
+                            B + j * ldb, ldb, snp_status ? snp_status + j : nullptr, st);
+      GLS_CUDA(cudaGetLastError());
+    }
+  } else if (algorithm == GLS_ALG_SEQ_GLS) {
+    // potrf and y~ once; per problem the whole X_i = [X_L | x_j] whitened
+    const int g = std::max(1, gls::kMaxP / p);  // problems per whitening launch
+    GLS_TRY(alloc(R, (size_t)npad * p * g));
+    GLS_TRY(alloc(Ws, (size_t)npad * p * g));
+    GLS_TRY(alloc(yt, (size_t)npad));
+    GLS_TRY(factor());
+    gls::launch_whiten(pl->Z, npad, n, npad, y, n, 1, yt.p, npad, pl->flags, st);
+    for (int64_t j0 = 0; j0 < k; j0 += g) {
+      const int gg = (int)std::min<int64_t>(g, k - j0);
+      gls::launch_variant_rhs(XL, ldxl, y, XR, ldxr, j0, gg, n, npad, p, 1, R.p, npad, st);
+      gls::launch_whiten(pl->Z, npad, n, npad, R.p, npad, p * gg, Ws.p, npad, pl->flags, st);
+      gls::launch_gram_posv(Ws.p, npad, n, p, p, gg, yt.p, gls::kTauFP64, B + j0 * ldb, ldb,
+                            snp_status ? snp_status + j0 : nullptr, st);
+      GLS_CUDA(cudaGetLastError());
+    }
+  } else {  // GLS_ALG_GWFGLS
+    // M^{-1} = Z^T Z and W_L = M^{-1} X_L once; per problem w = M^{-1} x_j, the
+    // unsymmetric S = (W_L | w)^T (X_L | x_j), r = (W_L | w)^T y, gesv
+    const int64_t kb_max = std::min<int64_t>(k, 16384);
+    const int nI = (int)gls::ceil_div(n, 64);
+    GLS_TRY(alloc(Mi, (size_t)npad * n));
+    GLS_TRY(alloc(WL, (size_t)npad * std::max(q, 1)));
+    GLS_TRY(alloc(F, (size_t)std::max(q * q, 1)));
+    GLS_TRY(alloc(bT, (size_t)std::max(q, 1)));
+    GLS_TRY(alloc(P, (size_t)nI * (2 * q + 2) * kb_max));
+    GLS_TRY(factor());
+    gls::launch_gemm_tn(pl->Z, npad, pl->Z, npad, Mi.p, npad, n, n, npad, st);
+    if (q > 0) {
+      gls::launch_gemm_tn(Mi.p, npad, XL, ldxl, WL.p, npad, n, q, n, st);
+      gls::launch_gemm_tn(WL.p, npad, XL, ldxl, F.p, q, q, q, n, st);
+      gls::launch_gemm_tn(WL.p, npad, y, n, bT.p, q, q, 1, n, st);
+    }
+    for (int64_t j0 = 0; j0 < k; j0 += kb_max) {
+      const int64_t kb = std::min(kb_max, k - j0);
+      gls::launch_dense_gram(Mi.p, npad, n, XR + j0 * ldxr, ldxr, kb, XL, ldxl, WL.p, npad, y,
+                             q, P.p, kb, st);
+      gls::launch_gesv(P.p, kb, nI, q, kb, F.p, std::max(q, 1), bT.p, gls::kTauFP64,
+                       B + j0 * ldb, ldb, snp_status ? snp_status + j0 : nullptr, st);
+      GLS_CUDA(cudaGetLastError());
+    }
+  }
+  int hf[gls::kFlagCount];
+  GLS_TRY(check_flags(pl, hf));
+  if (hf[gls::kFlagPotrf] != 0) {
+    set_error("M is not positive definite (pivot %d)", hf[gls::kFlagPotrf]);
+    return GLS_ERR_NOT_SPD;
+  }
+  return GLS_OK;
+}

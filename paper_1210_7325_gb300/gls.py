@@ -30,6 +30,8 @@ GLS_FLAG_FACTOR_NATIVE = 2
 GLS_FLAG_FACTOR_TENSOR = 4
 GLS_FLAG_EAGER = 8
 GLS_FLAG_STAGED_INPUT = 16
+# the paper's algorithms for a sequence of GLS problems (gls_solve_variant)
+ALGORITHMS = {"black_box": 3, "seq_gls": 4, "hp_gwas": 5, "gwfgls": 6}
 
 
 class GlsError(RuntimeError):
@@ -134,6 +136,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.gls_plan_stats.restype = i32
     lib.gls_plan_get_factor.argtypes = [vp, vp, i64, vp, i64]
     lib.gls_plan_get_factor.restype = i32
+    lib.gls_solve_variant.argtypes = [vp, i32, vp, i64, vp, i64, vp, vp, i64, i64, vp, i64, vp]
+    lib.gls_solve_variant.restype = i32
     _lib = lib
     return lib
 
@@ -361,6 +365,22 @@ class Plan:
             m = XP.shape[1]
         _check(lib.gls_solve_stream_packed(self._h, px, ldx, int(m), pb, ldb, _ptr(status)),
                "gls_solve_stream_packed")
+
+    def solve_variant(self, algorithm, M, XL, y, XR, B, status=None, k=None):
+        """One of the paper's algorithms ("black_box" Alg. 3, "seq_gls" Alg. 4,
+        "hp_gwas" Alg. 5, "gwfgls" Alg. 6) on device buffers: b_i of the k
+        SNP columns of XR into B (p x k).  Leaves the plan without a factor."""
+        lib = load()
+        alg = ALGORITHMS[algorithm] if isinstance(algorithm, str) else int(algorithm)
+        pm, ldm = _colmajor(M, self.n, 8, "M")
+        pl_, ldl = _colmajor(XL, self.n, 8, "XL")
+        py, _ = _colmajor(y, self.n, 8, "y")
+        px, ldx = _colmajor(XR, self.n, 1, "XR")
+        pb, ldb = _colmajor(B, self.p, 8, "B")
+        if k is None:
+            k = XR.shape[1] if XR.ndim == 2 else 1
+        _check(lib.gls_solve_variant(self._h, alg, pm, ldm, pl_, ldl, py, px, ldx, int(k), pb,
+                                     ldb, _ptr(status)), "gls_solve_variant")
 
     def get_factor(self, L=None, Zinv=None):
         """Copies L and L^{-1} (n x n column-major, host or device) of the last factor."""
