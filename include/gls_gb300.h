@@ -423,8 +423,9 @@ gls_status_t gls_plan_get_factor(gls_plan_t plan, double* L, int64_t ldl, double
  * may be NULL, 1 where S_i is singular and b_i NaN).  The plan must be a
  * binary64 plan with one phenotype and, except for Alg. 5, p <= 8.  All
  * pointers are device memory (M n x n, X_L n x (p-1), y n, X_R n x k int8).
- * The call is synchronous, allocates its own workspace (cudaMalloc) and
- * leaves the plan without a factor (gls_factor again before gls_solve_block).
+ * The call is synchronous and allocates its own workspace (cudaMalloc).
+ * Alg. 3, 4 and 6 overwrite the plan's factor and leave it without one
+ * (gls_factor again before gls_solve_block); Alg. 5 leaves its factor.
  * Errors: INVALID_ARG, NOT_SPD, OOM, CUDA.
  */
 typedef enum {

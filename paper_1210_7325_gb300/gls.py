@@ -369,7 +369,8 @@ class Plan:
     def solve_variant(self, algorithm, M, XL, y, XR, B, status=None, k=None):
         """One of the paper's algorithms ("black_box" Alg. 3, "seq_gls" Alg. 4,
         "hp_gwas" Alg. 5, "gwfgls" Alg. 6) on device buffers: b_i of the k
-        SNP columns of XR into B (p x k).  Leaves the plan without a factor."""
+        SNP columns of XR into B (p x k).  The comparison algorithms leave the
+        plan without a factor; "hp_gwas" leaves its factor in place."""
         lib = load()
         alg = ALGORITHMS[algorithm] if isinstance(algorithm, str) else int(algorithm)
         pm, ldm = _colmajor(M, self.n, 8, "M")

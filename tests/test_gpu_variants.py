@@ -29,9 +29,10 @@ def run_variant(pr, alg, kmax=None):
     st = torch.full((k,), -1, dtype=torch.int32, device="cuda")
     with gls.Plan(n, p, kmax or k, precision="fp64") as plan:
         plan.solve_variant(alg, M, XL, y, XR.t(), B.t(), st, k=k)
-        with pytest.raises(gls.GlsError) as ei:   # the variant left no factor behind
-            plan.solve_block(XR.t(), B.t(), st, k=min(k, kmax or k))
-        assert ei.value.status == 6
+        if alg != "hp_gwas":  # the comparison paths leave no factor behind
+            with pytest.raises(gls.GlsError) as ei:
+                plan.solve_block(XR.t(), B.t(), st, k=min(k, kmax or k))
+            assert ei.value.status == 6
     return B.cpu().numpy().T, st.cpu().numpy()
 
 
