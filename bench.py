@@ -961,6 +961,87 @@ def run_variants(torch, n=2000, p=4, h=0.5):
                     "ratios n, p, 1, 2 for Alg. 3, 4, 5, 6"}
 
 
+FILE_WORKLOADS = {
+    # the motivating scan's size (n = 1500, p = 4, binary64) at the paper's out-of-core scale
+    "file_n1500_p4_m10000000_fp64": dict(n=1500, p=4, m=10_000_000, h=0.5, precision="fp64",
+                                         block=65536, seed_offset=1),
+}
+
+
+def run_file_workload(args, fw, torch):
+    """Disk tier of Alg. 8: the genotypes (int8, or 2-bit with --packed) are
+    written to a file, then gls_factor + gls_solve_file stream them back through
+    the pinned ring, timed end to end.  The same plan's rate on the same
+    genotypes held in HBM (gls_solve_stream on device memory) is the reference
+    the file rate is compared with.  Reads after the write may be served by the
+    page cache; the line reports the read rate the ring sustained."""
+    import tempfile
+
+    import numpy as np
+    from paper_1210_7325_gb300 import gls, synth
+    n, p, m, prec, kmax = fw["n"], fw["p"], fw["m"], fw["precision"], fw["block"]
+    seed = synth.BASE_SEED + fw["seed_offset"]
+    width = gls.packed_rows(n) if args.packed else n
+    d = args.file_dir or tempfile.gettempdir()
+    path = os.path.join(d, f"gls_genotypes_n{n}_m{m}_{'2bit' if args.packed else 'int8'}.bin")
+    dev = torch.device("cuda")
+    XRd = synth.genotypes_torch(n, m, seed, device="cuda")             # (m, n) int8 in HBM
+    t0 = time.perf_counter()
+    with open(path, "wb") as f:
+        for s0 in range(0, m, 1 << 20):
+            blk = XRd[s0:s0 + (1 << 20)]
+            if args.packed:
+                blk = gls.pack_genotypes(blk.t()).t()
+            f.write(blk.contiguous().cpu().numpy().tobytes())
+    t_write = time.perf_counter() - t0
+    M = synth.kinship_M(n, fw["h"], seed)
+    XL = np.asfortranarray(synth.covariates(n, p, seed))
+    y = synth.phenotype(n, seed)
+    Bh = torch.empty((m, p), dtype=torch.float64, pin_memory=True)
+    sh = torch.empty(m, dtype=torch.int32, pin_memory=True)
+    plan = gls.Plan(n, p, kmax, precision=prec, flags=launch_flags(args, gls))
+    Mf = np.asfortranarray(M)
+    # in HBM: the same stream on device-resident genotypes (one warm pass)
+    plan.factor(Mf, XL, y)
+    plan.solve_stream(XRd.t(), Bh.t(), sh, m=min(m, 4 * kmax))
+    t0 = time.perf_counter()
+    plan.factor(Mf, XL, y)
+    plan.solve_stream(XRd.t(), Bh.t(), sh, m=m)
+    t_hbm = time.perf_counter() - t0
+    B_hbm = Bh[:: max(1, m // 4096)].clone()
+    del XRd
+    torch.cuda.empty_cache()
+    plan.set_timing(True)
+    t0 = time.perf_counter()
+    plan.factor(Mf, XL, y)
+    plan.solve_file(path, m, Bh.t(), sh, packed=args.packed)
+    t_file = time.perf_counter() - t0
+    st = plan.stats()
+    plan.close()
+    same = bool(torch.equal(Bh[:: max(1, m // 4096)], B_hbm))
+    try:
+        os.unlink(path)
+    except OSError:
+        pass
+    return {"metric": METRIC, "value": m / t_file, "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": t_file * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"bf16": "bf16", "fp16": "f16", "fp64": "f64"}[prec],
+            "data": "synthetic genotypes written to a file, then streamed back",
+            "config": {"workload": args.workload, "n": n, "p": p, "m": m, "block_snps": kmax,
+                       "file_format": "2-bit packed" if args.packed else "int8",
+                       "file_bytes": width * m, "file_dir": d, "parallelism": "replicas1"},
+            "in_hbm": {"value": m / t_hbm, "unit": UNIT, "seconds": t_hbm},
+            "file_vs_in_hbm": t_hbm / t_file,
+            "write_s": t_write, "read_gbps_overall": width * m / t_file / 1e9,
+            "file_results_equal_in_hbm_results": same,
+            "phase_ms": {"factor": st["factor_ms"], "solve_kernels": st["trsm_ms"] + st["solve_ms"],
+                         "h2d": st["h2d_ms"]},
+            "e2e": {"value": m / t_file, "unit": UNIT,
+                    "h2d_bytes_per_step": width * m + n * n * 8 + n * p * 8,
+                    "d2h_bytes_per_step": m * (p * 8 + 4)}}
+
+
 def sub_batch(args, torch, name="batch48_uneven_bf16", steps=2, warmup=1):
     """The batched uneven-scan workload as a sub-object of the default line."""
     sub = argparse.Namespace(**vars(args))
@@ -1035,8 +1116,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload",
-                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(SERVE_WORKLOADS),
+                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(SERVE_WORKLOADS)
+                    + sorted(FILE_WORKLOADS),
                     default=DEFAULT_WORKLOAD)
+    ap.add_argument("--file-dir", default=None,
+                    help="file workloads: directory of the genotype file (default: the temp dir)")
+    ap.add_argument("--packed", action="store_true",
+                    help="file workloads: write and read 2-bit packed genotypes")
     ap.add_argument("--requests", type=int, default=0, help="serving: number of requests")
     ap.add_argument("--time-cap", type=float, default=0.0, help="serving: wall-time cap (s)")
     ap.add_argument("--factor-only", action="store_true",
@@ -1060,6 +1146,13 @@ def main():
         from paper_1210_7325_gb300 import build as gbuild
         gbuild.build()
         print(json.dumps(run_serve_workload(args, SERVE_WORKLOADS[args.workload], torch)),
+              flush=True)
+        return
+    if args.workload in FILE_WORKLOADS:
+        import torch
+        from paper_1210_7325_gb300 import build as gbuild
+        gbuild.build()
+        print(json.dumps(run_file_workload(args, FILE_WORKLOADS[args.workload], torch)),
               flush=True)
         return
     if args.workload in BATCH_WORKLOADS:

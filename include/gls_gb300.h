@@ -62,7 +62,8 @@ typedef enum {
   GLS_ERR_TIMEOUT = 5,          /* a bounded device wait gave up; the result is not valid   */
   GLS_ERR_STATE = 6,            /* call out of order (e.g. solve before factor)             */
   GLS_ERR_UNSUPPORTED = 7,      /* precision or device not supported by this build          */
-  GLS_ERR_COVARIATES_SINGULAR = 8 /* X~_L^T X~_L not SPD; *info = 1-based failing pivot     */
+  GLS_ERR_COVARIATES_SINGULAR = 8, /* X~_L^T X~_L not SPD; *info = 1-based failing pivot    */
+  GLS_ERR_IO = 9                /* a genotype file could not be opened or read              */
 } gls_status_t;
 
 typedef enum {
@@ -269,6 +270,25 @@ gls_status_t gls_solve_block_packed(gls_plan_t plan, const uint8_t* XP, int64_t 
                                     double* B, int64_t ldb, int32_t* snp_status);
 gls_status_t gls_solve_stream_packed(gls_plan_t plan, const uint8_t* XP, int64_t ldxp,
                                      int64_t m, double* B, int64_t ldb, int32_t* snp_status);
+
+/*
+ * The disk tier of Alg. 8 (ooc-hp-gwas): the SNP stream read from a file.
+ * The file holds m genotype columns from byte `offset` on, column j at
+ * offset + j ldx: int8 codes (packed == 0, ldx >= n) or the 2-bit layout of
+ * gls_solve_block_packed (packed != 0, ldx >= ceil(n/4)).  Blocks follow the
+ * schedule of gls_solve_stream (a short first block, then doubling, Section
+ * 4.3).  A background thread reads them with parallel pread calls into a ring
+ * of three pinned slots, up to two blocks ahead of the GPU (the async_read of
+ * Alg. 8), and the GPU takes each block from its slot as from pinned input to
+ * gls_solve_stream.  The slots (3 x ldx x max_block_snps bytes of pinned host
+ * memory) stay with the plan for later calls.  B and snp_status as for
+ * gls_solve_stream.  Synchronous.  Errors: GLS_ERR_IO when the file cannot be
+ * opened, is shorter than offset + m ldx bytes, or a read fails; otherwise
+ * as for gls_solve_stream.
+ */
+gls_status_t gls_solve_file(gls_plan_t plan, const char* path, int64_t offset, int32_t packed,
+                            int64_t ldx, int64_t m, double* B, int64_t ldb,
+                            int32_t* snp_status);
 
 /*
  * Batched uneven scans: several independent sequences (each its own plan, with

@@ -1,12 +1,19 @@
 // plan.cu -- the C ABI of include/gls_gb300.h: plan objects, the setup phase,
 // one block of the SNP loop, and the double-buffered stream of Alg. 8.
+#include <errno.h>
+#include <fcntl.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
+#include <sys/stat.h>
+#include <unistd.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -116,6 +123,10 @@ struct gls_plan {
   uint8_t* h_xp[2]{};       // pinned staging for pageable packed inputs
   double* h_b[2]{};
   int32_t* h_s[2]{};
+  uint8_t* h_ring[3]{};     // pinned slots of the file reader (first gls_solve_file)
+  uint8_t* d_ring[3]{};     // their device addresses
+  size_t ring_bytes = 0;
+  cudaEvent_t ev_ring[3]{};
   gls::MixedState* mixed = nullptr;
   bool tc = false;          // factor on the tensor cores (exact slices)
   gls::TcFactor* tcf = nullptr;
@@ -473,6 +484,10 @@ void free_plan(gls_plan* pl) {
     if (pl->ev_stored[s]) cudaEventDestroy(pl->ev_stored[s]);
     if (pl->ev_staged[s]) cudaEventDestroy(pl->ev_staged[s]);
   }
+  for (int s = 0; s < 3; ++s) {
+    cudaFreeHost(pl->h_ring[s]);
+    if (pl->ev_ring[s]) cudaEventDestroy(pl->ev_ring[s]);
+  }
   for (gls_plan::Slot* sl :
        {&pl->t_trsm, &pl->t_convert, &pl->t_solve, &pl->t_factor, &pl->t_h2d, &pl->t_d2h})
     for (auto& pr : sl->pending) {
@@ -646,6 +661,7 @@ const char* gls_status_string(gls_status_t s) {
     case GLS_ERR_STATE: return "GLS_ERR_STATE";
     case GLS_ERR_UNSUPPORTED: return "GLS_ERR_UNSUPPORTED";
     case GLS_ERR_COVARIATES_SINGULAR: return "GLS_ERR_COVARIATES_SINGULAR";
+    case GLS_ERR_IO: return "GLS_ERR_IO";
   }
   return "GLS_ERR_UNKNOWN";
 }
@@ -999,16 +1015,128 @@ gls_status_t packed_staging(gls_plan* pl, bool pinned) {
   return GLS_OK;
 }
 
+// Block schedule of a stream of m SNPs: a short first block (its load is not
+// overlapped), then doubling up to max_block_snps (Section 4.3).
+std::vector<std::pair<int64_t, int64_t>> block_schedule(int64_t kmax, int64_t m) {
+  std::vector<std::pair<int64_t, int64_t>> blocks;
+  int64_t kb = std::min<int64_t>(kmax, std::max<int64_t>(256, kmax / 8));
+  for (int64_t s0 = 0; s0 < m;) {
+    const int64_t kk = std::min<int64_t>(kb, m - s0);
+    blocks.emplace_back(s0, kk);
+    s0 += kk;
+    kb = std::min<int64_t>(kmax, kb * 2);
+  }
+  return blocks;
+}
+
+// The disk tier of Alg. 8: genotype blocks are read from a file into a ring of
+// pinned host slots by a background thread, ahead of the GPU (the paper's
+// async_read).  Block j goes to slot j mod kSlots once the GPU has finished
+// reading the block that used that slot before: the compute thread records an
+// event after that read and the reader waits for it.  Each block is read by up
+// to 8 parallel pread calls (one per 64 MiB) so that page-cache and NVMe reads
+// reach their bandwidth.
+struct FileRing {
+  static constexpr int kSlots = 3;
+  int fd = -1;
+  int64_t offset = 0, ldx = 0;
+  std::vector<std::pair<int64_t, int64_t>> blocks;  // (first SNP, SNPs)
+  uint8_t* slot[kSlots]{};                           // pinned, ldx x kmax bytes each
+  cudaEvent_t released[kSlots]{};                    // the GPU has read the slot's block
+  std::mutex mu;
+  std::condition_variable cv;
+  int64_t filled = -1;    // last block read into its slot
+  int64_t recorded = -1;  // last block whose release event has been recorded
+  bool stop = false;
+  int err = 0;            // errno of a failed or short read
+  std::thread th;
+
+  void run() {
+    for (size_t jb = 0; jb < blocks.size(); ++jb) {
+      const int s = (int)(jb % kSlots);
+      if (jb >= (size_t)kSlots) {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return stop || recorded >= (int64_t)jb - kSlots; });
+        if (stop) return;
+        lk.unlock();
+        if (cudaEventSynchronize(released[s]) != cudaSuccess) {
+          cudaGetLastError();
+          fail(EIO);
+          return;
+        }
+      }
+      const int64_t bytes = blocks[jb].second * ldx;
+      const off_t at = (off_t)(offset + blocks[jb].first * ldx);
+      const int parts = (int)std::max<int64_t>(1, std::min<int64_t>(8, bytes >> 26));
+      std::vector<std::thread> rd;
+      std::atomic<int> rerr{0};
+      for (int t = 0; t < parts; ++t) {
+        const int64_t b0 = bytes * t / parts, b1 = bytes * (t + 1) / parts;
+        rd.emplace_back([&, b0, b1]() {
+          int64_t done = b0;
+          while (done < b1) {
+            const ssize_t r = pread(fd, slot[s] + done, (size_t)(b1 - done), at + done);
+            if (r <= 0) {
+              rerr = r == 0 ? EIO : errno;
+              return;
+            }
+            done += r;
+          }
+        });
+      }
+      for (auto& t : rd) t.join();
+      if (rerr) {
+        fail(rerr);
+        return;
+      }
+      std::lock_guard<std::mutex> lk(mu);
+      filled = (int64_t)jb;
+      cv.notify_all();
+    }
+  }
+  void fail(int e) {
+    std::lock_guard<std::mutex> lk(mu);
+    err = e;
+    cv.notify_all();
+  }
+  // Waits until block jb is in its slot; false on a read error.
+  bool wait_filled(size_t jb) {
+    std::unique_lock<std::mutex> lk(mu);
+    cv.wait(lk, [&] { return err != 0 || filled >= (int64_t)jb; });
+    return err == 0;
+  }
+  // After the GPU work that reads block jb has been enqueued on `st`.
+  cudaError_t release(size_t jb, cudaStream_t st) {
+    const cudaError_t e = cudaEventRecord(released[jb % kSlots], st);
+    std::lock_guard<std::mutex> lk(mu);
+    recorded = (int64_t)jb;
+    cv.notify_all();
+    return e;
+  }
+  void finish() {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      stop = true;
+      cv.notify_all();
+    }
+    if (th.joinable()) th.join();
+  }
+};
+
 // The SNP stream of Alg. 8 for int8 (packed = false, ldx >= n) or 2-bit
-// packed (packed = true, ldx >= ceil(n/4)) genotype columns X.
+// packed (packed = true, ldx >= ceil(n/4)) genotype columns X, or, with a
+// ring, for the blocks the ring reads from a file (X unused; its slots are
+// pinned host memory).
 gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packed, int64_t m,
-                         double* B, int64_t ldb, int32_t* snp_status) {
+                         double* B, int64_t ldb, int32_t* snp_status,
+                         FileRing* ring = nullptr) {
   DeviceGuard guard(pl->device);
   const int64_t n = pl->n, kmax = pl->kmax;
   const int p = pl->p, t = pl->t_active;  // b_ij of SNP i, phenotype j: column i t + j of B
   const int64_t width = packed ? gls::ceil_div(n, 4) : n;  // bytes per column
   const void* Xdev = nullptr;
-  const Mem mx = classify(X, &Xdev), mb = classify(B);
+  const Mem mx = ring ? Mem::Pinned : classify(X, &Xdev), mb = classify(B);
+  if (ring) Xdev = pl->d_ring[0];
   const Mem ms = snp_status ? classify(snp_status) : Mem::Device;
   // Mixed plans read pinned int8 blocks in place: the conversion kernel loads
   // them over the host link through the mapping's device address, and the
@@ -1017,18 +1145,16 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
                       !(pl->desc.flags & GLS_FLAG_STAGED_INPUT);
   const bool staged = (mx != Mem::Device) && !direct;
 
-  // Block schedule: a short first block (its load is not overlapped), then
-  // doubling up to max_block_snps (Section 4.3).
-  std::vector<std::pair<int64_t, int64_t>> blocks;
-  {
-    int64_t kb = std::min<int64_t>(kmax, std::max<int64_t>(256, kmax / 8));
-    for (int64_t s0 = 0; s0 < m;) {
-      const int64_t kk = std::min<int64_t>(kb, m - s0);
-      blocks.emplace_back(s0, kk);
-      s0 += kk;
-      kb = std::min<int64_t>(kmax, kb * 2);
-    }
-  }
+  const std::vector<std::pair<int64_t, int64_t>> blocks =
+      ring ? ring->blocks : block_schedule(kmax, m);
+  // host and device addresses of block jb's first column (ld = ldx)
+  auto src_host = [&](size_t jb) -> const uint8_t* {
+    return ring ? ring->slot[jb % FileRing::kSlots] : X + blocks[jb].first * ldx;
+  };
+  auto src_dev = [&](size_t jb) -> const uint8_t* {
+    return ring ? pl->d_ring[jb % FileRing::kSlots]
+                : reinterpret_cast<const uint8_t*>(Xdev) + blocks[jb].first * ldx;
+  };
   const bool pageable_in = (mx == Mem::Pageable);
   const bool out_b_host = (mb != Mem::Device);
   const bool out_s_host = snp_status && (ms != Mem::Device);
@@ -1077,9 +1203,14 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
       return copy2d(q.dst, q.width, q.src, q.ldsrc, q.width, q.cols, cudaMemcpyHostToDevice,
                     q.st);
     };
+    if (ring && !ring->wait_filled(jb)) {
+      set_error("reading genotype block %zu from the file failed: %s", jb, strerror(ring->err));
+      return GLS_ERR_IO;
+    }
     if (!pageable_in) {
-      Copy q{dev_in(s), X + s0 * ldx, (size_t)ldx, (size_t)width, (size_t)kb, pl->h2d};
+      Copy q{dev_in(s), src_host(jb), (size_t)ldx, (size_t)width, (size_t)kb, pl->h2d};
       GLS_CUDA(timed_copy(pl, &pl->t_h2d, pl->h2d, (size_t)width * kb, issue, &q));
+      if (ring) GLS_CUDA(ring->release(jb, pl->h2d));
     } else {
       GLS_CUDA(cudaEventSynchronize(pl->ev_staged[s]));  // pinned staging s is free
       for (int64_t c = 0; c < kb; ++c)
@@ -1109,6 +1240,10 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
     const int s = (int)(jb % 2);
     const int64_t s0 = blocks[jb].first, kb = blocks[jb].second;
     if (staged && jb + 1 < blocks.size()) GLS_TRY(issue_load(jb + 1));
+    if (direct && ring && !ring->wait_filled(jb)) {
+      set_error("reading genotype block %zu from the file failed: %s", jb, strerror(ring->err));
+      return GLS_ERR_IO;
+    }
     if (staged) GLS_CUDA(cudaStreamWaitEvent(cs, pl->ev_loaded[s], 0));
     GLS_CUDA(cudaStreamWaitEvent(cs, pl->ev_stored[s], 0));  // output slot s copied out
     double* bout = out_b_host ? pl->bdev[s] : B + s0 * t * ldb;
@@ -1136,7 +1271,8 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
         xin = pl->xr[s];
         ldin = n;
       } else if (mx == Mem::Device || direct) {
-        xin = reinterpret_cast<const int8_t*>(direct ? Xdev : X) + s0 * ldx;
+        xin = direct ? reinterpret_cast<const int8_t*>(src_dev(jb))
+                     : reinterpret_cast<const int8_t*>(X) + s0 * ldx;
         ldin = ldx;
       } else {
         xin = pl->xr[s];
@@ -1148,6 +1284,7 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
                        [&]() { return run_block(pl, xin, ldin, kb, bout, ldout, sout); }));
     }
     GLS_CUDA(cudaEventRecord(pl->ev_computed[s], cs));
+    if (direct && ring) GLS_CUDA(ring->release(jb, cs));  // the conversion has read the slot
     if (out_b_host || out_s_host) {
       GLS_CUDA(cudaStreamWaitEvent(pl->d2h, pl->ev_computed[s], 0));
       if (out_b_host) {
@@ -1228,6 +1365,68 @@ gls_status_t gls_solve_stream_packed(gls_plan_t pl, const uint8_t* XP, int64_t l
                       "gls_solve_stream_packed"));
   if (m == 0) return GLS_OK;
   return stream_impl(pl, XP, ldxp, true, m, B, ldb, snp_status);
+}
+
+gls_status_t gls_solve_file(gls_plan_t pl, const char* path, int64_t offset, int32_t packed,
+                            int64_t ldx, int64_t m, double* B, int64_t ldb,
+                            int32_t* snp_status) {
+  g_last_error.clear();
+  if (!path || offset < 0) {
+    set_error("path is NULL or offset < 0");
+    return GLS_ERR_INVALID_ARG;
+  }
+  GLS_TRY(stream_args(pl, path, ldx, pl ? (packed ? gls::ceil_div(pl->n, 4) : pl->n) : 0, m, B,
+                      ldb, "gls_solve_file"));
+  if (m == 0) return GLS_OK;
+  DeviceGuard guard(pl->device);
+  // the ring's pinned slots and their events stay with the plan for later calls
+  const size_t need = (size_t)ldx * (size_t)pl->kmax;
+  if (pl->ring_bytes < need) {
+    for (int s = 0; s < FileRing::kSlots; ++s) {
+      cudaFreeHost(pl->h_ring[s]);
+      pl->h_ring[s] = nullptr;
+      pl->d_ring[s] = nullptr;
+    }
+    pl->ring_bytes = 0;
+    for (int s = 0; s < FileRing::kSlots; ++s) {
+      GLS_TRY(host_alloc(&pl->h_ring[s], need));
+      GLS_CUDA(cudaHostGetDevicePointer((void**)&pl->d_ring[s], pl->h_ring[s], 0));
+    }
+    pl->ring_bytes = need;
+  }
+  for (int s = 0; s < FileRing::kSlots; ++s)
+    if (!pl->ev_ring[s]) GLS_CUDA(cudaEventCreateWithFlags(&pl->ev_ring[s], cudaEventDisableTiming));
+  const int fd = open(path, O_RDONLY | O_CLOEXEC);
+  if (fd < 0) {
+    set_error("cannot open %s: %s", path, strerror(errno));
+    return GLS_ERR_IO;
+  }
+  struct stat sb;
+  if (fstat(fd, &sb) != 0 || sb.st_size < offset + m * ldx) {
+    set_error("%s holds fewer than offset + m * ldx = %lld bytes", path,
+              (long long)(offset + m * ldx));
+    close(fd);
+    return GLS_ERR_IO;
+  }
+  posix_fadvise(fd, offset, m * ldx, POSIX_FADV_SEQUENTIAL);
+  FileRing ring;
+  ring.fd = fd;
+  ring.offset = offset;
+  ring.ldx = ldx;
+  ring.blocks = block_schedule(pl->kmax, m);
+  for (int s = 0; s < FileRing::kSlots; ++s) {
+    ring.slot[s] = pl->h_ring[s];
+    ring.released[s] = pl->ev_ring[s];
+  }
+  ring.th = std::thread([&ring]() { ring.run(); });
+  gls_status_t st = stream_impl(pl, nullptr, ldx, packed != 0, m, B, ldb, snp_status, &ring);
+  ring.finish();  // also stops a reader still waiting after an early return
+  close(fd);
+  if (st == GLS_OK && ring.err) {
+    set_error("reading %s failed: %s", path, strerror(ring.err));
+    st = GLS_ERR_IO;
+  }
+  return st;
 }
 
 gls_status_t gls_solve_block_packed(gls_plan_t pl, const uint8_t* XP, int64_t ldxp, int64_t k,

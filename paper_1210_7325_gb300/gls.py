@@ -22,7 +22,7 @@ GLS_OK = 0
 STATUS_NAMES = {
     0: "GLS_OK", 1: "GLS_ERR_INVALID_ARG", 2: "GLS_ERR_NOT_SPD", 3: "GLS_ERR_OOM",
     4: "GLS_ERR_CUDA", 5: "GLS_ERR_TIMEOUT", 6: "GLS_ERR_STATE", 7: "GLS_ERR_UNSUPPORTED",
-    8: "GLS_ERR_COVARIATES_SINGULAR",
+    8: "GLS_ERR_COVARIATES_SINGULAR", 9: "GLS_ERR_IO",
 }
 PRECISIONS = {"fp64": 0, "bf16": 1, "fp16": 2}
 GLS_FLAG_NAIVE_SPLIT = 1
@@ -106,6 +106,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.gls_solve_block_packed.restype = i32
     lib.gls_solve_stream_packed.argtypes = [vp, vp, i64, i64, vp, i64, vp]
     lib.gls_solve_stream_packed.restype = i32
+    lib.gls_solve_file.argtypes = [vp, ctypes.c_char_p, i64, i32, i64, i64, vp, i64, vp]
+    lib.gls_solve_file.restype = i32
     lib.gls_synchronize.argtypes = [vp]
     lib.gls_synchronize.restype = i32
     lib.gls_plan_stream.argtypes = [vp]
@@ -346,6 +348,17 @@ class Plan:
             m = XR.shape[1]
         _check(lib.gls_solve_stream(self._h, px, ldx, int(m), pb, ldb, _ptr(status)),
                "gls_solve_stream")
+
+    def solve_file(self, path, m, B, status=None, offset=0, packed=False, ldx=None):
+        """The SNP stream read from a file (gls_solve_file): m columns of int8
+        codes (or the 2-bit packed layout) from byte `offset`, ldx bytes apart
+        (default n, or ceil(n/4) packed)."""
+        lib = load()
+        if ldx is None:
+            ldx = packed_rows(self.n) if packed else self.n
+        pb, ldb = _colmajor(B, self.p, 8, "B")
+        _check(lib.gls_solve_file(self._h, os.fsencode(path), int(offset), int(bool(packed)),
+                                  int(ldx), int(m), pb, ldb, _ptr(status)), "gls_solve_file")
 
     def solve_block_packed(self, XP, B, status=None, k=None):
         """XP: ceil(n/4) x k uint8 column-major, 2-bit codes (see pack_genotypes)."""
