@@ -712,6 +712,22 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }  // namespace
 
 // ------------------------------------------------------------------ workspace
+// Recursion depths with their own workspace for T = L21 Z11 (the side stream).
+constexpr int kMaxDepth = 24;
+
+// Slices of T's two operands at one recursion depth: L21 (rows of the node's
+// lower part) and Z11 (by columns), with their row exponents and maxima.
+struct TWork {
+  size_t capA = 0, capB = 0;  // elements per slice plane
+  uint16_t* SA = nullptr;     // kS x capA
+  uint16_t* SB = nullptr;     // kS x capB
+  int* eA = nullptr;
+  int* eB = nullptr;
+  unsigned long long* maxA = nullptr;
+  unsigned long long* maxB = nullptr;
+  int64_t rowsA = 0, rowsB = 0;
+};
+
 struct TcFactor {
   int64_t npad = 0, half = 0;
   size_t cap = 0;             // elements per slice plane of SA / SB
@@ -723,6 +739,14 @@ struct TcFactor {
   unsigned long long* maxB = nullptr;
   int num_sms = 1;
   int64_t launches = 0;       // kernels enqueued so far
+  // T = L21 Z11 of each recursion node runs on its depth's side stream, beside
+  // the trailing update and the recursion on A22, with the depth's own operand
+  // slices (one stream per depth, so that the T of a deeper node never waits
+  // behind a larger one above it)
+  cudaStream_t side[kMaxDepth]{};
+  cudaEvent_t ready[kMaxDepth]{};   // L21 of the node at this depth is formed
+  cudaEvent_t tdone[kMaxDepth]{};   // its T is formed
+  TWork tw[kMaxDepth];
 };
 
 namespace {
@@ -874,30 +898,42 @@ cudaError_t launch_gemm(TcFactor* w, const Operand& A, const Operand& B, OzParam
   } while (0)
 
 cudaError_t rec(TcFactor* w, double* A, double* Z, int64_t ld, int64_t r0, int64_t n, int* flags,
-                cudaStream_t st) {
+                cudaStream_t st, int depth) {
   if (n == 64) {
     launch_potrf_diag64(A, Z, ld, r0, flags, st);
     ++w->launches;
     return cudaGetLastError();
   }
   const int64_t n1 = 64 * ((n / 64) / 2), n2 = n - n1;
-  TC_TRY(rec(w, A, Z, ld, r0, n1, flags, st));
+  TC_TRY(rec(w, A, Z, ld, r0, n1, flags, st, depth + 1));
   double* A21 = A + (r0 + n1) + r0 * ld;
   double* A22 = A + (r0 + n1) + (r0 + n1) * ld;
   double* Z11 = Z + r0 + r0 * ld;
   double* Z21 = Z + (r0 + n1) + r0 * ld;
   double* Z22 = Z + (r0 + n1) + (r0 + n1) * ld;
+  // T = L21 Z11 needs only L21 and Z11: it runs on the side stream while this
+  // stream updates A22 and factors it; T is kept in the Z21 block (zero until
+  // Z21 = -Z22 T overwrites it), which nothing else touches before that step
+  // (a depth without its stream or workspace keeps everything on this stream)
+  const bool split_t = depth < kMaxDepth && w->side[depth] != nullptr;
+  cudaStream_t sd = split_t ? w->side[depth] : st;
   if (n <= kSmallNode) {
     const dim3 rows((unsigned)n2), cols((unsigned)n1);
     small_rows_kernel<<<rows, kSmallThreads, 0, st>>>(A21, A21, Z11, ld, (int)n1, (int)n1,
                                                       kSmL21, flags);
+    if (split_t) {
+      TC_TRY(cudaEventRecord(w->ready[depth], st));
+      TC_TRY(cudaStreamWaitEvent(sd, w->ready[depth], 0));
+    }
+    small_rows_kernel<<<rows, kSmallThreads, 0, sd>>>(A21, Z21, Z11, ld, (int)n1, (int)n1, kSmT,
+                                                      flags);
+    if (split_t) TC_TRY(cudaEventRecord(w->tdone[depth], sd));
     small_rows_kernel<<<rows, kSmallThreads, 0, st>>>(A21, A22, A21, ld, (int)n2, (int)n1,
                                                       kSmSyrk, flags);
-    small_rows_kernel<<<rows, kSmallThreads, 0, st>>>(A21, Z21, Z11, ld, (int)n1, (int)n1, kSmT,
-                                                      flags);
     w->launches += 3;
     TC_TRY(cudaGetLastError());
-    TC_TRY(rec(w, A, Z, ld, r0 + n1, n2, flags, st));
+    TC_TRY(rec(w, A, Z, ld, r0 + n1, n2, flags, st, depth + 1));
+    if (split_t) TC_TRY(cudaStreamWaitEvent(st, w->tdone[depth], 0));
     small_z21_kernel<<<cols, kSmallThreads, 0, st>>>(Z22, Z21, ld, (int)n2, flags);
     ++w->launches;
     return cudaGetLastError();
@@ -909,21 +945,44 @@ cudaError_t rec(TcFactor* w, double* A, double* Z, int64_t ld, int64_t r0, int64
                 job(Z11, ld, n1, n1, true, w->SB, w->eB, w->maxB), flags, st));
   TC_TRY(gemm(w, SA1, SB1, A21, ld, (int)n2, (int)n1, (int)n1, kKLeJ, 0, false, 0, false, 0,
               flags, st));
-  // One slicing of L21 serves both the trailing update and T = L21 Z11, which
-  // does not depend on the factor of A22 and is formed before it.  T is kept
-  // in the Z21 block (zero until Z21 = -Z22 T overwrites it below); the
-  // recursion on A22 touches only A22 and Z22.
+  if (!split_t || !w->tw[depth].SA) {
+    // in order on this stream: one slicing of L21 serves the trailing update
+    // and T, which is formed before the recursion on A22 reuses the slices
+    TC_TRY(slice2(w, job(A21, ld, n2, n1, true, w->SA, w->eA, w->maxA),
+                  job(Z11, ld, n1, n1, false, w->SB, w->eB, w->maxB), flags, st));
+    TC_TRY(gemm(w, SA1, SA1, A22, ld, (int)n2, (int)n2, (int)n1, kKFull, 0, true, 1, true, 0,
+                flags, st));
+    TC_TRY(gemm(w, SA1, SB1, Z21, ld, (int)n2, (int)n1, (int)n1, kKGeJ, 0, false, 0, false, 0,
+                flags, st));
+    TC_TRY(rec(w, A, Z, ld, r0 + n1, n2, flags, st, depth + 1));
+    const Operand SA2{w->SA, w->eA, n2, round_up(n2, kKAlign)};
+    const Operand SB2{w->SB, w->eB, n1, round_up(n2, kKAlign)};
+    TC_TRY(slice2(w, job(Z22, ld, n2, n2, true, w->SA, w->eA, w->maxA),
+                  job(Z21, ld, n1, n2, false, w->SB, w->eB, w->maxB), flags, st));
+    return gemm(w, SA2, SB2, Z21, ld, (int)n2, (int)n1, (int)n2, kKLeI, 0, true, 0, false, 0,
+                flags, st);
+  }
+  TC_TRY(cudaEventRecord(w->ready[depth], st));
+  // side stream: T = L21 Z11 (Z11 lower: column j needs k >= j) from this
+  // depth's own slices of L21 (rows) and Z11 (columns)
+  TWork& tw = w->tw[depth];
+  TC_TRY(cudaStreamWaitEvent(sd, w->ready[depth], 0));
+  TC_TRY(slice2(w, job(A21, ld, n2, n1, true, tw.SA, tw.eA, tw.maxA),
+                job(Z11, ld, n1, n1, false, tw.SB, tw.eB, tw.maxB), flags, sd));
+  const Operand TA{tw.SA, tw.eA, n2, round_up(n1, kKAlign)};
+  const Operand TB{tw.SB, tw.eB, n1, round_up(n1, kKAlign)};
+  TC_TRY(gemm(w, TA, TB, Z21, ld, (int)n2, (int)n1, (int)n1, kKGeJ, 0, false, 0, false, 0, flags,
+              sd));
+  TC_TRY(cudaEventRecord(w->tdone[depth], sd));
+  // this stream: A22 -= L21 L21^T (lower triangle)
   TC_TRY(slice2(w, job(A21, ld, n2, n1, true, w->SA, w->eA, w->maxA),
-                job(Z11, ld, n1, n1, false, w->SB, w->eB, w->maxB), flags, st));
-  // A22 -= L21 L21^T (lower triangle)
+                job(nullptr, ld, 0, 0, true, w->SB, w->eB, w->maxB), flags, st));
   TC_TRY(gemm(w, SA1, SA1, A22, ld, (int)n2, (int)n2, (int)n1, kKFull, 0, true, 1, true, 0, flags,
               st));
-  // T = L21 Z11 (Z11 lower: column j needs k >= j)
-  TC_TRY(gemm(w, SA1, SB1, Z21, ld, (int)n2, (int)n1, (int)n1, kKGeJ, 0, false, 0, false, 0,
-              flags, st));
-  TC_TRY(rec(w, A, Z, ld, r0 + n1, n2, flags, st));
+  TC_TRY(rec(w, A, Z, ld, r0 + n1, n2, flags, st, depth + 1));
   // Z21 = -Z22 T (Z22 lower: row block I needs k < (I+1) 128); T's slices are
   // taken before the product overwrites it
+  TC_TRY(cudaStreamWaitEvent(st, w->tdone[depth], 0));
   const Operand SA2{w->SA, w->eA, n2, round_up(n2, kKAlign)};
   const Operand SB2{w->SB, w->eB, n1, round_up(n2, kKAlign)};
   TC_TRY(slice2(w, job(Z22, ld, n2, n2, true, w->SA, w->eA, w->maxA),
@@ -931,6 +990,24 @@ cudaError_t rec(TcFactor* w, double* A, double* Z, int64_t ld, int64_t r0, int64
   TC_TRY(gemm(w, SA2, SB2, Z21, ld, (int)n2, (int)n1, (int)n2, kKLeI, 0, true, 0, false, 0, flags,
               st));
   return cudaSuccess;
+}
+
+// Largest operands of T = L21 Z11 at each recursion depth of an npad x npad
+// factor (nodes above kSmallNode rows only): rows x padded k of L21's and of
+// Z11's slices, and their row counts.
+void t_sizes(int64_t n, int depth, size_t capA[], size_t capB[], int64_t rowsA[],
+             int64_t rowsB[]) {
+  if (n == 64 || depth >= kMaxDepth) return;
+  const int64_t n1 = 64 * ((n / 64) / 2), n2 = n - n1;
+  if (n > kSmallNode) {
+    const size_t k = (size_t)round_up(n1, kKAlign);
+    capA[depth] = std::max(capA[depth], (size_t)n2 * k);
+    capB[depth] = std::max(capB[depth], (size_t)n1 * k);
+    rowsA[depth] = std::max(rowsA[depth], n2);
+    rowsB[depth] = std::max(rowsB[depth], n1);
+  }
+  t_sizes(n1, depth + 1, capA, capB, rowsA, rowsB);
+  t_sizes(n2, depth + 1, capA, capB, rowsA, rowsB);
 }
 
 // Rows per panel so that rows x K fits one slice plane.
@@ -943,19 +1020,40 @@ int64_t panel_rows(const TcFactor* w, int64_t K) {
 }  // namespace
 
 size_t tc_factor_bytes(int64_t npad) {
-  return 2 * (size_t)kS * plane_cap(npad) * 2 + 2 * (size_t)npad * (4 + 8);
+  size_t capA[kMaxDepth] = {}, capB[kMaxDepth] = {};
+  int64_t rowsA[kMaxDepth] = {}, rowsB[kMaxDepth] = {};
+  t_sizes(npad, 0, capA, capB, rowsA, rowsB);
+  size_t b = 2 * (size_t)kS * plane_cap(npad) * 2 + 2 * (size_t)npad * (4 + 8);
+  for (int d = 0; d < kMaxDepth; ++d)
+    b += (size_t)kS * (capA[d] + capB[d]) * 2 + (size_t)(rowsA[d] + rowsB[d]) * (4 + 8);
+  return b;
 }
 
 const char* tc_factor_last_error() { return g_err.c_str(); }
 
 void tc_factor_free(TcFactor* w) {
   if (!w) return;
+  for (int d = 0; d < kMaxDepth; ++d)
+    if (w->side[d]) cudaStreamSynchronize(w->side[d]);
   cudaFree(w->SA);
   cudaFree(w->SB);
   cudaFree(w->eA);
   cudaFree(w->eB);
   cudaFree(w->maxA);
   cudaFree(w->maxB);
+  for (int d = 0; d < kMaxDepth; ++d) {
+    TWork& t = w->tw[d];
+    cudaFree(t.SA);
+    cudaFree(t.SB);
+    cudaFree(t.eA);
+    cudaFree(t.eB);
+    cudaFree(t.maxA);
+    cudaFree(t.maxB);
+    if (w->ready[d]) cudaEventDestroy(w->ready[d]);
+    if (w->tdone[d]) cudaEventDestroy(w->tdone[d]);
+    if (w->side[d]) cudaStreamDestroy(w->side[d]);
+  }
+  cudaGetLastError();
   delete w;
 }
 
@@ -983,6 +1081,36 @@ gls_status_t tc_factor_create(TcFactor** out, int64_t npad) {
     g_err = "cudaMalloc of the tensor-core factor workspace failed";
     return GLS_ERR_OOM;
   }
+  size_t capA[kMaxDepth] = {}, capB[kMaxDepth] = {};
+  int64_t rowsA[kMaxDepth] = {}, rowsB[kMaxDepth] = {};
+  t_sizes(npad, 0, capA, capB, rowsA, rowsB);
+  // depths the recursion reaches: 64-row leaves below npad / 2^depth
+  int depths = 1;
+  while (depths < kMaxDepth && (npad >> depths) >= 64) ++depths;
+  bool ok = true;
+  for (int d = 0; d < depths && ok; ++d) {
+    ok = cudaStreamCreateWithFlags(&w->side[d], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&w->ready[d], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&w->tdone[d], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok || capA[d] == 0) continue;
+    TWork& t = w->tw[d];
+    t.capA = capA[d];
+    t.capB = capB[d];
+    t.rowsA = rowsA[d];
+    t.rowsB = rowsB[d];
+    ok = cudaMalloc(&t.SA, (size_t)kS * t.capA * 2) == cudaSuccess &&
+         cudaMalloc(&t.SB, (size_t)kS * t.capB * 2) == cudaSuccess &&
+         cudaMalloc(&t.eA, (size_t)t.rowsA * 4) == cudaSuccess &&
+         cudaMalloc(&t.eB, (size_t)t.rowsB * 4) == cudaSuccess &&
+         cudaMalloc(&t.maxA, (size_t)t.rowsA * 8) == cudaSuccess &&
+         cudaMalloc(&t.maxB, (size_t)t.rowsB * 8) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    tc_factor_free(w);
+    g_err = "allocation of the side stream's factor workspace failed";
+    return GLS_ERR_OOM;
+  }
   *out = w;
   return GLS_OK;
 }
@@ -995,7 +1123,7 @@ cudaError_t tc_potrf_trtri(TcFactor* w, double* A, double* Z, int64_t ld, int64_
     g_err = "workspace size does not match npad";
     return cudaErrorInvalidValue;
   }
-  TC_TRY(rec(w, A, Z, ld, 0, npad, flags, st));
+  TC_TRY(rec(w, A, Z, ld, 0, npad, flags, st, 0));
   return cudaSuccess;
 }
 
