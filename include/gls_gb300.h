@@ -238,10 +238,11 @@ gls_status_t gls_solve_block(gls_plan_t plan, const int8_t* XR, int64_t ldxr, in
  * copy of block j+1 to the device runs on a side stream while block j is
  * solved, and b of block j is copied back while block j+1 is solved
  * (Section 4.2).  Mixed plans read pinned int8 input in place instead (see
- * GLS_FLAG_STAGED_INPUT).  The first block is smaller so that its unoverlapped load is
- * short (Section 4.3).  B (p x m, or p x (m t) with t phenotypes; ldb >= p)
- * and snp_status (m, may be NULL) are host memory.  Synchronous.  Device-resident XR is also accepted, in
- * which case only B and snp_status are copied.
+ * GLS_FLAG_STAGED_INPUT).  The first block of host input is smaller so that
+ * its unoverlapped load is short (Section 4.3).  B (p x m, or p x (m t) with
+ * t phenotypes; ldb >= p) and snp_status (m, may be NULL) are host or device
+ * memory.  Synchronous.  Device-resident XR is also accepted: blocks are then
+ * max_block_snps columns throughout and only host outputs are copied.
  */
 gls_status_t gls_solve_stream(gls_plan_t plan, const int8_t* XR, int64_t ldxr, int64_t m,
                               double* B, int64_t ldb, int32_t* snp_status);

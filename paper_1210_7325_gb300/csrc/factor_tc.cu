@@ -17,16 +17,16 @@
 //     x_k = 2^(E-8) sum_t s_t + d_k,   |d_k| <= 2^(E-57).
 // A product of two operands is then
 //     sum_k x_k y_k = 2^(E_x + E_y - 16) sum_k sum_{t,u} s_t s'_u  (+ truncation),
-// keeping the 28 slice pairs with t + u <= 6.  Pairs of equal level t + u
-// share one FP32 tensor-memory accumulator.  Over a chunk of at most 128
+// keeping the 28 slice pairs with t + u <= 6.  Each level t + u has its own
+// FP32 tensor-memory accumulator (7 x BN columns).  Over a chunk of at most 128
 // values of k the level-L sums are integer multiples of 2^(-8L) whose integer
 // part stays below 2^24 for L <= 3 (level 0: 128 * 2^16; level 1:
 // 2 * 128 * 2^15; level 2: 128 * (2 * 2^15 + 2^14); level 3:
 // 128 * (2 * 2^15 + 2 * 2^14)), so the tensor core adds them exactly.  Levels
-// 4..6 share a fifth accumulator whose weight is at most 2^-32 of level 0, so
-// its FP32 rounding stays near 2^-56 of the result.  The epilogue converts the
-// four exact levels of every chunk to one int64 (exact across chunks), keeps
-// the tail in FP32, and rounds once to binary64 at the end: the result carries
+// 4..6 weigh at most 2^-32 of level 0, so FP32 rounding of their sums stays
+// near 2^-56 of the result.  The epilogue converts the four exact levels of
+// every chunk to one int64 (exact across chunks), adds the tail levels in
+// FP32, and rounds once to binary64 at the end: the result carries
 // the slice truncation (about 2^-54 of max|x| max|y| per product), which is
 // below the rounding error of a binary64 dot product.
 //
@@ -48,13 +48,20 @@
 //   warp 0     TMA producer: per 16-deep stage, the 7 slices of a 128-row A tile
 //              and of a BN-row B tile (32-byte swizzle), 5-6 stages in flight
 //   warp 1     TMEM allocator and the thread issuing tcgen05.mma (M = 128,
-//              N = BN, K = 16, BF16 in, FP32 accumulate): 28 pairs per stage
-//              into five accumulators; each accumulator has its own full/empty
-//              barrier pair, so the epilogue drains level L of one 128-deep
+//              K = 16, BF16 in, FP32 accumulate), the 28 pairs of a stage in
+//              one of two orders.  The first stage of a 128-deep chunk goes
+//              level by level (N = BN, 28 MMAs), each level waiting only for
+//              the epilogue's drain of its own accumulator.  The other stages
+//              multiply A slice t by B slices 0..6-t at once: those B slices
+//              lie back to back in shared memory and the accumulators of
+//              levels t..6 back to back in tensor memory, so one MMA of
+//              N = c BN covers c pairs (c <= 256 / BN: 10 MMAs per stage for
+//              BN = 64, 7 for BN = 16).  Each accumulator has its own
+//              full/empty barrier pair, so the epilogue drains level L of a
 //              chunk while the tensor core works on the later levels and the
 //              next chunk
 //   warps 2-9  epilogue: two warps per TMEM lane quarter, BN/2 columns each;
-//              per chunk tcgen05.ld of the five accumulators into the int64 and
+//              per chunk tcgen05.ld of the seven accumulators into the int64 and
 //              FP32 sums, per tile the binary64 result written to C (three
 //              binary64 operations per element; the power-of-two scale is an
 //              exponent-field add)
@@ -86,7 +93,8 @@ constexpr int OBM = 128;               // output rows per tile (TMEM lanes)
 constexpr int OBK = 16;                // K per stage: 16 x 16-bit = one 32-byte swizzle row
 constexpr int kChunkStages = 8;        // exact chunks of 128
 constexpr int kKAlign = 32;            // operand rows are stored padded to a multiple of 32
-constexpr int kAcc = 5;                // levels 0, 1, 2, 3 (exact) and the tail 4..6
+constexpr int kAcc = kS;               // one accumulator per level t + u = 0..6
+constexpr int kExact = 4;              // levels 0..3 are summed exactly
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint64_t kWaitLimitNs = 1000000000ull;
@@ -102,8 +110,12 @@ struct Shape {
   static constexpr int kStageBytes = kABytes + kBBytes;    // multiples of 512
   static constexpr int kStages = BN == 64 ? 5 : 6;
   static constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
-  static constexpr uint32_t kTmemCols = BN == 64 ? 512 : 128;  // 5 accumulators x BN
+  static constexpr uint32_t kTmemCols = BN == 64 ? 512 : 128;  // 7 accumulators x BN
   static constexpr int kCols = BN / 2;                     // columns per epilogue warp
+  static constexpr int kASlice = OBM * OBK * 2;            // bytes of one A slice per stage
+  static constexpr int kBSlice = BN * OBK * 2;             // bytes of one B slice per stage
+  static constexpr int kPerMma = 256 / BN;                 // B slices one MMA can take (N <= 256)
+  static_assert(kAcc * BN <= (int)kTmemCols, "accumulators exceed the tensor-memory allocation");
 };
 
 enum KMode : int { kKFull = 0, kKLeJ = 1, kKGeJ = 2, kKLeI = 3, kKGeI = 4 };
@@ -307,25 +319,41 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t sbb = sa + Sh::kABytes;
             const bool chunk_first = s == 0;
             const bool chunk_last = s == ns - 1;
+            if (chunk_first) {
+              // level by level, so that each level waits only for the epilogue's
+              // drain of its own accumulator from the previous chunk
 #pragma unroll
-            for (int lam = 0; lam < kS; ++lam) {
-              const int acc = lam < kAcc - 1 ? lam : kAcc - 1;
-              if (chunk_first && lam < kAcc) {
-                // the previous chunk's value of this accumulator has been read
-                if (!mbar_wait_bounded(&aempty[acc], par ^ 1, abort_flag, kWaitLimitNs)) {
+              for (int lam = 0; lam < kS; ++lam) {
+                if (!mbar_wait_bounded(&aempty[lam], par ^ 1, abort_flag, kWaitLimitNs)) {
                   ok = false;
                   break;
                 }
                 tc_fence_after();
-              }
 #pragma unroll
-              for (int ta = 0; ta <= lam; ++ta) {
-                const int tb = lam - ta;
-                const bool fresh = chunk_first && ta == 0 && lam < kAcc;
-                umma_f16(tmem + (uint32_t)(acc * BN), umma_desc_sw32(sa + ta * (OBM * OBK * 2)),
-                         umma_desc_sw32(sbb + tb * (BN * OBK * 2)), idesc, fresh ? 0u : 1u);
+                for (int ta = 0; ta <= lam; ++ta)
+                  umma_f16(tmem + (uint32_t)(lam * BN), umma_desc_sw32(sa + ta * Sh::kASlice),
+                           umma_desc_sw32(sbb + (lam - ta) * Sh::kBSlice), idesc,
+                           ta == 0 ? 0u : 1u);
+                if (chunk_last) umma_commit(&afull[lam]);
               }
-              if (chunk_last && (lam < kAcc - 1 || lam == kS - 1)) umma_commit(&afull[acc]);
+            } else {
+              // A slice ta against B slices 0..6-ta at once: the B slices lie back
+              // to back in shared memory (one 8-row group every 256 bytes) and the
+              // accumulators of levels ta..6 back to back in tensor memory, so one
+              // MMA of N = c BN covers c consecutive pairs (c <= 256 / BN)
+#pragma unroll
+              for (int ta = 0; ta < kS; ++ta) {
+#pragma unroll
+                for (int u0 = 0; u0 < kS - ta; u0 += Sh::kPerMma) {
+                  const int c = (kS - ta - u0) < Sh::kPerMma ? (kS - ta - u0) : Sh::kPerMma;
+                  umma_f16(tmem + (uint32_t)((ta + u0) * BN),
+                           umma_desc_sw32(sa + ta * Sh::kASlice),
+                           umma_desc_sw32(sbb + u0 * Sh::kBSlice),
+                           umma_idesc_f16(OBM, c * BN, true), 1u);
+                }
+                // level ta has had its last product (ta, 0)
+                if (chunk_last) umma_commit(&afull[ta]);
+              }
             }
             umma_commit(&empty[st]);
           }
@@ -348,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!w.valid) continue;
       const int nk = (w.k1 - w.k0) / OBK;
       long long V[CW];  // exact levels 0..3, in units of 2^-24 of level 0
-      float tl[CW];     // levels 4..6
+      float tl[CW];     // levels 4..6 (weights <= 2^-32)
 #pragma unroll
       for (int j = 0; j < CW; ++j) {
         V[j] = 0;
@@ -370,7 +398,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&aempty[a]);
-          if (a < kAcc - 1) {
+          if (a < kExact) {
             // level a: an integer multiple of 2^(-8a)
             const float up = (float)(1u << (8 * a));
             const long long wgt = 1ll << (24 - 8 * a);
@@ -712,22 +740,6 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }  // namespace
 
 // ------------------------------------------------------------------ workspace
-// Recursion depths with their own workspace for T = L21 Z11 (the side stream).
-constexpr int kMaxDepth = 24;
-
-// Slices of T's two operands at one recursion depth: L21 (rows of the node's
-// lower part) and Z11 (by columns), with their row exponents and maxima.
-struct TWork {
-  size_t capA = 0, capB = 0;  // elements per slice plane
-  uint16_t* SA = nullptr;     // kS x capA
-  uint16_t* SB = nullptr;     // kS x capB
-  int* eA = nullptr;
-  int* eB = nullptr;
-  unsigned long long* maxA = nullptr;
-  unsigned long long* maxB = nullptr;
-  int64_t rowsA = 0, rowsB = 0;
-};
-
 struct TcFactor {
   int64_t npad = 0, half = 0;
   size_t cap = 0;             // elements per slice plane of SA / SB
@@ -739,14 +751,6 @@ struct TcFactor {
   unsigned long long* maxB = nullptr;
   int num_sms = 1;
   int64_t launches = 0;       // kernels enqueued so far
-  // T = L21 Z11 of each recursion node runs on its depth's side stream, beside
-  // the trailing update and the recursion on A22, with the depth's own operand
-  // slices (one stream per depth, so that the T of a deeper node never waits
-  // behind a larger one above it)
-  cudaStream_t side[kMaxDepth]{};
-  cudaEvent_t ready[kMaxDepth]{};   // L21 of the node at this depth is formed
-  cudaEvent_t tdone[kMaxDepth]{};   // its T is formed
-  TWork tw[kMaxDepth];
 };
 
 namespace {
@@ -898,42 +902,30 @@ cudaError_t launch_gemm(TcFactor* w, const Operand& A, const Operand& B, OzParam
   } while (0)
 
 cudaError_t rec(TcFactor* w, double* A, double* Z, int64_t ld, int64_t r0, int64_t n, int* flags,
-                cudaStream_t st, int depth) {
+                cudaStream_t st) {
   if (n == 64) {
     launch_potrf_diag64(A, Z, ld, r0, flags, st);
     ++w->launches;
     return cudaGetLastError();
   }
   const int64_t n1 = 64 * ((n / 64) / 2), n2 = n - n1;
-  TC_TRY(rec(w, A, Z, ld, r0, n1, flags, st, depth + 1));
+  TC_TRY(rec(w, A, Z, ld, r0, n1, flags, st));
   double* A21 = A + (r0 + n1) + r0 * ld;
   double* A22 = A + (r0 + n1) + (r0 + n1) * ld;
   double* Z11 = Z + r0 + r0 * ld;
   double* Z21 = Z + (r0 + n1) + r0 * ld;
   double* Z22 = Z + (r0 + n1) + (r0 + n1) * ld;
-  // T = L21 Z11 needs only L21 and Z11: it runs on the side stream while this
-  // stream updates A22 and factors it; T is kept in the Z21 block (zero until
-  // Z21 = -Z22 T overwrites it), which nothing else touches before that step
-  // (a depth without its stream or workspace keeps everything on this stream)
-  const bool split_t = depth < kMaxDepth && w->side[depth] != nullptr;
-  cudaStream_t sd = split_t ? w->side[depth] : st;
   if (n <= kSmallNode) {
     const dim3 rows((unsigned)n2), cols((unsigned)n1);
     small_rows_kernel<<<rows, kSmallThreads, 0, st>>>(A21, A21, Z11, ld, (int)n1, (int)n1,
                                                       kSmL21, flags);
-    if (split_t) {
-      TC_TRY(cudaEventRecord(w->ready[depth], st));
-      TC_TRY(cudaStreamWaitEvent(sd, w->ready[depth], 0));
-    }
-    small_rows_kernel<<<rows, kSmallThreads, 0, sd>>>(A21, Z21, Z11, ld, (int)n1, (int)n1, kSmT,
-                                                      flags);
-    if (split_t) TC_TRY(cudaEventRecord(w->tdone[depth], sd));
     small_rows_kernel<<<rows, kSmallThreads, 0, st>>>(A21, A22, A21, ld, (int)n2, (int)n1,
                                                       kSmSyrk, flags);
+    small_rows_kernel<<<rows, kSmallThreads, 0, st>>>(A21, Z21, Z11, ld, (int)n1, (int)n1, kSmT,
+                                                      flags);
     w->launches += 3;
     TC_TRY(cudaGetLastError());
-    TC_TRY(rec(w, A, Z, ld, r0 + n1, n2, flags, st, depth + 1));
-    if (split_t) TC_TRY(cudaStreamWaitEvent(st, w->tdone[depth], 0));
+    TC_TRY(rec(w, A, Z, ld, r0 + n1, n2, flags, st));
     small_z21_kernel<<<cols, kSmallThreads, 0, st>>>(Z22, Z21, ld, (int)n2, flags);
     ++w->launches;
     return cudaGetLastError();
@@ -945,44 +937,21 @@ cudaError_t rec(TcFactor* w, double* A, double* Z, int64_t ld, int64_t r0, int64
                 job(Z11, ld, n1, n1, true, w->SB, w->eB, w->maxB), flags, st));
   TC_TRY(gemm(w, SA1, SB1, A21, ld, (int)n2, (int)n1, (int)n1, kKLeJ, 0, false, 0, false, 0,
               flags, st));
-  if (!split_t || !w->tw[depth].SA) {
-    // in order on this stream: one slicing of L21 serves the trailing update
-    // and T, which is formed before the recursion on A22 reuses the slices
-    TC_TRY(slice2(w, job(A21, ld, n2, n1, true, w->SA, w->eA, w->maxA),
-                  job(Z11, ld, n1, n1, false, w->SB, w->eB, w->maxB), flags, st));
-    TC_TRY(gemm(w, SA1, SA1, A22, ld, (int)n2, (int)n2, (int)n1, kKFull, 0, true, 1, true, 0,
-                flags, st));
-    TC_TRY(gemm(w, SA1, SB1, Z21, ld, (int)n2, (int)n1, (int)n1, kKGeJ, 0, false, 0, false, 0,
-                flags, st));
-    TC_TRY(rec(w, A, Z, ld, r0 + n1, n2, flags, st, depth + 1));
-    const Operand SA2{w->SA, w->eA, n2, round_up(n2, kKAlign)};
-    const Operand SB2{w->SB, w->eB, n1, round_up(n2, kKAlign)};
-    TC_TRY(slice2(w, job(Z22, ld, n2, n2, true, w->SA, w->eA, w->maxA),
-                  job(Z21, ld, n1, n2, false, w->SB, w->eB, w->maxB), flags, st));
-    return gemm(w, SA2, SB2, Z21, ld, (int)n2, (int)n1, (int)n2, kKLeI, 0, true, 0, false, 0,
-                flags, st);
-  }
-  TC_TRY(cudaEventRecord(w->ready[depth], st));
-  // side stream: T = L21 Z11 (Z11 lower: column j needs k >= j) from this
-  // depth's own slices of L21 (rows) and Z11 (columns)
-  TWork& tw = w->tw[depth];
-  TC_TRY(cudaStreamWaitEvent(sd, w->ready[depth], 0));
-  TC_TRY(slice2(w, job(A21, ld, n2, n1, true, tw.SA, tw.eA, tw.maxA),
-                job(Z11, ld, n1, n1, false, tw.SB, tw.eB, tw.maxB), flags, sd));
-  const Operand TA{tw.SA, tw.eA, n2, round_up(n1, kKAlign)};
-  const Operand TB{tw.SB, tw.eB, n1, round_up(n1, kKAlign)};
-  TC_TRY(gemm(w, TA, TB, Z21, ld, (int)n2, (int)n1, (int)n1, kKGeJ, 0, false, 0, false, 0, flags,
-              sd));
-  TC_TRY(cudaEventRecord(w->tdone[depth], sd));
-  // this stream: A22 -= L21 L21^T (lower triangle)
+  // One slicing of L21 serves both the trailing update and T = L21 Z11, which
+  // does not depend on the factor of A22 and is formed before it.  T is kept
+  // in the Z21 block (zero until Z21 = -Z22 T overwrites it below); the
+  // recursion on A22 touches only A22 and Z22.
   TC_TRY(slice2(w, job(A21, ld, n2, n1, true, w->SA, w->eA, w->maxA),
-                job(nullptr, ld, 0, 0, true, w->SB, w->eB, w->maxB), flags, st));
+                job(Z11, ld, n1, n1, false, w->SB, w->eB, w->maxB), flags, st));
+  // A22 -= L21 L21^T (lower triangle)
   TC_TRY(gemm(w, SA1, SA1, A22, ld, (int)n2, (int)n2, (int)n1, kKFull, 0, true, 1, true, 0, flags,
               st));
-  TC_TRY(rec(w, A, Z, ld, r0 + n1, n2, flags, st, depth + 1));
+  // T = L21 Z11 (Z11 lower: column j needs k >= j)
+  TC_TRY(gemm(w, SA1, SB1, Z21, ld, (int)n2, (int)n1, (int)n1, kKGeJ, 0, false, 0, false, 0,
+              flags, st));
+  TC_TRY(rec(w, A, Z, ld, r0 + n1, n2, flags, st));
   // Z21 = -Z22 T (Z22 lower: row block I needs k < (I+1) 128); T's slices are
   // taken before the product overwrites it
-  TC_TRY(cudaStreamWaitEvent(st, w->tdone[depth], 0));
   const Operand SA2{w->SA, w->eA, n2, round_up(n2, kKAlign)};
   const Operand SB2{w->SB, w->eB, n1, round_up(n2, kKAlign)};
   TC_TRY(slice2(w, job(Z22, ld, n2, n2, true, w->SA, w->eA, w->maxA),
@@ -990,24 +959,6 @@ cudaError_t rec(TcFactor* w, double* A, double* Z, int64_t ld, int64_t r0, int64
   TC_TRY(gemm(w, SA2, SB2, Z21, ld, (int)n2, (int)n1, (int)n2, kKLeI, 0, true, 0, false, 0, flags,
               st));
   return cudaSuccess;
-}
-
-// Largest operands of T = L21 Z11 at each recursion depth of an npad x npad
-// factor (nodes above kSmallNode rows only): rows x padded k of L21's and of
-// Z11's slices, and their row counts.
-void t_sizes(int64_t n, int depth, size_t capA[], size_t capB[], int64_t rowsA[],
-             int64_t rowsB[]) {
-  if (n == 64 || depth >= kMaxDepth) return;
-  const int64_t n1 = 64 * ((n / 64) / 2), n2 = n - n1;
-  if (n > kSmallNode) {
-    const size_t k = (size_t)round_up(n1, kKAlign);
-    capA[depth] = std::max(capA[depth], (size_t)n2 * k);
-    capB[depth] = std::max(capB[depth], (size_t)n1 * k);
-    rowsA[depth] = std::max(rowsA[depth], n2);
-    rowsB[depth] = std::max(rowsB[depth], n1);
-  }
-  t_sizes(n1, depth + 1, capA, capB, rowsA, rowsB);
-  t_sizes(n2, depth + 1, capA, capB, rowsA, rowsB);
 }
 
 // Rows per panel so that rows x K fits one slice plane.
@@ -1020,40 +971,19 @@ int64_t panel_rows(const TcFactor* w, int64_t K) {
 }  // namespace
 
 size_t tc_factor_bytes(int64_t npad) {
-  size_t capA[kMaxDepth] = {}, capB[kMaxDepth] = {};
-  int64_t rowsA[kMaxDepth] = {}, rowsB[kMaxDepth] = {};
-  t_sizes(npad, 0, capA, capB, rowsA, rowsB);
-  size_t b = 2 * (size_t)kS * plane_cap(npad) * 2 + 2 * (size_t)npad * (4 + 8);
-  for (int d = 0; d < kMaxDepth; ++d)
-    b += (size_t)kS * (capA[d] + capB[d]) * 2 + (size_t)(rowsA[d] + rowsB[d]) * (4 + 8);
-  return b;
+  return 2 * (size_t)kS * plane_cap(npad) * 2 + 2 * (size_t)npad * (4 + 8);
 }
 
 const char* tc_factor_last_error() { return g_err.c_str(); }
 
 void tc_factor_free(TcFactor* w) {
   if (!w) return;
-  for (int d = 0; d < kMaxDepth; ++d)
-    if (w->side[d]) cudaStreamSynchronize(w->side[d]);
   cudaFree(w->SA);
   cudaFree(w->SB);
   cudaFree(w->eA);
   cudaFree(w->eB);
   cudaFree(w->maxA);
   cudaFree(w->maxB);
-  for (int d = 0; d < kMaxDepth; ++d) {
-    TWork& t = w->tw[d];
-    cudaFree(t.SA);
-    cudaFree(t.SB);
-    cudaFree(t.eA);
-    cudaFree(t.eB);
-    cudaFree(t.maxA);
-    cudaFree(t.maxB);
-    if (w->ready[d]) cudaEventDestroy(w->ready[d]);
-    if (w->tdone[d]) cudaEventDestroy(w->tdone[d]);
-    if (w->side[d]) cudaStreamDestroy(w->side[d]);
-  }
-  cudaGetLastError();
   delete w;
 }
 
@@ -1081,36 +1011,6 @@ gls_status_t tc_factor_create(TcFactor** out, int64_t npad) {
     g_err = "cudaMalloc of the tensor-core factor workspace failed";
     return GLS_ERR_OOM;
   }
-  size_t capA[kMaxDepth] = {}, capB[kMaxDepth] = {};
-  int64_t rowsA[kMaxDepth] = {}, rowsB[kMaxDepth] = {};
-  t_sizes(npad, 0, capA, capB, rowsA, rowsB);
-  // depths the recursion reaches: 64-row leaves below npad / 2^depth
-  int depths = 1;
-  while (depths < kMaxDepth && (npad >> depths) >= 64) ++depths;
-  bool ok = true;
-  for (int d = 0; d < depths && ok; ++d) {
-    ok = cudaStreamCreateWithFlags(&w->side[d], cudaStreamNonBlocking) == cudaSuccess &&
-         cudaEventCreateWithFlags(&w->ready[d], cudaEventDisableTiming) == cudaSuccess &&
-         cudaEventCreateWithFlags(&w->tdone[d], cudaEventDisableTiming) == cudaSuccess;
-    if (!ok || capA[d] == 0) continue;
-    TWork& t = w->tw[d];
-    t.capA = capA[d];
-    t.capB = capB[d];
-    t.rowsA = rowsA[d];
-    t.rowsB = rowsB[d];
-    ok = cudaMalloc(&t.SA, (size_t)kS * t.capA * 2) == cudaSuccess &&
-         cudaMalloc(&t.SB, (size_t)kS * t.capB * 2) == cudaSuccess &&
-         cudaMalloc(&t.eA, (size_t)t.rowsA * 4) == cudaSuccess &&
-         cudaMalloc(&t.eB, (size_t)t.rowsB * 4) == cudaSuccess &&
-         cudaMalloc(&t.maxA, (size_t)t.rowsA * 8) == cudaSuccess &&
-         cudaMalloc(&t.maxB, (size_t)t.rowsB * 8) == cudaSuccess;
-  }
-  if (!ok) {
-    cudaGetLastError();
-    tc_factor_free(w);
-    g_err = "allocation of the side stream's factor workspace failed";
-    return GLS_ERR_OOM;
-  }
   *out = w;
   return GLS_OK;
 }
@@ -1123,7 +1023,7 @@ cudaError_t tc_potrf_trtri(TcFactor* w, double* A, double* Z, int64_t ld, int64_
     g_err = "workspace size does not match npad";
     return cudaErrorInvalidValue;
   }
-  TC_TRY(rec(w, A, Z, ld, 0, npad, flags, st, 0));
+  TC_TRY(rec(w, A, Z, ld, 0, npad, flags, st));
   return cudaSuccess;
 }
 

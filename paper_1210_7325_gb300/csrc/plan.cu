@@ -1016,10 +1016,12 @@ gls_status_t packed_staging(gls_plan* pl, bool pinned) {
 }
 
 // Block schedule of a stream of m SNPs: a short first block (its load is not
-// overlapped), then doubling up to max_block_snps (Section 4.3).
-std::vector<std::pair<int64_t, int64_t>> block_schedule(int64_t kmax, int64_t m) {
+// overlapped), then doubling up to max_block_snps (Section 4.3); uniform:
+// max_block_snps throughout.
+std::vector<std::pair<int64_t, int64_t>> block_schedule(int64_t kmax, int64_t m,
+                                                        bool uniform = false) {
   std::vector<std::pair<int64_t, int64_t>> blocks;
-  int64_t kb = std::min<int64_t>(kmax, std::max<int64_t>(256, kmax / 8));
+  int64_t kb = uniform ? kmax : std::min<int64_t>(kmax, std::max<int64_t>(256, kmax / 8));
   for (int64_t s0 = 0; s0 < m;) {
     const int64_t kk = std::min<int64_t>(kb, m - s0);
     blocks.emplace_back(s0, kk);
@@ -1145,8 +1147,9 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
                       !(pl->desc.flags & GLS_FLAG_STAGED_INPUT);
   const bool staged = (mx != Mem::Device) && !direct;
 
+  // device-resident input has no load to hide behind a short first block
   const std::vector<std::pair<int64_t, int64_t>> blocks =
-      ring ? ring->blocks : block_schedule(kmax, m);
+      ring ? ring->blocks : block_schedule(kmax, m, mx == Mem::Device);
   // host and device addresses of block jb's first column (ld = ldx)
   auto src_host = [&](size_t jb) -> const uint8_t* {
     return ring ? ring->slot[jb % FileRing::kSlots] : X + blocks[jb].first * ldx;

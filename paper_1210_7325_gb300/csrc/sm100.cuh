@@ -95,18 +95,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 // ---------------------------------------------------------------- TMA
-// A tensor map that the host wrote into global memory (cudaMemcpy) is seen by
-// the TMA unit through the tensormap proxy, which may hold a cached copy of
-// whatever descriptor was at that address before (an earlier allocation that
-// was freed and reused).  This acquire fence, at system scope because the
-// writer is the host, makes the current contents visible to the calling
-// thread's later TMA operations on that map.
-__device__ __forceinline__ void tensormap_acquire_sys(const CUtensorMap* map) {
-  asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(
-                   reinterpret_cast<uint64_t>(map))
-               : "memory");
-}
-
 __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }

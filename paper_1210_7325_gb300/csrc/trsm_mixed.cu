@@ -65,10 +65,11 @@
 // it for a few percent of the time.
 //
 // One launch can serve many independent problems (scans with their own M, n,
-// p and SNP block): each problem has a descriptor in device memory (its TMA
-// maps and buffers) and the launch's by-value run parameters give each
-// problem's block size and the prefix of its work items; the persistent CTAs
-// walk the concatenated item list, largest problems first.
+// p and SNP block): each problem has a descriptor in device memory (its
+// buffers), its TMA maps travel by value in the launch's parameters, and the
+// by-value run parameters give each problem's block size and the prefix of
+// its work items; the persistent CTAs walk the concatenated item list,
+// largest problems first.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -111,10 +112,8 @@ constexpr int kDefaultGroup = 3;        // row-block pairs per rasterization gro
 
 thread_local std::string g_err;
 
-// Per-problem constants, in device memory (64-byte aligned for the TMA maps).
-struct alignas(64) ProblemDesc {
-  CUtensorMap tmA;        // slices of Z and W^T: (npad, npad + 128, S), 16-bit
-  CUtensorMap tmB;        // genotype operand X16: (npad, kmax), 16-bit
+// Per-problem constants, in device memory.
+struct ProblemDesc {
   const uint8_t* x8a;     // genotypes as bytes, SNP-major [j][npad], zero rows >= n
   const float* rowscale;  // u_r, npad + 128 rows
   const float* diagKL;    // npad x (k[4], l[4]): split diagonal blocks
@@ -124,6 +123,15 @@ struct alignas(64) ProblemDesc {
   int64_t npad, ldp;
   int nI, p;
   uint32_t idesc, idesc_half;  // MMA N = 256 (two row blocks) and N = 128 (one), BF16 or FP16
+};
+
+// The TMA maps of every problem of a launch, passed by value as a
+// __grid_constant__ parameter (16 KB for kMaxBatch problems): the TMA unit
+// reads them from parameter space, so no map ever lives in global memory
+// that the host writes and later frees and reuses.
+struct MapSet {
+  CUtensorMap tmA[kMaxBatch];  // slices of Z and W^T: (npad, npad + 128, S), 16-bit
+  CUtensorMap tmB[kMaxBatch];  // genotype operand X16: (npad, kmax), 16-bit
 };
 
 // Per-launch values, by value: each problem's block size and item range.
@@ -252,7 +260,8 @@ __device__ __forceinline__ void add_square(uint32_t aH, uint32_t aR, float u, fl
 
 __global__ void __launch_bounds__(kThreads, 1)
     trsm_gram_mixed_kernel(const ProblemDesc* __restrict__ probs,
-                           const __grid_constant__ RunParams run, const KConst kc) {
+                           const __grid_constant__ RunParams run, const KConst kc,
+                           const __grid_constant__ MapSet maps) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -297,14 +306,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       int last_pi = -1;
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
         const Item w = item_at(probs, run, t);
-        const ProblemDesc* pd = probs + w.pi;
+        const CUtensorMap* tA = &maps.tmA[w.pi];
+        const CUtensorMap* tB = &maps.tmB[w.pi];
         if (w.pi != last_pi) {
-          // the maps live in global memory written by the host: fence before
-          // this thread's first TMA with them (see tensormap_acquire_sys)
-          tensormap_acquire_sys(&pd->tmA);
-          tensormap_acquire_sys(&pd->tmB);
-          tma_prefetch_desc(&pd->tmA);
-          tma_prefetch_desc(&pd->tmB);
+          tma_prefetch_desc(tA);
+          tma_prefetch_desc(tB);
           last_pi = w.pi;
         }
         // always a 256-row box: rows past the W^T block read as zeros, and the
@@ -320,8 +326,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           mbar_arrive_expect_tx(&full[st], (uint32_t)S * kSliceBytes + kXBytes);
           uint8_t* sb = base + (size_t)st * kc.stage_bytes;
           for (int s = 0; s < S; ++s)
-            tma_load_3d(sb + s * kSliceBytes, &pd->tmA, &full[st], kb * BK, row0, s);
-          tma_load_2d(sb + S * kSliceBytes, &pd->tmB, &full[st], kb * BK, w.J * BN);
+            tma_load_3d(sb + s * kSliceBytes, tA, &full[st], kb * BK, row0, s);
+          tma_load_2d(sb + S * kSliceBytes, tB, &full[st], kb * BK, w.J * BN);
         }
       }
       if (!ok) raise_error(kc.flags, 1);
@@ -847,6 +853,7 @@ struct MixedState {
   uint16_t* x16 = nullptr;     // kmax x npad
   uint8_t* x8a = nullptr;      // kmax x npad
   ProblemDesc desc;            // host copy (buffers filled in by the plan per call)
+  MapSet maps;                 // this problem's maps in slot 0 (single-problem launches)
   ProblemDesc* d_desc = nullptr;  // device copy used by single-problem launches
   double* d_Pbr = nullptr;     // buffers the device copy currently points to
   double* d_Glin = nullptr;
@@ -857,6 +864,7 @@ struct MixedState {
 struct MixedBatch {
   std::vector<MixedState*> states;  // launch order (largest n first)
   std::vector<int> order;           // states[i] = input[order[i]]
+  MapSet maps;                      // slot i: the maps of states[i]
   ProblemDesc* d_desc = nullptr;
   std::vector<double*> Pbr, Glin;
 };
@@ -976,12 +984,14 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
       ms->bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   ProblemDesc& d = ms->desc;
   memset(&d, 0, sizeof(d));
+  memset(&ms->maps, 0, sizeof(ms->maps));
   {
     cuuint64_t dims[3] = {(cuuint64_t)npad, (cuuint64_t)rows, (cuuint64_t)ms->S};
     cuuint64_t strides[2] = {(cuuint64_t)npad * 2, (cuuint64_t)rows * npad * 2};
     cuuint32_t box[3] = {BK, kPair, 1};
     cuuint32_t es[3] = {1, 1, 1};
-    if (enc(&d.tmA, dt, 3, ms->slices, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    if (enc(&ms->maps.tmA[0], dt, 3, ms->slices, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return fail(GLS_ERR_CUDA, "tensor map encode (slices) failed");
@@ -991,7 +1001,8 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
     cuuint64_t strides[1] = {(cuuint64_t)npad * 2};
     cuuint32_t box[2] = {BK, BN};
     cuuint32_t es[2] = {1, 1};
-    if (enc(&d.tmB, dt, 2, ms->x16, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    if (enc(&ms->maps.tmB[0], dt, 2, ms->x16, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return fail(GLS_ERR_CUDA, "tensor map encode (genotypes) failed");
@@ -1087,11 +1098,11 @@ int items_of(const MixedState* ms, int64_t k) {
 }
 
 cudaError_t launch(const MixedState* ms0, const ProblemDesc* d_desc, const RunParams& run,
-                   int* flags, cudaStream_t st) {
+                   const MapSet& maps, int* flags, cudaStream_t st) {
   KConst kc = ms0->kc;
   kc.flags = flags;
   const int grid = std::min(ms0->num_sms, std::max(run.total, 1));
-  trsm_gram_mixed_kernel<<<grid, kThreads, ms0->smem, st>>>(d_desc, run, kc);
+  trsm_gram_mixed_kernel<<<grid, kThreads, ms0->smem, st>>>(d_desc, run, kc, maps);
   return cudaGetLastError();
 }
 
@@ -1122,7 +1133,7 @@ cudaError_t mixed_trsm_gram(MixedState* ms, const int8_t* xr, int64_t ldxr, int6
   run.nJ[0] = (int)ceil_div(k, BN);
   run.item_begin[0] = 0;
   run.total = run.item_begin[1] = items_of(ms, k);
-  return launch(ms, ms->d_desc, run, flags, st);
+  return launch(ms, ms->d_desc, run, ms->maps, flags, st);
 }
 
 int mixed_split_terms(const MixedState* ms) { return ms->S; }
@@ -1148,9 +1159,12 @@ gls_status_t mixed_batch_create(MixedState* const* states, const double* const* 
   std::stable_sort(b->order.begin(), b->order.end(),
                    [&](int a, int c) { return states[a]->n > states[c]->n; });
   std::vector<ProblemDesc> h(count);
+  memset(&b->maps, 0, sizeof(b->maps));
   for (int i = 0; i < count; ++i) {
     const int o = b->order[i];
     b->states.push_back(states[o]);
+    b->maps.tmA[i] = states[o]->maps.tmA[0];
+    b->maps.tmB[i] = states[o]->maps.tmB[0];
     h[i] = states[o]->desc;
     h[i].Pbr = const_cast<double*>(Pbr[o]);
     h[i].Glin = const_cast<double*>(Glin[o]);
@@ -1193,7 +1207,7 @@ cudaError_t mixed_batch_run(MixedBatch* b, const int64_t* k, int group, int* fla
   run.item_begin[count] = total;
   run.total = total;
   if (total == 0) return cudaSuccess;
-  return launch(b->states[0], b->d_desc, run, flags, st);
+  return launch(b->states[0], b->d_desc, run, b->maps, flags, st);
 }
 
 }  // namespace gls
