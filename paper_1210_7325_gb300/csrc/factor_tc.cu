@@ -129,22 +129,11 @@ struct OzParams {
   const int* eB;     // row exponents of the B operand
   int64_t diag_off;  // lower: store only where row + diag_off >= col
   int M, N, tilesI, tilesJ;
+  int ntiles;        // tiles of the launch: tilesI x tilesJ, or the lower ones only
   int Kend, kmode, koff;
   int neg, beta, lower;  // C = (neg ? -1 : 1) A B^T + (beta ? C : 0)
   int* flags;        // plan status words: kFlagPotrf read, kFlagKernel / kFlagWhere written
 };
-
-// K-major operand tile written by TMA with 32-byte swizzling: rows of 32
-// bytes (16 BF16), 8-row groups 256 bytes apart.
-__device__ __forceinline__ uint64_t umma_desc_sw32(uint32_t smem_addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)(16u >> 4) << 16;   // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(256u >> 4) << 32;  // stride byte offset: 8 rows x 32 bytes
-  d |= (uint64_t)1 << 46;            // descriptor version
-  d |= (uint64_t)6 << 61;            // 32-byte swizzle
-  return d;
-}
 
 __device__ __forceinline__ double pow2i(int e) {
   if (e >= -1022 && e <= 1023) return __longlong_as_double((long long)(e + 1023) << 52);
@@ -165,12 +154,40 @@ struct TileWork {
   bool valid;
 };
 
+// Valid tiles of block row I of a lower-triangular output: J = 0 .. count - 1.
+template <int BN>
+__device__ __forceinline__ int lower_count(const OzParams& q, int I) {
+  const int64_t c = ((int64_t)I * OBM + OBM - 1 + q.diag_off) / BN + 1;
+  return (int)(c < 0 ? 0 : (c > q.tilesJ ? q.tilesJ : c));
+}
+
+// Tile t of the launch, heaviest first: the persistent CTAs take tiles t,
+// t + grid, ... so that the longest K ranges are spread over all of them
+// first (a triangular operand's K range grows or shrinks with I or J), and a
+// lower-triangular output lists only its valid tiles.
 template <int BN>
 __device__ __forceinline__ TileWork tile_work(const OzParams& q, int t) {
   TileWork w;
-  w.I = t / q.tilesJ;
-  w.J = t - w.I * q.tilesJ;
-  w.valid = !q.lower || ((int64_t)w.I * OBM + OBM - 1 + q.diag_off >= (int64_t)w.J * BN);
+  w.valid = t < q.ntiles;
+  switch (q.kmode) {
+    case kKLeJ: w.J = q.tilesJ - 1 - t / q.tilesI; w.I = t % q.tilesI; break;
+    case kKGeJ: w.J = t / q.tilesI; w.I = t % q.tilesI; break;
+    case kKLeI: w.I = q.tilesI - 1 - t / q.tilesJ; w.J = t % q.tilesJ; break;
+    case kKGeI: w.I = t / q.tilesJ; w.J = t % q.tilesJ; break;
+    default:
+      if (q.lower) {
+        int I = 0, r = t;
+        while (I < q.tilesI - 1 && r >= lower_count<BN>(q, I)) r -= lower_count<BN>(q, I++);
+        w.I = I;
+        w.J = r;
+      } else {
+        w.I = t / q.tilesJ;
+        w.J = t % q.tilesJ;
+      }
+      break;
+  }
+  w.valid = w.valid && w.I >= 0 && w.I < q.tilesI && w.J >= 0 && w.J < q.tilesJ &&
+            (!q.lower || ((int64_t)w.I * OBM + OBM - 1 + q.diag_off >= (int64_t)w.J * BN));
   int k0 = 0, k1 = q.Kend;
   switch (q.kmode) {
     case kKLeJ: k1 = min(k1, (w.J + 1) * BN + q.koff); break;
@@ -261,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int ntiles = q.tilesI * q.tilesJ;
+  const int ntiles = q.ntiles;
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -519,6 +536,20 @@ __global__ void __launch_bounds__(kSmallThreads)
 
 // ---------------------------------------------------------------- slicing
 // The kS slices of x relative to 2^E (see the file header), as BF16 bits.
+// BF16 bits of a 2^(-8t) for an integer |a| <= 256, a value BF16 holds
+// exactly: the float of |a| from the 2^23 exponent trick (an integer OR and
+// one FP32 subtraction), scaled by an exact power of two, its upper half
+// taken (its lower half is zero) and the sign set.  Integer and FP32
+// arithmetic only: the conversion instructions this replaces (integer to
+// float, float to BF16, two per digit and seven digits per element) share a
+// pipe a quarter as wide and bounded the slicing kernel.
+__device__ __forceinline__ uint16_t bf16_digit(int a, int t) {
+  const unsigned int m = (unsigned int)(a < 0 ? -a : a);
+  const float f = (__uint_as_float(0x4B000000u | m) - 8388608.0f) *
+                  __uint_as_float((uint32_t)(127 - 8 * t) << 23);
+  return (uint16_t)((__float_as_uint(f) >> 16) | (a < 0 ? 0x8000u : 0u));
+}
+
 __device__ __forceinline__ void slice_value(double x, int E, uint16_t (&s)[kS]) {
   const long long bits = __double_as_longlong(x);
   const int ex = (int)((bits >> 52) & 0x7FF);
@@ -538,9 +569,9 @@ __device__ __forceinline__ void slice_value(double x, int E, uint16_t (&s)[kS]) 
     const int sh = 48 - 8 * t;
     const long long a = (r + (1ll << (sh - 1))) >> sh;
     r -= a * (1ll << sh);
-    s[t] = __bfloat16_as_ushort(__float2bfloat16_rn(ldexpf((float)a, -8 * t)));
+    s[t] = bf16_digit((int)a, t);
   }
-  s[kS - 1] = __bfloat16_as_ushort(__float2bfloat16_rn(ldexpf((float)r, -8 * (kS - 1))));
+  s[kS - 1] = bf16_digit((int)r, kS - 1);
 }
 
 // One operand to slice: x(i, k) = src[i + k ld] (rows mode, operand rows are
@@ -561,13 +592,6 @@ struct SliceJob {
   int nblocks;  // bands x kblocks
 };
 
-__device__ __forceinline__ void pack8(const uint16_t (&v)[8][kS], int t, uint4& o) {
-  o.x = (uint32_t)v[0][t] | ((uint32_t)v[1][t] << 16);
-  o.y = (uint32_t)v[2][t] | ((uint32_t)v[3][t] << 16);
-  o.z = (uint32_t)v[4][t] | ((uint32_t)v[5][t] << 16);
-  o.w = (uint32_t)v[6][t] | ((uint32_t)v[7][t] << 16);
-}
-
 constexpr int kSliceWarps = 16;
 constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
 
@@ -587,19 +611,52 @@ __device__ __forceinline__ int exponent_of_bits(unsigned long long mb) {
 
 // 8 consecutive k (k0 .. k0+7) of one operand row: x(k) = base[k * stride],
 // sliced and stored as one 16-byte vector per slice.
-__device__ __forceinline__ void slice_store8(const double* base, int64_t stride, int64_t K,
-                                             int64_t k0, int E, uint16_t* dst, size_t plane) {
-  uint16_t v[8][kS];
+__device__ __forceinline__ void load8(const double* base, int64_t stride, int64_t K, int64_t k0,
+                                      double (&x)[8]) {
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int64_t k = k0 + e;
-    slice_value(k < K ? base[k * stride] : 0.0, E, v[e]);
+    x[e] = k < K ? base[k * stride] : 0.0;
+  }
+}
+
+// The slices of x (8 consecutive k from k0), one 16-byte store per slice:
+// slice t of elements 2w and 2w+1 share word w of that store.
+__device__ __forceinline__ void store8(const double (&x)[8], int64_t k0, int E, uint16_t* dst,
+                                       size_t plane) {
+  uint32_t o[kS][4];
+#pragma unroll
+  for (int e = 0; e < 8; e += 2) {
+    uint16_t a[kS], b[kS];
+    slice_value(x[e], E, a);
+    slice_value(x[e + 1], E, b);
+#pragma unroll
+    for (int t = 0; t < kS; ++t) o[t][e / 2] = (uint32_t)a[t] | ((uint32_t)b[t] << 16);
   }
 #pragma unroll
-  for (int t = 0; t < kS; ++t) {
-    uint4 o;
-    pack8(v, t, o);
-    *reinterpret_cast<uint4*>(dst + t * plane + k0) = o;
+  for (int t = 0; t < kS; ++t)
+    *reinterpret_cast<uint4*>(dst + t * plane + k0) = make_uint4(o[t][0], o[t][1], o[t][2], o[t][3]);
+}
+
+// k0 = first, first + step, ... < kend: each iteration's loads are issued
+// before the previous iteration's values are sliced and stored, so a warp
+// keeps two iterations of loads in flight (the kernel is bound by the latency
+// of its loads, not by their bandwidth).
+__device__ __forceinline__ void slice_span(const double* base, int64_t stride, int64_t K,
+                                           int64_t first, int64_t kend, int64_t step, int E,
+                                           uint16_t* dst, size_t plane) {
+  if (first >= kend) return;
+  double x[8];
+  load8(base, stride, K, first, x);
+  for (int64_t k0 = first; k0 < kend; k0 += step) {
+    double xn[8];
+    const bool more = k0 + step < kend;
+    if (more) load8(base, stride, K, k0 + step, xn);
+    store8(x, k0, E, dst, plane);
+    if (more) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) x[e] = xn[e];
+    }
   }
 }
 
@@ -638,8 +695,7 @@ __device__ void slice_rows_tile(const SliceJob& j, int band, int kb) {
   const size_t plane = (size_t)j.R * j.kld;
   uint16_t* dst = j.out + i * j.kld;
   const int64_t kend = min(j.kld, (int64_t)(kb + 1) * j.kspan);
-  for (int64_t k0 = (int64_t)kb * j.kspan + w * 8; k0 < kend; k0 += 8 * kSliceWarps)
-    slice_store8(row, j.ld, j.K, k0, E, dst, plane);
+  slice_span(row, j.ld, j.K, (int64_t)kb * j.kspan + w * 8, kend, 8 * kSliceWarps, E, dst, plane);
 }
 
 // Columns mode tile: 16 operand rows (one warp each, a contiguous source
@@ -664,8 +720,7 @@ __device__ void slice_cols_tile(const SliceJob& j, int band, int kb) {
   const size_t plane = (size_t)j.R * j.kld;
   uint16_t* dst = j.out + i * j.kld;
   const int64_t kend = min(j.kld, (int64_t)(kb + 1) * j.kspan);
-  for (int64_t k0 = (int64_t)kb * j.kspan + l * 8; k0 < kend; k0 += 256)
-    slice_store8(col, 1, j.K, k0, E, dst, plane);
+  slice_span(col, 1, j.K, (int64_t)kb * j.kspan + l * 8, kend, 256, E, dst, plane);
 }
 
 // Up to two operands in one launch: blocks [0, a.nblocks) slice a, the rest b.
@@ -888,8 +943,18 @@ cudaError_t launch_gemm(TcFactor* w, const Operand& A, const Operand& B, OzParam
   cudaError_t e;
   if ((e = encode(&ta, A, OBM)) != cudaSuccess) return e;
   if ((e = encode(&tb, B, BN)) != cudaSuccess) return e;
-  const int tiles = q.tilesI * q.tilesJ;
-  const int grid = std::max(1, std::min(w->num_sms, tiles));
+  // tiles of the launch (the lower ones only for a lower-triangular output)
+  int64_t tiles = (int64_t)q.tilesI * q.tilesJ;
+  if (q.lower && q.kmode == kKFull) {  // tile_work lists only the valid ones then
+    tiles = 0;
+    for (int I = 0; I < q.tilesI; ++I) {
+      const int64_t c = ((int64_t)I * OBM + OBM - 1 + q.diag_off) / BN + 1;
+      tiles += c < 0 ? 0 : std::min<int64_t>(c, q.tilesJ);
+    }
+  }
+  if (tiles == 0) return cudaSuccess;
+  q.ntiles = (int)tiles;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(w->num_sms, tiles));
   oz_gemm_kernel<BN><<<grid, kThreads, Sh::kSmemBytes, st>>>(ta, tb, q);
   ++w->launches;
   return cudaGetLastError();

@@ -155,6 +155,18 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t smem_addr) {
   return d;
 }
 
+// The same for 32-byte swizzling: rows of 32 bytes (16 16-bit values), 8-row
+// groups 256 bytes apart, layout 6.
+__device__ __forceinline__ uint64_t umma_desc_sw32(uint32_t smem_addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(256u >> 4) << 32;  // stride byte offset: 8 rows x 32 bytes
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)6 << 61;            // 32-byte swizzle
+  return d;
+}
+
 // The same for 64-byte swizzling: rows of 64 bytes, 8-row groups 512 bytes
 // apart, layout 4.
 __device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t smem_addr) {

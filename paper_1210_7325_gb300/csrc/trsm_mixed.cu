@@ -521,6 +521,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 1) tmem_dealloc(tmem, kTmemCols);
 }
 
+// BF16 or FP16 bits of a genotype code c (|c| <= 128, exact in both): the
+// float of |c| from the 2^23 exponent trick (an integer OR and one FP32
+// subtraction), then its upper half (BF16) or its exponent rebased and
+// mantissa shifted (FP16), and the sign.  Integer and FP32 arithmetic only,
+// instead of two conversion instructions per code on a pipe a quarter as wide.
+template <bool kBF16>
+__device__ __forceinline__ uint32_t code16(int c) {
+  const uint32_t m = (uint32_t)(c < 0 ? -c : c);
+  const uint32_t fb = __float_as_uint(__uint_as_float(0x4B000000u | m) - 8388608.0f);
+  uint32_t h;
+  if (kBF16) h = fb >> 16;
+  else h = m ? (fb >> 13) - (112u << 10) : 0u;
+  return h | (c < 0 ? 0x8000u : 0u);
+}
+
 // X_R block (n x k int8, ldx) -> operand layout X16[j][c] (16-bit) and the
 // aligned byte copy X8a[j][c], c < npad (zero rows >= n).
 template <bool kBF16>
@@ -540,9 +555,7 @@ __global__ void convert_x_kernel(const int8_t* __restrict__ x8, int64_t ldx, int
       const int64_t c = c0 + e;
       const int xi = (c < n) ? (int)x8[c + j * ldx] : 0;
       b[e] = (uint32_t)(uint8_t)(int8_t)xi;
-      const float xf = (float)xi;
-      v[e] = kBF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(xf))
-                   : __half_as_ushort(__float2half_rn(xf));
+      v[e] = (uint16_t)code16<kBF16>(xi);
     }
     uint4 w;
     w.x = (uint32_t)v[0] | ((uint32_t)v[1] << 16);
@@ -585,12 +598,10 @@ __global__ void __launch_bounds__(256) convert_x_wide_kernel(
     uint32_t o[8];
 #pragma unroll
     for (int e = 0; e < 16; e += 2) {
-      const float a = (float)(int8_t)(wv[e / 4] >> (8 * (e % 4)));
-      const float b = (float)(int8_t)(wv[e / 4] >> (8 * (e % 4 + 1)));
-      const uint32_t va = kBF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(a))
-                                : __half_as_ushort(__float2half_rn(a));
-      const uint32_t vb = kBF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(b))
-                                : __half_as_ushort(__float2half_rn(b));
+      const int a = (int)(int8_t)(wv[e / 4] >> (8 * (e % 4)));
+      const int b = (int)(int8_t)(wv[e / 4] >> (8 * (e % 4 + 1)));
+      const uint32_t va = code16<kBF16>(a);
+      const uint32_t vb = code16<kBF16>(b);
       o[e / 2] = va | (vb << 16);
     }
     uint4* dst = reinterpret_cast<uint4*>(x16 + j * npad + c0);
@@ -625,9 +636,7 @@ __global__ void convert_xp_kernel(const uint8_t* __restrict__ xp, int64_t ldp, i
     for (int e = 0; e < 8; ++e) {
       const int xi = (c0 + e < n) ? (int)((w >> (2 * e)) & 3u) : 0;
       b[e] = (uint32_t)xi;
-      const float xf = (float)xi;
-      v[e] = kBF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(xf))
-                   : __half_as_ushort(__float2half_rn(xf));
+      v[e] = (uint16_t)code16<kBF16>(xi);
     }
     uint4 o;
     o.x = (uint32_t)v[0] | ((uint32_t)v[1] << 16);
@@ -706,19 +715,35 @@ __global__ void __launch_bounds__(256) split_kernel(const double* __restrict__ Z
   }
   __syncthreads();
   const double inv_u = 1.0 / red[0][l];  // power of two: exact
-  for (int64_t c0 = 0; c0 < npad; c0 += 64) {
+  // The solve reads the rows of pair I = stripe / 256 up to column 256 (I + 1)
+  // only; columns past that stay as the zeros the buffer was created with.
+  // Chunks right of every row's diagonal block are zeros: no arithmetic.
+  const int64_t stripe0 = (int64_t)blockIdx.x * 32;
+  const int64_t cend = std::min<int64_t>(npad, (stripe0 / kPair + 1) * kPair);
+  const int64_t czero = stripe0 + 31 - ((stripe0 + 31) % kDiag);  // largest r0 of the stripe
+  for (int64_t c0 = 0; c0 < cend; c0 += 64) {
+    if (c0 >= czero) {
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int cc = w + 8 * e;
-      const int64_t c = c0 + cc;
-      const double z = (c < r0) ? Z[r + c * ldz] * inv_u : 0.0;
-      double h = naive ? from16<kBF16>(to16<kBF16>(z)) : rint(z);
-      const double rem = z - h;
-      const uint16_t s1 = to16<kBF16>(rem);
-      const uint16_t s2 = to16<kBF16>(rem - from16<kBF16>(s1));
-      sh[0][l][cc] = to16<kBF16>(h);
-      sh[1][l][cc] = s1;
-      sh[2][l][cc] = s2;
+      for (int e = 0; e < 8; ++e) {
+        const int cc = w + 8 * e;
+        sh[0][l][cc] = 0;
+        sh[1][l][cc] = 0;
+        sh[2][l][cc] = 0;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int cc = w + 8 * e;
+        const int64_t c = c0 + cc;
+        const double z = (c < r0) ? Z[r + c * ldz] * inv_u : 0.0;
+        double h = naive ? from16<kBF16>(to16<kBF16>(z)) : rint(z);
+        const double rem = z - h;
+        const uint16_t s1 = to16<kBF16>(rem);
+        const uint16_t s2 = to16<kBF16>(rem - from16<kBF16>(s1));
+        sh[0][l][cc] = to16<kBF16>(h);
+        sh[1][l][cc] = s1;
+        sh[2][l][cc] = s2;
+      }
     }
     __syncthreads();
     {
