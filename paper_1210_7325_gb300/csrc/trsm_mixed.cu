@@ -110,10 +110,35 @@ constexpr uint64_t kWaitLimitNs = 1000000000ull;  // bounded waits give up after
 constexpr uint64_t kDrainLimitNs = 100000000ull;
 constexpr int kDefaultGroup = 3;        // row-block pairs per rasterization group
 
+// Z's slices (and the rows of W^T) are stored pre-tiled for plain bulk copies:
+// per slice s, 256-row group g (row pair g of Z; g = nP holds the W^T rows)
+// and 32-deep K stage kb, one 16 KB tile in the MMA's K-major layout without
+// swizzling: core matrices of 8 rows x 8 values (128 contiguous bytes), the 4
+// along K 128 bytes apart, groups of 8 rows 512 bytes apart.  A stage's slice
+// then arrives as 128 long contiguous requests instead of 256 rows of 64
+// bytes: the solve is bound by the rate of requests an SM sends to L2 (one
+// 64-byte row per request through a tensor map, measured: halving the rows
+// to 32 bytes doubled the requests and made it 58% slower).
+constexpr int kTileElems = kPair * BK;   // 8192 16-bit values, 16 KB
+constexpr uint32_t kCoreLbo = 128;       // bytes between core matrices adjacent along K
+constexpr uint32_t kCoreSbo = 512;       // bytes between groups of 8 rows
+
+__host__ __device__ __forceinline__ size_t tile_index(int s, int g, int64_t kb, int nG,
+                                                      int64_t nKB) {
+  return ((size_t)s * nG + g) * (size_t)nKB + (size_t)kb;
+}
+// Position of (row rr < 256, column kk < 32) inside a tile.
+__host__ __device__ __forceinline__ int in_tile(int rr, int kk) {
+  return (((rr >> 3) * 4 + (kk >> 3)) * 8 + (rr & 7)) * 8 + (kk & 7);
+}
+
 thread_local std::string g_err;
 
 // Per-problem constants, in device memory.
 struct ProblemDesc {
+  const uint16_t* tiles;  // the pre-tiled slices of Z and W^T (see kTileElems)
+  int64_t nKB;            // K stages per row: npad / 32
+  int nG;                 // 256-row groups: row pairs plus the W^T group
   const uint8_t* x8a;     // genotypes as bytes, SNP-major [j][npad], zero rows >= n
   const float* rowscale;  // u_r, npad + 128 rows
   const float* diagKL;    // npad x (k[4], l[4]): split diagonal blocks
@@ -125,12 +150,11 @@ struct ProblemDesc {
   uint32_t idesc, idesc_half;  // MMA N = 256 (two row blocks) and N = 128 (one), BF16 or FP16
 };
 
-// The TMA maps of every problem of a launch, passed by value as a
-// __grid_constant__ parameter (16 KB for kMaxBatch problems): the TMA unit
+// The TMA map of every problem's genotype operand in a launch, passed by value
+// as a __grid_constant__ parameter (8 KB for kMaxBatch problems): the TMA unit
 // reads them from parameter space, so no map ever lives in global memory
 // that the host writes and later frees and reuses.
 struct MapSet {
-  CUtensorMap tmA[kMaxBatch];  // slices of Z and W^T: (npad, npad + 128, S), 16-bit
   CUtensorMap tmB[kMaxBatch];  // genotype operand X16: (npad, kmax), 16-bit
 };
 
@@ -306,16 +330,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       int last_pi = -1;
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
         const Item w = item_at(probs, run, t);
-        const CUtensorMap* tA = &maps.tmA[w.pi];
+        const ProblemDesc* pd = probs + w.pi;
         const CUtensorMap* tB = &maps.tmB[w.pi];
         if (w.pi != last_pi) {
-          tma_prefetch_desc(tA);
           tma_prefetch_desc(tB);
           last_pi = w.pi;
         }
-        // always a 256-row box: rows past the W^T block read as zeros, and the
-        // rows an N = 128 product does not use are never read by the MMA
-        const int kblocks = w.kblocks(), row0 = w.row0();
+        // group I of the tiled slices (I = nP is the W^T group); an N = 128
+        // product reads the first 128 rows of the tile only: its first 8 KB
+        const uint16_t* tiles = pd->tiles;
+        const int nG = pd->nG;
+        const int64_t nKB = pd->nKB;
+        const uint32_t slice_bytes = w.wide() ? (uint32_t)kSliceBytes : (uint32_t)kSliceBytes / 2;
+        const int kblocks = w.kblocks();
         for (int kb = 0; kb < kblocks; ++kb, ++g) {
           const int st = (int)(g % stages);
           const uint32_t ph = g / stages;
@@ -323,10 +350,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(&full[st], (uint32_t)S * kSliceBytes + kXBytes);
+          mbar_arrive_expect_tx(&full[st], (uint32_t)S * slice_bytes + kXBytes);
           uint8_t* sb = base + (size_t)st * kc.stage_bytes;
           for (int s = 0; s < S; ++s)
-            tma_load_3d(sb + s * kSliceBytes, tA, &full[st], kb * BK, row0, s);
+            bulk_load(sb + s * kSliceBytes, tiles + tile_index(s, w.I, kb, nG, nKB) * kTileElems,
+                      slice_bytes, &full[st]);
           tma_load_2d(sb + S * kSliceBytes, tB, &full[st], kb * BK, w.J * BN);
         }
       }
@@ -368,12 +396,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t sx = sz + (uint32_t)S * kSliceBytes;                 // genotypes
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
+            // genotypes: 64-byte swizzled rows (TMA); slices: untiled core
+            // matrices, the second K = 16 half two core matrices further on
             const uint64_t adesc = umma_desc_sw64(sx + kk * 32);
             const uint32_t first = (kb | kk) != 0;
-            umma_f16(dH, adesc, umma_desc_sw64(sz + kk * 32), idesc, first);
+            umma_f16(dH, adesc, umma_desc_noswz(sz + kk * 2 * kCoreLbo, kCoreLbo, kCoreSbo), idesc,
+                     first);
             for (int s = 1; s < S; ++s)
-              umma_f16(dR, adesc, umma_desc_sw64(sz + s * kSliceBytes + kk * 32), idesc,
-                       first | (s > 1));
+              umma_f16(dR, adesc,
+                       umma_desc_noswz(sz + s * kSliceBytes + kk * 2 * kCoreLbo, kCoreLbo, kCoreSbo),
+                       idesc, first | (s > 1));
           }
           umma_commit(&empty[st]);
         }
@@ -670,7 +702,7 @@ __device__ __forceinline__ double from16(uint16_t b) {
 template <bool kBF16>
 __global__ void __launch_bounds__(256) split_kernel(const double* __restrict__ Z, int64_t ldz,
                                                     int64_t npad, int S, int bits, int naive,
-                                                    uint16_t* __restrict__ slices,
+                                                    int nG, uint16_t* __restrict__ tiles,
                                                     float* __restrict__ rowscale,
                                                     float* __restrict__ diagKL,
                                                     float* __restrict__ diagS) {
@@ -747,8 +779,13 @@ __global__ void __launch_bounds__(256) split_kernel(const double* __restrict__ Z
     }
     __syncthreads();
     {
-      const int rl = threadIdx.x / 8, ch = threadIdx.x % 8;
-      const int64_t rr = (int64_t)blockIdx.x * 32 + rl;
+      // one 16-byte core-matrix row per thread, 8 threads per core matrix: a
+      // warp writes 4 core matrices of one tile (512 contiguous bytes)
+      const int r8 = threadIdx.x & 7, ch = (threadIdx.x >> 3) & 7, rl = (threadIdx.x >> 6) * 8 + r8;
+      const int64_t row = stripe0 + rl;
+      const int g = (int)(row / kPair), rr = (int)(row % kPair);
+      const int64_t c = c0 + ch * 8;
+      const int64_t nKB = npad / BK;
       for (int s = 0; s < S; ++s) {
         uint4 v;
         const uint16_t* src = &sh[s][rl][ch * 8];
@@ -756,8 +793,8 @@ __global__ void __launch_bounds__(256) split_kernel(const double* __restrict__ Z
         v.y = (uint32_t)src[2] | ((uint32_t)src[3] << 16);
         v.z = (uint32_t)src[4] | ((uint32_t)src[5] << 16);
         v.w = (uint32_t)src[6] | ((uint32_t)src[7] << 16);
-        *reinterpret_cast<uint4*>(slices + (size_t)s * (npad + 128) * npad + rr * npad + c0 +
-                                  ch * 8) = v;
+        *reinterpret_cast<uint4*>(tiles + tile_index(s, g, c / BK, nG, nKB) * kTileElems +
+                                  in_tile(rr, (int)(c % BK))) = v;
       }
     }
     __syncthreads();
@@ -808,8 +845,8 @@ __global__ void __launch_bounds__(256) wtrans_kernel(const double* __restrict__ 
 // with its own scale u = 2^(E - bits) over the whole row.  One CTA per q.
 template <bool kBF16>
 __global__ void __launch_bounds__(256) split_w_kernel(const double* __restrict__ W, int64_t npad,
-                                                      int bits, int naive,
-                                                      uint16_t* __restrict__ slices,
+                                                      int bits, int naive, int nG,
+                                                      uint16_t* __restrict__ tiles,
                                                       float* __restrict__ rowscale) {
   __shared__ double red[256];
   const int q = blockIdx.x;
@@ -832,16 +869,19 @@ __global__ void __launch_bounds__(256) split_w_kernel(const double* __restrict__
   const int64_t row = npad + q;
   if (threadIdx.x == 0) rowscale[row] = (float)u;
   const double inv_u = 1.0 / u;
-  const size_t plane = (size_t)(npad + 128) * npad;
+  // row q of the W^T group (the last 256-row group of the tiles)
+  const int64_t nKB = npad / BK;
+  const int gW = nG - 1;
   for (int64_t c = threadIdx.x; c < npad; c += blockDim.x) {
     const double z = w[c] * inv_u;
     const double h = naive ? from16<kBF16>(to16<kBF16>(z)) : rint(z);
     const double rem = z - h;
     const uint16_t s1 = to16<kBF16>(rem);
     const uint16_t s2 = to16<kBF16>(rem - from16<kBF16>(s1));
-    slices[row * npad + c] = to16<kBF16>(h);
-    slices[plane + row * npad + c] = s1;
-    slices[2 * plane + row * npad + c] = s2;
+    const int o = in_tile(q, (int)(c % BK));
+    tiles[tile_index(0, gW, c / BK, nG, nKB) * kTileElems + o] = to16<kBF16>(h);
+    tiles[tile_index(1, gW, c / BK, nG, nKB) * kTileElems + o] = s1;
+    tiles[tile_index(2, gW, c / BK, nG, nKB) * kTileElems + o] = s2;
   }
 }
 
@@ -870,7 +910,9 @@ struct MixedState {
   bool bf16 = true;
   bool naive = false;
   int num_sms = 1;
-  uint16_t* slices = nullptr;  // 3 planes x (npad + 128) x npad, row-major (K-major)
+  uint16_t* slices = nullptr;  // 3 planes of nG x nKB tiles (see kTileElems)
+  int nG = 1;                  // 256-row groups: row pairs plus the W^T group
+  int64_t nKB = 1;             // 32-deep K stages per row
   float* rowscale = nullptr;   // npad + 128
   float* diagKL = nullptr;     // npad x 8: k[4], l[4] of the diagonal blocks
   float* diagS = nullptr;      // npad
@@ -907,10 +949,16 @@ bool g_attr_done = false;
 
 }  // namespace
 
+size_t tiles_bytes(int64_t npad) {
+  const int64_t nI = npad / BM;
+  const int64_t nG = (nI + 1) / 2 + 1;
+  return (size_t)3 * nG * (npad / BK) * kTileElems * 2;
+}
+
 size_t mixed_footprint(int64_t n, int64_t npad, int p, int64_t kmax, int split_terms) {
   (void)n;
   (void)split_terms;
-  size_t b = (size_t)3 * (npad + 128) * npad * 2;
+  size_t b = tiles_bytes(npad);
   b += (size_t)(npad + 128) * 4 + (size_t)npad * (9 * 4 + 8 * p);
   b += (size_t)kmax * npad * 3 + sizeof(ProblemDesc);
   return b;
@@ -950,6 +998,8 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   ms->npad = npad;
   ms->kmax = kmax;
   ms->p = p;
+  ms->nG = (int)((npad / BM + 1) / 2 + 1);
+  ms->nKB = npad / BK;
   // BF16 slices below kBf16MinN rows fall short of 1e-6 on b_i; FP16 slices
   // (three more bits per slice, same tensor rate) meet it at every size
   ms->bf16 = (precision == GLS_PREC_MIXED_BF16) && n >= kBf16MinN;
@@ -965,7 +1015,7 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&ms->num_sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t rows = (size_t)npad + 128;
-  if (cudaMalloc(&ms->slices, 3 * rows * npad * 2) != cudaSuccess ||
+  if (cudaMalloc(&ms->slices, tiles_bytes(npad)) != cudaSuccess ||
       cudaMalloc(&ms->rowscale, rows * 4) != cudaSuccess ||
       cudaMalloc(&ms->diagKL, (size_t)npad * 8 * 4) != cudaSuccess ||
       cudaMalloc(&ms->diagS, (size_t)npad * 4) != cudaSuccess ||
@@ -977,7 +1027,7 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
     return fail(GLS_ERR_OOM, "cudaMalloc of the mixed-precision operands failed");
   }
   // the W^T block's unused rows stay zero
-  if (cudaMemsetAsync(ms->slices, 0, 3 * rows * npad * 2, st) != cudaSuccess ||
+  if (cudaMemsetAsync(ms->slices, 0, tiles_bytes(npad), st) != cudaSuccess ||
       cudaMemsetAsync(ms->rowscale, 0, rows * 4, st) != cudaSuccess) {
     cudaGetLastError();
     return fail(GLS_ERR_CUDA, "cudaMemset of the operand slices failed");
@@ -1011,17 +1061,6 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   memset(&d, 0, sizeof(d));
   memset(&ms->maps, 0, sizeof(ms->maps));
   {
-    cuuint64_t dims[3] = {(cuuint64_t)npad, (cuuint64_t)rows, (cuuint64_t)ms->S};
-    cuuint64_t strides[2] = {(cuuint64_t)npad * 2, (cuuint64_t)rows * npad * 2};
-    cuuint32_t box[3] = {BK, kPair, 1};
-    cuuint32_t es[3] = {1, 1, 1};
-    if (enc(&ms->maps.tmA[0], dt, 3, ms->slices, dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return fail(GLS_ERR_CUDA, "tensor map encode (slices) failed");
-  }
-  {
     cuuint64_t dims[2] = {(cuuint64_t)npad, (cuuint64_t)kmax};
     cuuint64_t strides[1] = {(cuuint64_t)npad * 2};
     cuuint32_t box[2] = {BK, BN};
@@ -1032,6 +1071,9 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return fail(GLS_ERR_CUDA, "tensor map encode (genotypes) failed");
   }
+  d.tiles = ms->slices;
+  d.nKB = ms->nKB;
+  d.nG = ms->nG;
   d.x8a = ms->x8a;
   d.rowscale = ms->rowscale;
   d.diagKL = ms->diagKL;
@@ -1053,20 +1095,22 @@ gls_status_t mixed_prepare(MixedState* ms, const double* Z, int64_t ldz, const d
     const unsigned grid = (unsigned)(ms->npad / 32);
     if (ms->bf16)
       split_kernel<true><<<grid, 256, 0, st>>>(Z, ldz, ms->npad, ms->S, ms->bits, ms->naive,
-                                               ms->slices, ms->rowscale, ms->diagKL, ms->diagS);
+                                               ms->nG, ms->slices, ms->rowscale, ms->diagKL,
+                                               ms->diagS);
     else
       split_kernel<false><<<grid, 256, 0, st>>>(Z, ldz, ms->npad, ms->S, ms->bits, ms->naive,
-                                                ms->slices, ms->rowscale, ms->diagKL, ms->diagS);
+                                                ms->nG, ms->slices, ms->rowscale, ms->diagKL,
+                                                ms->diagS);
   }
   if (!w_ready)
     wtrans_kernel<<<(unsigned)(ms->npad / 64), 256, 0, st>>>(Z, ldz, ms->npad, Wt, ldw, ms->p,
                                                              ms->Wm);
   if (ms->bf16)
     split_w_kernel<true><<<(unsigned)ms->p, 256, 0, st>>>(ms->Wm, ms->npad, ms->bits, ms->naive,
-                                                         ms->slices, ms->rowscale);
+                                                         ms->nG, ms->slices, ms->rowscale);
   else
     split_w_kernel<false><<<(unsigned)ms->p, 256, 0, st>>>(ms->Wm, ms->npad, ms->bits, ms->naive,
-                                                          ms->slices, ms->rowscale);
+                                                          ms->nG, ms->slices, ms->rowscale);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     g_err = std::string("mixed prepare: ") + cudaGetErrorString(e);
@@ -1188,7 +1232,6 @@ gls_status_t mixed_batch_create(MixedState* const* states, const double* const* 
   for (int i = 0; i < count; ++i) {
     const int o = b->order[i];
     b->states.push_back(states[o]);
-    b->maps.tmA[i] = states[o]->maps.tmA[0];
     b->maps.tmB[i] = states[o]->maps.tmB[0];
     h[i] = states[o]->desc;
     h[i].Pbr = const_cast<double*>(Pbr[o]);
