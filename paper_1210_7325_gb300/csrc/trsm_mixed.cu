@@ -148,6 +148,7 @@ struct ProblemDesc {
   int64_t npad, ldp;
   int nI, p;
   uint32_t idesc, idesc_half;  // MMA N = 256 (two row blocks) and N = 128 (one), BF16 or FP16
+  uint32_t idesc_w;            // MMA N = 32: the W^T block (p <= 32 rows)
 };
 
 // The TMA map of every problem's genotype operand in a launch, passed by value
@@ -337,11 +338,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           last_pi = w.pi;
         }
         // group I of the tiled slices (I = nP is the W^T group); an N = 128
-        // product reads the first 128 rows of the tile only: its first 8 KB
+        // product reads the first 128 rows of the tile only (its first 8 KB),
+        // the W^T product (N = 32) its first 32 rows (2 KB)
         const uint16_t* tiles = pd->tiles;
         const int nG = pd->nG;
         const int64_t nKB = pd->nKB;
-        const uint32_t slice_bytes = w.wide() ? (uint32_t)kSliceBytes : (uint32_t)kSliceBytes / 2;
+        const uint32_t slice_bytes = w.wide()  ? (uint32_t)kSliceBytes
+                                     : w.lin() ? (uint32_t)kSliceBytes / 8
+                                               : (uint32_t)kSliceBytes / 2;
         const int kblocks = w.kblocks();
         for (int kb = 0; kb < kblocks; ++kb, ++g) {
           const int st = (int)(g % stages);
@@ -377,7 +381,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const Item w = item_at(probs, run, t);
         const int kblocks = w.kblocks();
         // the operand type is per problem: a batch may mix BF16 and FP16 plans
-        const uint32_t idesc = w.wide() ? probs[w.pi].idesc : probs[w.pi].idesc_half;
+        const uint32_t idesc = w.wide()  ? probs[w.pi].idesc
+                               : w.lin() ? probs[w.pi].idesc_w
+                                         : probs[w.pi].idesc_half;
         // the epilogue has read the previous item's accumulators
         if (!mbar_wait_bounded(tempty, ((uint32_t)it & 1) ^ 1, abort_flag, kc.wait_ns)) {
           ok = false;
@@ -1083,6 +1089,7 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   d.p = p;
   d.idesc = umma_idesc_f16(BN, kPair, ms->bf16);
   d.idesc_half = umma_idesc_f16(BN, BM, ms->bf16);
+  d.idesc_w = umma_idesc_f16(BN, 32, ms->bf16);
   *out = ms;
   return GLS_OK;
 }
