@@ -1262,7 +1262,8 @@ def main():
                                 "h2d_bytes_per_step": res["e2e_int8_h2d"],
                                 "d2h_bytes_per_step": res["e2e_d2h"],
                                 "genotype_input": "int8 (gls_solve_stream), pinned blocks "
-                                                  "read in place by the conversion kernel",
+                                                  "read in place, block j+1 converted on 8 "
+                                                  "SMs beside block j's solve",
                                 "step_ms": res.get("e2e_int8_step_ms"),
                                 "diagnostic_step": res.get("e2e_int8_diag"),
                                 "staged_copy_engine": res.get("e2e_int8_staged")}

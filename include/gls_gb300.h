@@ -125,8 +125,12 @@ typedef enum {
  * the copy engine (double-buffered on a side stream) instead of reading them
  * in place.  By default the conversion kernel reads each pinned block over the
  * host link itself: the copy engine's rate on this part falls several-fold
- * while kernels run, reading in place does not depend on it.  Results are the
- * same either way. */
+ * while kernels run, reading in place does not depend on it.  When the
+ * columns start on 16-byte boundaries, block j+1 is then converted beside
+ * the solve of block j, on 8 SMs that solve leaves free, into a second
+ * operand buffer (3 x max_block_snps x npad bytes more device memory,
+ * npad = n rounded up to 128, allocated on the first such call).  Results
+ * are the same either way. */
 #define GLS_FLAG_STAGED_INPUT 16u
 
 /* Plan description.  Zero-initialise and fill the fields that matter. */
@@ -345,7 +349,9 @@ int32_t gls_plan_operand_precision(gls_plan_t plan);
 /* Frees every resource of the plan (after waiting for its work).  NULL is OK. */
 gls_status_t gls_destroy(gls_plan_t plan);
 
-/* Device bytes a plan with this description allocates (0 for an invalid one). */
+/* Device bytes a plan with this description allocates at creation (0 for an
+ * invalid one); a mixed plan's first in-place int8 stream adds a second
+ * operand buffer (see GLS_FLAG_STAGED_INPUT). */
 size_t gls_plan_footprint_bytes(const gls_plan_desc_t* desc);
 
 /* Static, NUL-terminated name of a status code. */

@@ -35,18 +35,31 @@ gls_status_t mixed_prepare(MixedState* ms, const double* Z, int64_t ldz, const d
 // Device buffer (npad x p, column-major) holding W = M^{-1} [X_L | y].
 double* mixed_w_buffer(MixedState* ms);
 
-// One block, step 1: int8 genotypes -> the 16-bit operand layout read by TMA.
+// Adds genotype operand buffer 1 (mixed_buffer_bytes more device memory), so
+// that a stream can convert block j+1 into one buffer beside the solve of
+// block j from the other.  OOM leaves the state usable with buffer 0 alone.
+gls_status_t mixed_add_buffer(MixedState* ms);
+size_t mixed_buffer_bytes(int64_t npad, int64_t kmax);
+// SMs a conversion beside a solve occupies (mixed_convert with side = true).
+constexpr int kSideSms = 8;
+
+// One block, step 1: int8 genotypes -> the 16-bit operand layout read by TMA,
+// into operand buffer buf.  With side, the conversion runs as kSideSms CTAs
+// of 1024 threads meant to run beside a solve launched with side_sms =
+// kSideSms (columns on 16-byte boundaries only).
 cudaError_t mixed_convert(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,
-                          cudaStream_t st);
+                          cudaStream_t st, int buf = 0, bool side = false);
 // The same from 2-bit packed genotype columns (ldp bytes each, four codes a byte).
 cudaError_t mixed_convert_packed(MixedState* ms, const uint8_t* xp, int64_t ldp, int64_t k,
                                  cudaStream_t st);
 // One block, step 2: the persistent tcgen05 solve + Gram epilogue.  Writes the
 // S_BR partials Pbr[I][j] (I < npad/128) and the linear Gram entries
 // Glin[q][j] (q < p-1: S_BL, q = p-1: b_B), j < k, leading dimension ldp.
+// The solve reads operand buffer buf; side_sms > 0 leaves that many SMs free
+// for a conversion running beside it.
 cudaError_t mixed_trsm_gram(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,
                             double* Pbr, double* Glin, int64_t ldp, int* flags,
-                            cudaStream_t st);
+                            cudaStream_t st, int buf = 0, int side_sms = 0);
 
 // Size of the diagonal blocks kept out of the tensor-core slices.
 int mixed_diag_block(const MixedState* ms);

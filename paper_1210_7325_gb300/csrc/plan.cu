@@ -102,6 +102,10 @@ struct gls_plan {
   bool own_stream = false;
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaEvent_t ev_loaded[2]{}, ev_computed[2]{}, ev_stored[2]{}, ev_staged[2]{};
+  // mixed streams reading pinned int8 in place: block j+1 is converted on cvt
+  // into operand buffer (j+1) % 2 beside the solve of block j (first such call)
+  cudaStream_t cvt = nullptr;
+  cudaEvent_t ev_conv[2]{};
 
   double* A = nullptr;      // L, npad x npad
   double* Z = nullptr;      // L^{-1}, npad x npad
@@ -235,15 +239,19 @@ struct Timed {
   gls_plan* pl;
   gls_plan::Slot* slot;
   Capture* cap;
+  cudaStream_t st;
   cudaEvent_t e0 = nullptr;
-  Timed(gls_plan* p, gls_plan::Slot* s) : pl(p), slot(s), cap(p->cap) {
+  // on pl->stream (inside a capture when one is open), or on `side`, a stream
+  // that is never captured
+  Timed(gls_plan* p, gls_plan::Slot* s, cudaStream_t side = nullptr)
+      : pl(p), slot(s), cap(side ? nullptr : p->cap), st(side ? side : p->stream) {
     if (!pl->timing) return;
     e0 = cap ? cap->take() : pool_event(pl);
     if (e0) record(e0);
   }
   void record(cudaEvent_t e) {
-    if (cap) cudaEventRecordWithFlags(e, pl->stream, cudaEventRecordExternal);
-    else cudaEventRecord(e, pl->stream);
+    if (cap) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else cudaEventRecord(e, st);
   }
   void finish() {
     if (!e0) return;
@@ -497,6 +505,9 @@ void free_plan(gls_plan* pl) {
   for (cudaEvent_t e : pl->event_pool) cudaEventDestroy(e);
   if (pl->h2d) cudaStreamDestroy(pl->h2d);
   if (pl->d2h) cudaStreamDestroy(pl->d2h);
+  if (pl->cvt) cudaStreamDestroy(pl->cvt);
+  for (cudaEvent_t e : pl->ev_conv)
+    if (e) cudaEventDestroy(e);
   if (pl->own_stream && pl->stream) cudaStreamDestroy(pl->stream);
   cudaGetLastError();
   delete pl;
@@ -606,9 +617,12 @@ gls_status_t check_flags(gls_plan* pl, int host_flags[gls::kFlagCount]) {
 // Solves one block whose inputs/outputs are all device resident, on pl->stream.
 // Mixed paths only: with xp set, the genotypes are 2-bit packed columns (ldp
 // bytes each) converted straight to the tensor-core operand (xr unused).
+// With `converted` the block's operand is already in buffer buf (xr unused);
+// side_sms > 0 leaves that many SMs to a conversion running beside the solve.
 gls_status_t run_block(gls_plan* pl, const int8_t* xr, int64_t ldxr, int64_t k, double* B,
                        int64_t ldb, int32_t* status, const uint8_t* xp = nullptr,
-                       int64_t ldp = 0) {
+                       int64_t ldp = 0, int buf = 0, bool converted = false,
+                       int side_sms = 0) {
   if (k == 0) return GLS_OK;
   if (pl->precision == GLS_PREC_FP64) {
     {
@@ -623,20 +637,21 @@ gls_status_t run_block(gls_plan* pl, const int8_t* xr, int64_t ldxr, int64_t k, 
   } else {
     double* Pbr = pl->partials;                      // nI x ldp
     double* Glin = pl->partials + (int64_t)pl->nI * pl->ldp;  // p x ldp
-    {
+    if (!converted) {
       Timed t(pl, &pl->t_convert);
       if (xp) GLS_CUDA(gls::mixed_convert_packed(pl->mixed, xp, ldp, k, pl->stream));
       else GLS_CUDA(gls::mixed_convert(pl->mixed, xr, ldxr, k, pl->stream));
+      pl->launches += 1;
     }
     {
       Timed t(pl, &pl->t_trsm);
       GLS_CUDA(gls::mixed_trsm_gram(pl->mixed, xr, ldxr, k, Pbr, Glin, pl->ldp, pl->flags,
-                                    pl->stream));
+                                    pl->stream, buf, side_sms));
     }
     Timed t(pl, &pl->t_solve);
     gls::launch_assemble_solve_split(Glin, Pbr, pl->ldp, pl->nI, pl->p, pl->t_active, k, pl->RTL,
                                      pl->zT, gls::kTauMixed, B, ldb, status, pl->stream);
-    pl->launches += 3;
+    pl->launches += 2;
   }
   GLS_CUDA(cudaGetLastError());
   return GLS_OK;
@@ -1125,6 +1140,29 @@ struct FileRing {
   }
 };
 
+// The second genotype operand buffer, the conversion stream and its events
+// of a mixed plan (first stream that converts beside its solves).  False when
+// they cannot be had; the stream then converts every block in line.
+bool ensure_side(gls_plan* pl) {
+  if (pl->cvt) return true;
+  if (gls::mixed_add_buffer(pl->mixed) != GLS_OK) return false;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+    return false;
+  }
+  pl->cvt = st;
+  pl->ev_conv[0] = ev[0];
+  pl->ev_conv[1] = ev[1];
+  return true;
+}
+
 // The SNP stream of Alg. 8 for int8 (packed = false, ldx >= n) or 2-bit
 // packed (packed = true, ldx >= ceil(n/4)) genotype columns X, or, with a
 // ring, for the blocks the ring reads from a file (X unused; its slots are
@@ -1238,11 +1276,42 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
     return GLS_OK;
   };
 
+  // Reading pinned int8 in place over the host link takes the conversion
+  // several times longer than from HBM, so there block j+1 is converted beside
+  // block j's solve: the solve leaves gls::kSideSms SMs free and the
+  // conversion (that many CTAs of 1024 threads, which never share an SM with a
+  // solve CTA) reads into the other operand buffer there.
+  const bool side = direct && !ring && blocks.size() >= 2 &&
+                    (reinterpret_cast<uintptr_t>(Xdev) % 16) == 0 && (ldx % 16) == 0 &&
+                    ensure_side(pl);
+  auto side_convert = [&](size_t jb) -> gls_status_t {
+    const int b = (int)(jb % 2);
+    // operand buffer b is free once block jb-2 is solved
+    GLS_CUDA(cudaStreamWaitEvent(pl->cvt, pl->ev_computed[b], 0));
+    {
+      Timed tm(pl, &pl->t_convert, pl->cvt);
+      GLS_CUDA(gls::mixed_convert(pl->mixed, reinterpret_cast<const int8_t*>(src_dev(jb)), ldx,
+                                  blocks[jb].second, pl->cvt, b, true));
+    }
+    pl->launches += 1;
+    GLS_CUDA(cudaEventRecord(pl->ev_conv[b], pl->cvt));
+    return GLS_OK;
+  };
+  if (side) {  // block 0 has the GPU to itself
+    Timed tm(pl, &pl->t_convert);
+    GLS_CUDA(gls::mixed_convert(pl->mixed, reinterpret_cast<const int8_t*>(src_dev(0)), ldx,
+                                blocks[0].second, cs, 0, false));
+    pl->launches += 1;
+  }
+
   if (staged) GLS_TRY(issue_load(0));
   for (size_t jb = 0; jb < blocks.size(); ++jb) {
     const int s = (int)(jb % 2);
     const int64_t s0 = blocks[jb].first, kb = blocks[jb].second;
     if (staged && jb + 1 < blocks.size()) GLS_TRY(issue_load(jb + 1));
+    // queued before block jb's solve, so that the two start together
+    if (side && jb + 1 < blocks.size()) GLS_TRY(side_convert(jb + 1));
+    if (side && jb >= 1) GLS_CUDA(cudaStreamWaitEvent(cs, pl->ev_conv[s], 0));
     if (direct && ring && !ring->wait_filled(jb)) {
       set_error("reading genotype block %zu from the file failed: %s", jb, strerror(ring->err));
       return GLS_ERR_IO;
@@ -1252,7 +1321,16 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
     double* bout = out_b_host ? pl->bdev[s] : B + s0 * t * ldb;
     const int64_t ldout = out_b_host ? p : ldb;
     int32_t* sout = snp_status ? (out_s_host ? pl->sdev[s] : snp_status + s0) : nullptr;
-    if (packed && pl->precision != GLS_PREC_FP64) {
+    if (side) {
+      const int side_sms = jb + 1 < blocks.size() ? gls::kSideSms : 0;
+      GLS_TRY(replayed(pl, pl->replays,
+                       (KeyHash() << 5u << (uint64_t)s << kb << bout << ldout << sout
+                        << (uint64_t)t << (uint64_t)side_sms).h,
+                       [&]() {
+                         return run_block(pl, nullptr, 0, kb, bout, ldout, sout, nullptr, 0, s,
+                                          true, side_sms);
+                       }));
+    } else if (packed && pl->precision != GLS_PREC_FP64) {
       // the mixed paths convert the packed codes straight to their operand
       const uint8_t* src = (mx == Mem::Device) ? X + s0 * ldx : pl->xp[s];
       const int64_t ld = (mx == Mem::Device) ? ldx : width;

@@ -649,6 +649,70 @@ __global__ void __launch_bounds__(256) convert_x_wide_kernel(
   }
 }
 
+// The conversion of the next block beside a running solve, for sources whose
+// columns start on 16-byte boundaries: kSideCtas CTAs of 1024 threads, each
+// thread with two 16-byte loads in flight (pinned host memory read over the
+// host link needs bytes in flight).  A solve CTA (about 53.8K registers) and
+// one of these (32K) never fit on one SM together, and the solve launch leaves
+// kSideCtas SMs free, so the two kernels do not share SMs whichever starts
+// first.
+constexpr int kSideCtas = kSideSms;
+constexpr int kSideThreads = 1024;
+
+template <bool kBF16>
+__device__ __forceinline__ void convert16(uint4 raw, int64_t j, int64_t c0, int64_t npad,
+                                          uint16_t* __restrict__ x16, uint8_t* __restrict__ x8a) {
+  const uint32_t wv[4] = {raw.x, raw.y, raw.z, raw.w};
+  uint32_t o[8];
+#pragma unroll
+  for (int e = 0; e < 16; e += 2) {
+    const int a = (int)(int8_t)(wv[e / 4] >> (8 * (e % 4)));
+    const int b = (int)(int8_t)(wv[e / 4] >> (8 * (e % 4 + 1)));
+    o[e / 2] = code16<kBF16>(a) | (code16<kBF16>(b) << 16);
+  }
+  uint4* dst = reinterpret_cast<uint4*>(x16 + j * npad + c0);
+  dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+  dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+  *reinterpret_cast<uint4*>(x8a + j * npad + c0) = raw;
+}
+
+template <bool kBF16>
+__device__ __forceinline__ uint4 load16(const int8_t* __restrict__ x8, int64_t ldx, int64_t n,
+                                        int64_t idx, int64_t per_col, int64_t* j, int64_t* c0) {
+  *j = idx / per_col;
+  *c0 = (idx - *j * per_col) * 16;
+  const int8_t* col = x8 + *j * ldx;
+  uint4 raw = make_uint4(0, 0, 0, 0);
+  if (*c0 + 16 <= n) {
+    raw = *reinterpret_cast<const uint4*>(col + *c0);
+  } else if (*c0 < n) {  // ragged end of the column: bytes, rows >= n stay zero
+    uint32_t w[4] = {0, 0, 0, 0};
+    for (int e = 0; e < 16 && *c0 + e < n; ++e)
+      w[e / 4] |= (uint32_t)(uint8_t)col[*c0 + e] << (8 * (e % 4));
+    raw = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  return raw;
+}
+
+template <bool kBF16>
+__global__ void __launch_bounds__(kSideThreads) convert_x_side_kernel(
+    const int8_t* __restrict__ x8, int64_t ldx, int64_t n, int64_t k, int64_t npad,
+    uint16_t* __restrict__ x16, uint8_t* __restrict__ x8a) {
+  const int64_t per_col = npad / 16;
+  const int64_t total = k * per_col;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += 2 * stride) {
+    int64_t j0, c00, j1 = 0, c01 = 0;
+    const uint4 r0 = load16<kBF16>(x8, ldx, n, idx, per_col, &j0, &c00);
+    const bool two = idx + stride < total;
+    uint4 r1 = make_uint4(0, 0, 0, 0);
+    if (two) r1 = load16<kBF16>(x8, ldx, n, idx + stride, per_col, &j1, &c01);
+    convert16<kBF16>(r0, j0, c00, npad, x16, x8a);
+    if (two) convert16<kBF16>(r1, j1, c01, npad, x16, x8a);
+  }
+}
+
 // The same outputs from 2-bit packed genotype columns (ldp bytes each; row i
 // in bits 2 (i mod 4) .. 2 (i mod 4) + 1 of byte i / 4): the 8 rows of a
 // thread are two packed bytes, so the block is read once, at a quarter of
@@ -930,6 +994,15 @@ struct MixedState {
   ProblemDesc* d_desc = nullptr;  // device copy used by single-problem launches
   double* d_Pbr = nullptr;     // buffers the device copy currently points to
   double* d_Glin = nullptr;
+  // Genotype operand buffer 1 (mixed_add_buffer): a stream converts block j+1
+  // into one buffer beside the solve of block j from the other.
+  uint16_t* x16b = nullptr;
+  uint8_t* x8ab = nullptr;
+  ProblemDesc descb;
+  MapSet mapsb;
+  ProblemDesc* d_descb = nullptr;
+  double* d_Pbrb = nullptr;
+  double* d_Glinb = nullptr;
   KConst kc{};
   size_t smem = 0;
 };
@@ -984,8 +1057,60 @@ void mixed_free(MixedState* ms) {
   cudaFree(ms->x16);
   cudaFree(ms->x8a);
   cudaFree(ms->d_desc);
+  cudaFree(ms->x16b);
+  cudaFree(ms->x8ab);
+  cudaFree(ms->d_descb);
   delete ms;
 }
+
+namespace {
+
+// The tensor map of a genotype operand buffer (kmax x npad 16-bit, boxes of
+// BK x BN, 64-byte swizzle) into slot 0 of maps.
+bool encode_x16(const MixedState* ms, uint16_t* x16, MapSet* maps) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+  if (!enc) return false;
+  const CUtensorMapDataType dt =
+      ms->bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  cuuint64_t dims[2] = {(cuuint64_t)ms->npad, (cuuint64_t)ms->kmax};
+  cuuint64_t strides[1] = {(cuuint64_t)ms->npad * 2};
+  cuuint32_t box[2] = {BK, BN};
+  cuuint32_t es[2] = {1, 1};
+  return enc(&maps->tmB[0], dt, 2, x16, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+gls_status_t mixed_add_buffer(MixedState* ms) {
+  if (ms->x16b) return GLS_OK;
+  const size_t cells = (size_t)ms->kmax * ms->npad;
+  if (cudaMalloc(&ms->x16b, cells * 2) != cudaSuccess ||
+      cudaMalloc(&ms->x8ab, cells) != cudaSuccess ||
+      cudaMalloc(&ms->d_descb, sizeof(ProblemDesc)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(ms->x16b);
+    cudaFree(ms->x8ab);
+    cudaFree(ms->d_descb);
+    ms->x16b = nullptr;
+    ms->x8ab = nullptr;
+    ms->d_descb = nullptr;
+    g_err = "cudaMalloc of the second genotype operand buffer failed";
+    return GLS_ERR_OOM;
+  }
+  ms->descb = ms->desc;
+  ms->descb.x8a = ms->x8ab;
+  ms->d_Pbrb = ms->d_Glinb = nullptr;  // the device copy is written on first use
+  memset(&ms->mapsb, 0, sizeof(ms->mapsb));
+  if (!encode_x16(ms, ms->x16b, &ms->mapsb)) {
+    g_err = "tensor map encode (second genotype buffer) failed";
+    return GLS_ERR_CUDA;
+  }
+  return GLS_OK;
+}
+
+size_t mixed_buffer_bytes(int64_t npad, int64_t kmax) { return (size_t)kmax * npad * 3; }
 
 gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int64_t kmax,
                           int precision, int split_terms, uint32_t flags, int32_t wait_limit_us,
@@ -1066,17 +1191,9 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   ProblemDesc& d = ms->desc;
   memset(&d, 0, sizeof(d));
   memset(&ms->maps, 0, sizeof(ms->maps));
-  {
-    cuuint64_t dims[2] = {(cuuint64_t)npad, (cuuint64_t)kmax};
-    cuuint64_t strides[1] = {(cuuint64_t)npad * 2};
-    cuuint32_t box[2] = {BK, BN};
-    cuuint32_t es[2] = {1, 1};
-    if (enc(&ms->maps.tmB[0], dt, 2, ms->x16, dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return fail(GLS_ERR_CUDA, "tensor map encode (genotypes) failed");
-  }
+  (void)dt;
+  if (!encode_x16(ms, ms->x16, &ms->maps))
+    return fail(GLS_ERR_CUDA, "tensor map encode (genotypes) failed");
   d.tiles = ms->slices;
   d.nKB = ms->nKB;
   d.nG = ms->nG;
@@ -1127,28 +1244,42 @@ gls_status_t mixed_prepare(MixedState* ms, const double* Z, int64_t ldz, const d
 }
 
 cudaError_t mixed_convert(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,
-                          cudaStream_t st) {
+                          cudaStream_t st, int buf, bool side) {
   if (k <= 0) return cudaSuccess;
-  if (((uintptr_t)xr % 16) == 0 && (ldxr % 16) == 0) {
+  if (buf != 0 && !ms->x16b) return cudaErrorInvalidValue;
+  uint16_t* x16 = buf ? ms->x16b : ms->x16;
+  uint8_t* x8a = buf ? ms->x8ab : ms->x8a;
+  const bool wide = ((uintptr_t)xr % 16) == 0 && (ldxr % 16) == 0;
+  if (side) {
+    if (!wide) return cudaErrorInvalidValue;
+    if (ms->bf16)
+      convert_x_side_kernel<true><<<kSideCtas, kSideThreads, 0, st>>>(xr, ldxr, ms->n, k,
+                                                                     ms->npad, x16, x8a);
+    else
+      convert_x_side_kernel<false><<<kSideCtas, kSideThreads, 0, st>>>(xr, ldxr, ms->n, k,
+                                                                      ms->npad, x16, x8a);
+    return cudaGetLastError();
+  }
+  if (wide) {
     const int64_t work = k * (ms->npad / 16);
     const unsigned grid =
         (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 256), ms->num_sms * 8));
     if (ms->bf16)
-      convert_x_wide_kernel<true><<<grid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, ms->x16,
-                                                        ms->x8a);
+      convert_x_wide_kernel<true><<<grid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, x16,
+                                                        x8a);
     else
-      convert_x_wide_kernel<false><<<grid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, ms->x16,
-                                                         ms->x8a);
+      convert_x_wide_kernel<false><<<grid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, x16,
+                                                         x8a);
     return cudaGetLastError();
   }
   const int64_t work = k * (ms->npad / 8);
   const unsigned cgrid = (unsigned)std::min<int64_t>(ceil_div(work, 256), 65535 * 4);
   if (ms->bf16)
-    convert_x_kernel<true><<<cgrid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, ms->x16,
-                                                  ms->x8a);
+    convert_x_kernel<true><<<cgrid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, x16,
+                                                  x8a);
   else
-    convert_x_kernel<false><<<cgrid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, ms->x16,
-                                                   ms->x8a);
+    convert_x_kernel<false><<<cgrid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, x16,
+                                                   x8a);
   return cudaGetLastError();
 }
 
@@ -1174,10 +1305,11 @@ int items_of(const MixedState* ms, int64_t k) {
 }
 
 cudaError_t launch(const MixedState* ms0, const ProblemDesc* d_desc, const RunParams& run,
-                   const MapSet& maps, int* flags, cudaStream_t st) {
+                   const MapSet& maps, int* flags, cudaStream_t st, int max_ctas = 0) {
   KConst kc = ms0->kc;
   kc.flags = flags;
-  const int grid = std::min(ms0->num_sms, std::max(run.total, 1));
+  const int ctas = max_ctas > 0 ? std::min(max_ctas, ms0->num_sms) : ms0->num_sms;
+  const int grid = std::min(ctas, std::max(run.total, 1));
   trsm_gram_mixed_kernel<<<grid, kThreads, ms0->smem, st>>>(d_desc, run, kc, maps);
   return cudaGetLastError();
 }
@@ -1185,21 +1317,26 @@ cudaError_t launch(const MixedState* ms0, const ProblemDesc* d_desc, const RunPa
 }  // namespace
 
 cudaError_t mixed_trsm_gram(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,
-                            double* Pbr, double* Glin, int64_t ldp, int* flags, cudaStream_t st) {
+                            double* Pbr, double* Glin, int64_t ldp, int* flags, cudaStream_t st,
+                            int buf, int side_sms) {
   (void)xr;
   (void)ldxr;
   if (k <= 0) return cudaSuccess;
-  if (Pbr != ms->d_Pbr || Glin != ms->d_Glin || ms->desc.ldp != ldp) {
-    ms->desc.Pbr = Pbr;
-    ms->desc.Glin = Glin;
-    ms->desc.ldp = ldp;
-    cudaError_t e = cudaMemcpyAsync(ms->d_desc, &ms->desc, sizeof(ProblemDesc),
-                                    cudaMemcpyHostToDevice, st);
+  if (buf != 0 && !ms->x16b) return cudaErrorInvalidValue;
+  ProblemDesc& d = buf ? ms->descb : ms->desc;
+  ProblemDesc* dd = buf ? ms->d_descb : ms->d_desc;
+  double*& dPbr = buf ? ms->d_Pbrb : ms->d_Pbr;
+  double*& dGlin = buf ? ms->d_Glinb : ms->d_Glin;
+  if (Pbr != dPbr || Glin != dGlin || d.ldp != ldp) {
+    d.Pbr = Pbr;
+    d.Glin = Glin;
+    d.ldp = ldp;
+    cudaError_t e = cudaMemcpyAsync(dd, &d, sizeof(ProblemDesc), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
     e = cudaStreamSynchronize(st);  // the host copy may change on a later call
     if (e != cudaSuccess) return e;
-    ms->d_Pbr = Pbr;
-    ms->d_Glin = Glin;
+    dPbr = Pbr;
+    dGlin = Glin;
   }
   RunParams run;
   memset(&run, 0, sizeof(run));
@@ -1209,7 +1346,8 @@ cudaError_t mixed_trsm_gram(MixedState* ms, const int8_t* xr, int64_t ldxr, int6
   run.nJ[0] = (int)ceil_div(k, BN);
   run.item_begin[0] = 0;
   run.total = run.item_begin[1] = items_of(ms, k);
-  return launch(ms, ms->d_desc, run, ms->maps, flags, st);
+  return launch(ms, dd, run, buf ? ms->mapsb : ms->maps, flags, st,
+                side_sms > 0 ? ms->num_sms - side_sms : 0);
 }
 
 int mixed_split_terms(const MixedState* ms) { return ms->S; }
