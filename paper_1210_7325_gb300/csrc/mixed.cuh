@@ -40,15 +40,16 @@ double* mixed_w_buffer(MixedState* ms);
 // block j from the other.  OOM leaves the state usable with buffer 0 alone.
 gls_status_t mixed_add_buffer(MixedState* ms);
 size_t mixed_buffer_bytes(int64_t npad, int64_t kmax);
-// SMs a conversion beside a solve occupies (mixed_convert with side = true).
+// SMs a conversion beside a solve occupies (reading pinned host memory over
+// the host link).
 constexpr int kSideSms = 8;
 
 // One block, step 1: int8 genotypes -> the 16-bit operand layout read by TMA,
-// into operand buffer buf.  With side, the conversion runs as kSideSms CTAs
-// of 1024 threads meant to run beside a solve launched with side_sms =
-// kSideSms (columns on 16-byte boundaries only).
+// into operand buffer buf.  With side_ctas > 0 the conversion runs as that
+// many CTAs of 1024 threads, meant to run beside a solve launched with
+// side_sms = side_ctas (columns on 16-byte boundaries only).
 cudaError_t mixed_convert(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,
-                          cudaStream_t st, int buf = 0, bool side = false);
+                          cudaStream_t st, int buf = 0, int side_ctas = 0);
 // The same from 2-bit packed genotype columns (ldp bytes each, four codes a byte).
 cudaError_t mixed_convert_packed(MixedState* ms, const uint8_t* xp, int64_t ldp, int64_t k,
                                  cudaStream_t st);

@@ -1280,18 +1280,26 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
   // several times longer than from HBM, so there block j+1 is converted beside
   // block j's solve: the solve leaves gls::kSideSms SMs free and the
   // conversion (that many CTAs of 1024 threads, which never share an SM with a
-  // solve CTA) reads into the other operand buffer there.
-  const bool side = direct && !ring && blocks.size() >= 2 &&
-                    (reinterpret_cast<uintptr_t>(Xdev) % 16) == 0 && (ldx % 16) == 0 &&
+  // solve CTA) writes the other operand buffer there.  From HBM the
+  // conversion stays in line: on 3 SMs it took longer than the solves it ran
+  // beside (about 54 GB/s per SM), and 8 SMs cost the solve more than the
+  // 0.5 ms per block the conversion takes on the whole GPU.
+  const uint8_t* side_base = reinterpret_cast<const uint8_t*>(Xdev);
+  const bool side = direct && !ring && blocks.size() >= 2 && side_base &&
+                    (reinterpret_cast<uintptr_t>(side_base) % 16) == 0 && (ldx % 16) == 0 &&
                     ensure_side(pl);
+  const int side_sms = gls::kSideSms;
+  auto side_src = [&](size_t jb) -> const int8_t* {
+    return reinterpret_cast<const int8_t*>(side_base + blocks[jb].first * ldx);
+  };
   auto side_convert = [&](size_t jb) -> gls_status_t {
     const int b = (int)(jb % 2);
     // operand buffer b is free once block jb-2 is solved
     GLS_CUDA(cudaStreamWaitEvent(pl->cvt, pl->ev_computed[b], 0));
     {
       Timed tm(pl, &pl->t_convert, pl->cvt);
-      GLS_CUDA(gls::mixed_convert(pl->mixed, reinterpret_cast<const int8_t*>(src_dev(jb)), ldx,
-                                  blocks[jb].second, pl->cvt, b, true));
+      GLS_CUDA(gls::mixed_convert(pl->mixed, side_src(jb), ldx, blocks[jb].second, pl->cvt, b,
+                                  side_sms));
     }
     pl->launches += 1;
     GLS_CUDA(cudaEventRecord(pl->ev_conv[b], pl->cvt));
@@ -1299,8 +1307,7 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
   };
   if (side) {  // block 0 has the GPU to itself
     Timed tm(pl, &pl->t_convert);
-    GLS_CUDA(gls::mixed_convert(pl->mixed, reinterpret_cast<const int8_t*>(src_dev(0)), ldx,
-                                blocks[0].second, cs, 0, false));
+    GLS_CUDA(gls::mixed_convert(pl->mixed, side_src(0), ldx, blocks[0].second, cs, 0, 0));
     pl->launches += 1;
   }
 
@@ -1322,13 +1329,13 @@ gls_status_t stream_impl(gls_plan* pl, const uint8_t* X, int64_t ldx, bool packe
     const int64_t ldout = out_b_host ? p : ldb;
     int32_t* sout = snp_status ? (out_s_host ? pl->sdev[s] : snp_status + s0) : nullptr;
     if (side) {
-      const int side_sms = jb + 1 < blocks.size() ? gls::kSideSms : 0;
+      const int free_sms = jb + 1 < blocks.size() ? side_sms : 0;
       GLS_TRY(replayed(pl, pl->replays,
                        (KeyHash() << 5u << (uint64_t)s << kb << bout << ldout << sout
-                        << (uint64_t)t << (uint64_t)side_sms).h,
+                        << (uint64_t)t << (uint64_t)free_sms).h,
                        [&]() {
                          return run_block(pl, nullptr, 0, kb, bout, ldout, sout, nullptr, 0, s,
-                                          true, side_sms);
+                                          true, free_sms);
                        }));
     } else if (packed && pl->precision != GLS_PREC_FP64) {
       // the mixed paths convert the packed codes straight to their operand

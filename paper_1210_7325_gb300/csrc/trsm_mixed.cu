@@ -650,13 +650,12 @@ __global__ void __launch_bounds__(256) convert_x_wide_kernel(
 }
 
 // The conversion of the next block beside a running solve, for sources whose
-// columns start on 16-byte boundaries: kSideCtas CTAs of 1024 threads, each
-// thread with two 16-byte loads in flight (pinned host memory read over the
-// host link needs bytes in flight).  A solve CTA (about 53.8K registers) and
-// one of these (32K) never fit on one SM together, and the solve launch leaves
-// kSideCtas SMs free, so the two kernels do not share SMs whichever starts
-// first.
-constexpr int kSideCtas = kSideSms;
+// columns start on 16-byte boundaries: up to kSideSms CTAs of 1024 threads,
+// each thread with two 16-byte loads in flight (pinned host memory read over
+// the host link needs bytes in flight).  A solve CTA (about 53.8K registers)
+// and one of these (32K or more) never fit on one SM together, and the solve
+// launch leaves as many SMs free as there are conversion CTAs, so the two
+// kernels do not share SMs whichever starts first.
 constexpr int kSideThreads = 1024;
 
 template <bool kBF16>
@@ -1244,20 +1243,21 @@ gls_status_t mixed_prepare(MixedState* ms, const double* Z, int64_t ldz, const d
 }
 
 cudaError_t mixed_convert(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_t k,
-                          cudaStream_t st, int buf, bool side) {
+                          cudaStream_t st, int buf, int side_ctas) {
   if (k <= 0) return cudaSuccess;
   if (buf != 0 && !ms->x16b) return cudaErrorInvalidValue;
   uint16_t* x16 = buf ? ms->x16b : ms->x16;
   uint8_t* x8a = buf ? ms->x8ab : ms->x8a;
   const bool wide = ((uintptr_t)xr % 16) == 0 && (ldxr % 16) == 0;
-  if (side) {
+  if (side_ctas > 0) {
     if (!wide) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)std::min(side_ctas, kSideSms);
     if (ms->bf16)
-      convert_x_side_kernel<true><<<kSideCtas, kSideThreads, 0, st>>>(xr, ldxr, ms->n, k,
-                                                                     ms->npad, x16, x8a);
+      convert_x_side_kernel<true><<<grid, kSideThreads, 0, st>>>(xr, ldxr, ms->n, k, ms->npad,
+                                                                x16, x8a);
     else
-      convert_x_side_kernel<false><<<kSideCtas, kSideThreads, 0, st>>>(xr, ldxr, ms->n, k,
-                                                                      ms->npad, x16, x8a);
+      convert_x_side_kernel<false><<<grid, kSideThreads, 0, st>>>(xr, ldxr, ms->n, k, ms->npad,
+                                                                 x16, x8a);
     return cudaGetLastError();
   }
   if (wide) {

@@ -129,20 +129,23 @@ def test_mixed_matches_fp64_and_is_block_independent(prec, n):
 
 
 @pytest.mark.parametrize("n", [500, 512])   # columns on 16-byte boundaries or not
-@pytest.mark.parametrize("flags", [0, gls.GLS_FLAG_STAGED_INPUT])
-def test_stream_mixed(n, flags):
-    """Pinned int8 input read in place by the conversion kernel (default; with
-    16-byte-aligned columns block j+1 is converted beside block j's solve into
-    a second operand buffer) or copied by the copy engine
-    (GLS_FLAG_STAGED_INPUT): every call equals the block solve of
-    device-resident input bit for bit, over three calls on one plan (the
-    third replays captured graphs) with odd and even block counts."""
+@pytest.mark.parametrize("flags,source", [(0, "pinned"), (gls.GLS_FLAG_STAGED_INPUT, "pinned"),
+                                          (0, "device")])
+def test_stream_mixed(n, flags, source):
+    """Pinned int8 input read in place by the conversion kernel (default) or
+    copied by the copy engine (GLS_FLAG_STAGED_INPUT), and int8 input held in
+    device memory; with 16-byte-aligned columns, in place or from HBM, block
+    j+1 is converted beside block j's solve into a second operand buffer.
+    Every call equals the block solve of device-resident input bit for bit,
+    over three calls on one plan (the third replays captured graphs) with odd
+    and even block counts."""
     import torch
     pr = synth.problem(n, 4, 3100, 0.5, seed=14, n_markers=700)
     Bb, sb = run_gpu(pr, "fp16", kmax=1000)
     with gls.Plan(n, 4, 1000, precision="fp16", flags=flags) as plan:
         plan.factor(np.asfortranarray(pr["M"]), np.asfortranarray(pr["XL"]), pr["y"])
-        XR = torch.from_numpy(np.ascontiguousarray(pr["XR"].T)).pin_memory()
+        XR = torch.from_numpy(np.ascontiguousarray(pr["XR"].T))
+        XR = XR.pin_memory() if source == "pinned" else XR.cuda()
         for m in (2500, 3100, 3100):                # 5 and 6 blocks
             B = np.full((4, m), -1.0, order="F")
             st = np.full(m, -1, np.int32)
