@@ -128,7 +128,7 @@ typedef enum {
  * while kernels run, reading in place does not depend on it.  When the
  * columns start on 16-byte boundaries, block j+1 is then converted beside
  * the solve of block j, on 8 SMs that solve leaves free, into a second
- * operand buffer (3 x max_block_snps x npad bytes more device memory,
+ * operand buffer (2 x max_block_snps x npad bytes more device memory,
  * npad = n rounded up to 128, allocated on the first such call).  Results
  * are the same either way. */
 #define GLS_FLAG_STAGED_INPUT 16u

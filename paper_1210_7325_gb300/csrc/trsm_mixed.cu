@@ -139,7 +139,8 @@ struct ProblemDesc {
   const uint16_t* tiles;  // the pre-tiled slices of Z and W^T (see kTileElems)
   int64_t nKB;            // K stages per row: npad / 32
   int nG;                 // 256-row groups: row pairs plus the W^T group
-  const uint8_t* x8a;     // genotypes as bytes, SNP-major [j][npad], zero rows >= n
+  const uint16_t* x16;    // genotype operand, SNP-major [j][npad], zero rows >= n
+  int bf16;               // its codes are BF16 (else FP16)
   const float* rowscale;  // u_r, npad + 128 rows
   const float* diagKL;    // npad x (k[4], l[4]): split diagonal blocks
   const float* diagS;     // npad: s_r
@@ -248,6 +249,21 @@ __device__ __forceinline__ bool epilogue_all(bool ok) {
 __device__ __forceinline__ bool wait_drain(uint64_t* bar, uint32_t parity) {
   volatile int never = 0;
   return mbar_wait_bounded(bar, parity, &never, kDrainLimitNs);
+}
+
+// Four 16-bit genotype codes (two per word, low half first) as four signed
+// bytes.  The codes hold integers, so each converts back exactly: BF16 widens
+// to FP32 by a shift, FP16 through the half type.
+__device__ __forceinline__ uint32_t codes_to_bytes(uint32_t w0, uint32_t w1, bool bf16) {
+  const uint32_t h[4] = {w0 & 0xFFFFu, w0 >> 16, w1 & 0xFFFFu, w1 >> 16};
+  uint32_t r = 0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float f = bf16 ? __uint_as_float(h[e] << 16)
+                         : __half2float(__ushort_as_half((unsigned short)h[e]));
+    r |= (uint32_t)(uint8_t)(int8_t)__float2int_rz(f) << (8 * e);
+  }
+  return r;
 }
 
 // Signed byte k of w as a float: the byte (offset by 128) becomes the low
@@ -457,14 +473,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           ss[et] = pd->diagS[r];
         }
       }
-      uint4 xv[BM / 16];  // this SNP's genotypes of this warp's 128 rows
+      // this SNP's genotypes of this warp's 128 rows, as signed bytes, read
+      // from the operand while the tile's products are still running
+      uint4 xv[BM / 16];
 #pragma unroll
       for (int i = 0; i < BM / 16; ++i) xv[i] = make_uint4(0, 0, 0, 0);
       if (bv && jv) {
         const uint4* src =
-            reinterpret_cast<const uint4*>(pd->x8a + j * pd->npad + (int64_t)blk * BM);
+            reinterpret_cast<const uint4*>(pd->x16 + j * pd->npad + (int64_t)blk * BM);
+        const bool b16 = pd->bf16 != 0;
 #pragma unroll
-        for (int i = 0; i < BM / 16; ++i) xv[i] = __ldg(src + i);
+        for (int i = 0; i < BM / 16; ++i) {
+          const uint4 a = __ldg(src + 2 * i), b = __ldg(src + 2 * i + 1);
+          xv[i] = make_uint4(codes_to_bytes(a.x, a.y, b16), codes_to_bytes(a.z, a.w, b16),
+                             codes_to_bytes(b.x, b.y, b16), codes_to_bytes(b.z, b.w, b16));
+        }
       }
       const bool got = mbar_wait_bounded(tfull, ph, abort_flag, kc.wait_ns);
       if (!epilogue_all(got)) {  // all epilogue threads leave together; also orders the row data
@@ -574,12 +597,11 @@ __device__ __forceinline__ uint32_t code16(int c) {
   return h | (c < 0 ? 0x8000u : 0u);
 }
 
-// X_R block (n x k int8, ldx) -> operand layout X16[j][c] (16-bit) and the
-// aligned byte copy X8a[j][c], c < npad (zero rows >= n).
+// X_R block (n x k int8, ldx) -> operand layout X16[j][c] (16-bit), c < npad
+// (zero rows >= n).
 template <bool kBF16>
 __global__ void convert_x_kernel(const int8_t* __restrict__ x8, int64_t ldx, int64_t n,
-                                 int64_t k, int64_t npad, uint16_t* __restrict__ x16,
-                                 uint8_t* __restrict__ x8a) {
+                                 int64_t k, int64_t npad, uint16_t* __restrict__ x16) {
   const int64_t per_col = npad / 8;
   const int64_t total = k * per_col;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -587,12 +609,10 @@ __global__ void convert_x_kernel(const int8_t* __restrict__ x8, int64_t ldx, int
     const int64_t j = idx / per_col;
     const int64_t c0 = (idx - j * per_col) * 8;
     uint16_t v[8];
-    uint32_t b[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int64_t c = c0 + e;
       const int xi = (c < n) ? (int)x8[c + j * ldx] : 0;
-      b[e] = (uint32_t)(uint8_t)(int8_t)xi;
       v[e] = (uint16_t)code16<kBF16>(xi);
     }
     uint4 w;
@@ -601,21 +621,17 @@ __global__ void convert_x_kernel(const int8_t* __restrict__ x8, int64_t ldx, int
     w.z = (uint32_t)v[4] | ((uint32_t)v[5] << 16);
     w.w = (uint32_t)v[6] | ((uint32_t)v[7] << 16);
     *reinterpret_cast<uint4*>(x16 + j * npad + c0) = w;
-    uint2 bb;
-    bb.x = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
-    bb.y = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
-    *reinterpret_cast<uint2*>(x8a + j * npad + c0) = bb;
   }
 }
 
-// The same outputs with 16 rows per thread and one 16-byte load of codes, for
+// The same output with 16 rows per thread and one 16-byte load of codes, for
 // sources whose columns start on 16-byte boundaries.  Used for HBM sources
 // and for pinned host memory read in place over the host link (the stream's
 // direct path), where wide requests keep enough bytes in flight.
 template <bool kBF16>
 __global__ void __launch_bounds__(256) convert_x_wide_kernel(
     const int8_t* __restrict__ x8, int64_t ldx, int64_t n, int64_t k, int64_t npad,
-    uint16_t* __restrict__ x16, uint8_t* __restrict__ x8a) {
+    uint16_t* __restrict__ x16) {
   const int64_t per_col = npad / 16;
   const int64_t total = k * per_col;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -645,7 +661,6 @@ __global__ void __launch_bounds__(256) convert_x_wide_kernel(
     uint4* dst = reinterpret_cast<uint4*>(x16 + j * npad + c0);
     dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
     dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
-    *reinterpret_cast<uint4*>(x8a + j * npad + c0) = raw;
   }
 }
 
@@ -660,7 +675,7 @@ constexpr int kSideThreads = 1024;
 
 template <bool kBF16>
 __device__ __forceinline__ void convert16(uint4 raw, int64_t j, int64_t c0, int64_t npad,
-                                          uint16_t* __restrict__ x16, uint8_t* __restrict__ x8a) {
+                                          uint16_t* __restrict__ x16) {
   const uint32_t wv[4] = {raw.x, raw.y, raw.z, raw.w};
   uint32_t o[8];
 #pragma unroll
@@ -672,7 +687,6 @@ __device__ __forceinline__ void convert16(uint4 raw, int64_t j, int64_t c0, int6
   uint4* dst = reinterpret_cast<uint4*>(x16 + j * npad + c0);
   dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
   dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
-  *reinterpret_cast<uint4*>(x8a + j * npad + c0) = raw;
 }
 
 template <bool kBF16>
@@ -696,7 +710,7 @@ __device__ __forceinline__ uint4 load16(const int8_t* __restrict__ x8, int64_t l
 template <bool kBF16>
 __global__ void __launch_bounds__(kSideThreads) convert_x_side_kernel(
     const int8_t* __restrict__ x8, int64_t ldx, int64_t n, int64_t k, int64_t npad,
-    uint16_t* __restrict__ x16, uint8_t* __restrict__ x8a) {
+    uint16_t* __restrict__ x16) {
   const int64_t per_col = npad / 16;
   const int64_t total = k * per_col;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -707,19 +721,18 @@ __global__ void __launch_bounds__(kSideThreads) convert_x_side_kernel(
     const bool two = idx + stride < total;
     uint4 r1 = make_uint4(0, 0, 0, 0);
     if (two) r1 = load16<kBF16>(x8, ldx, n, idx + stride, per_col, &j1, &c01);
-    convert16<kBF16>(r0, j0, c00, npad, x16, x8a);
-    if (two) convert16<kBF16>(r1, j1, c01, npad, x16, x8a);
+    convert16<kBF16>(r0, j0, c00, npad, x16);
+    if (two) convert16<kBF16>(r1, j1, c01, npad, x16);
   }
 }
 
-// The same outputs from 2-bit packed genotype columns (ldp bytes each; row i
+// The same output from 2-bit packed genotype columns (ldp bytes each; row i
 // in bits 2 (i mod 4) .. 2 (i mod 4) + 1 of byte i / 4): the 8 rows of a
 // thread are two packed bytes, so the block is read once, at a quarter of
 // the int8 bytes, with no separate unpacking pass.
 template <bool kBF16>
 __global__ void convert_xp_kernel(const uint8_t* __restrict__ xp, int64_t ldp, int64_t n,
-                                  int64_t k, int64_t npad, uint16_t* __restrict__ x16,
-                                  uint8_t* __restrict__ x8a) {
+                                  int64_t k, int64_t npad, uint16_t* __restrict__ x16) {
   const int64_t per_col = npad / 8;
   const int64_t total = k * per_col;
   const int64_t nb = (n + 3) / 4;
@@ -732,11 +745,9 @@ __global__ void convert_xp_kernel(const uint8_t* __restrict__ xp, int64_t ldp, i
     if (b0 < nb) w = xp[j * ldp + b0];
     if (b0 + 1 < nb) w |= (uint32_t)xp[j * ldp + b0 + 1] << 8;
     uint16_t v[8];
-    uint32_t b[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int xi = (c0 + e < n) ? (int)((w >> (2 * e)) & 3u) : 0;
-      b[e] = (uint32_t)xi;
       v[e] = (uint16_t)code16<kBF16>(xi);
     }
     uint4 o;
@@ -745,10 +756,6 @@ __global__ void convert_xp_kernel(const uint8_t* __restrict__ xp, int64_t ldp, i
     o.z = (uint32_t)v[4] | ((uint32_t)v[5] << 16);
     o.w = (uint32_t)v[6] | ((uint32_t)v[7] << 16);
     *reinterpret_cast<uint4*>(x16 + j * npad + c0) = o;
-    uint2 bb;
-    bb.x = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
-    bb.y = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
-    *reinterpret_cast<uint2*>(x8a + j * npad + c0) = bb;
   }
 }
 
@@ -987,7 +994,6 @@ struct MixedState {
   float* diagS = nullptr;      // npad
   double* Wm = nullptr;        // W = M^{-1} [X_L | y], npad x p
   uint16_t* x16 = nullptr;     // kmax x npad
-  uint8_t* x8a = nullptr;      // kmax x npad
   ProblemDesc desc;            // host copy (buffers filled in by the plan per call)
   MapSet maps;                 // this problem's maps in slot 0 (single-problem launches)
   ProblemDesc* d_desc = nullptr;  // device copy used by single-problem launches
@@ -996,7 +1002,6 @@ struct MixedState {
   // Genotype operand buffer 1 (mixed_add_buffer): a stream converts block j+1
   // into one buffer beside the solve of block j from the other.
   uint16_t* x16b = nullptr;
-  uint8_t* x8ab = nullptr;
   ProblemDesc descb;
   MapSet mapsb;
   ProblemDesc* d_descb = nullptr;
@@ -1038,7 +1043,7 @@ size_t mixed_footprint(int64_t n, int64_t npad, int p, int64_t kmax, int split_t
   (void)split_terms;
   size_t b = tiles_bytes(npad);
   b += (size_t)(npad + 128) * 4 + (size_t)npad * (9 * 4 + 8 * p);
-  b += (size_t)kmax * npad * 3 + sizeof(ProblemDesc);
+  b += (size_t)kmax * npad * 2 + sizeof(ProblemDesc);
   return b;
 }
 
@@ -1054,10 +1059,8 @@ void mixed_free(MixedState* ms) {
   cudaFree(ms->diagS);
   cudaFree(ms->Wm);
   cudaFree(ms->x16);
-  cudaFree(ms->x8a);
   cudaFree(ms->d_desc);
   cudaFree(ms->x16b);
-  cudaFree(ms->x8ab);
   cudaFree(ms->d_descb);
   delete ms;
 }
@@ -1086,20 +1089,17 @@ gls_status_t mixed_add_buffer(MixedState* ms) {
   if (ms->x16b) return GLS_OK;
   const size_t cells = (size_t)ms->kmax * ms->npad;
   if (cudaMalloc(&ms->x16b, cells * 2) != cudaSuccess ||
-      cudaMalloc(&ms->x8ab, cells) != cudaSuccess ||
       cudaMalloc(&ms->d_descb, sizeof(ProblemDesc)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(ms->x16b);
-    cudaFree(ms->x8ab);
     cudaFree(ms->d_descb);
     ms->x16b = nullptr;
-    ms->x8ab = nullptr;
     ms->d_descb = nullptr;
     g_err = "cudaMalloc of the second genotype operand buffer failed";
     return GLS_ERR_OOM;
   }
   ms->descb = ms->desc;
-  ms->descb.x8a = ms->x8ab;
+  ms->descb.x16 = ms->x16b;
   ms->d_Pbrb = ms->d_Glinb = nullptr;  // the device copy is written on first use
   memset(&ms->mapsb, 0, sizeof(ms->mapsb));
   if (!encode_x16(ms, ms->x16b, &ms->mapsb)) {
@@ -1109,7 +1109,7 @@ gls_status_t mixed_add_buffer(MixedState* ms) {
   return GLS_OK;
 }
 
-size_t mixed_buffer_bytes(int64_t npad, int64_t kmax) { return (size_t)kmax * npad * 3; }
+size_t mixed_buffer_bytes(int64_t npad, int64_t kmax) { return (size_t)kmax * npad * 2; }
 
 gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int64_t kmax,
                           int precision, int split_terms, uint32_t flags, int32_t wait_limit_us,
@@ -1151,7 +1151,6 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
       cudaMalloc(&ms->diagS, (size_t)npad * 4) != cudaSuccess ||
       cudaMalloc(&ms->Wm, (size_t)npad * p * 8) != cudaSuccess ||
       cudaMalloc(&ms->x16, (size_t)kmax * npad * 2) != cudaSuccess ||
-      cudaMalloc(&ms->x8a, (size_t)kmax * npad) != cudaSuccess ||
       cudaMalloc(&ms->d_desc, sizeof(ProblemDesc)) != cudaSuccess) {
     cudaGetLastError();
     return fail(GLS_ERR_OOM, "cudaMalloc of the mixed-precision operands failed");
@@ -1196,7 +1195,8 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   d.tiles = ms->slices;
   d.nKB = ms->nKB;
   d.nG = ms->nG;
-  d.x8a = ms->x8a;
+  d.x16 = ms->x16;
+  d.bf16 = ms->bf16 ? 1 : 0;
   d.rowscale = ms->rowscale;
   d.diagKL = ms->diagKL;
   d.diagS = ms->diagS;
@@ -1247,17 +1247,16 @@ cudaError_t mixed_convert(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_
   if (k <= 0) return cudaSuccess;
   if (buf != 0 && !ms->x16b) return cudaErrorInvalidValue;
   uint16_t* x16 = buf ? ms->x16b : ms->x16;
-  uint8_t* x8a = buf ? ms->x8ab : ms->x8a;
   const bool wide = ((uintptr_t)xr % 16) == 0 && (ldxr % 16) == 0;
   if (side_ctas > 0) {
     if (!wide) return cudaErrorInvalidValue;
     const unsigned grid = (unsigned)std::min(side_ctas, kSideSms);
     if (ms->bf16)
-      convert_x_side_kernel<true><<<grid, kSideThreads, 0, st>>>(xr, ldxr, ms->n, k, ms->npad,
-                                                                x16, x8a);
+      convert_x_side_kernel<true>
+          <<<grid, kSideThreads, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, x16);
     else
-      convert_x_side_kernel<false><<<grid, kSideThreads, 0, st>>>(xr, ldxr, ms->n, k, ms->npad,
-                                                                 x16, x8a);
+      convert_x_side_kernel<false>
+          <<<grid, kSideThreads, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, x16);
     return cudaGetLastError();
   }
   if (wide) {
@@ -1265,21 +1264,17 @@ cudaError_t mixed_convert(MixedState* ms, const int8_t* xr, int64_t ldxr, int64_
     const unsigned grid =
         (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 256), ms->num_sms * 8));
     if (ms->bf16)
-      convert_x_wide_kernel<true><<<grid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, x16,
-                                                        x8a);
+      convert_x_wide_kernel<true><<<grid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, x16);
     else
-      convert_x_wide_kernel<false><<<grid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, x16,
-                                                         x8a);
+      convert_x_wide_kernel<false><<<grid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, x16);
     return cudaGetLastError();
   }
   const int64_t work = k * (ms->npad / 8);
   const unsigned cgrid = (unsigned)std::min<int64_t>(ceil_div(work, 256), 65535 * 4);
   if (ms->bf16)
-    convert_x_kernel<true><<<cgrid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, x16,
-                                                  x8a);
+    convert_x_kernel<true><<<cgrid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, x16);
   else
-    convert_x_kernel<false><<<cgrid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, x16,
-                                                   x8a);
+    convert_x_kernel<false><<<cgrid, 256, 0, st>>>(xr, ldxr, ms->n, k, ms->npad, x16);
   return cudaGetLastError();
 }
 
@@ -1289,11 +1284,9 @@ cudaError_t mixed_convert_packed(MixedState* ms, const uint8_t* xp, int64_t ldp,
   const int64_t work = k * (ms->npad / 8);
   const unsigned cgrid = (unsigned)std::min<int64_t>(ceil_div(work, 256), 65535 * 4);
   if (ms->bf16)
-    convert_xp_kernel<true><<<cgrid, 256, 0, st>>>(xp, ldp, ms->n, k, ms->npad, ms->x16,
-                                                   ms->x8a);
+    convert_xp_kernel<true><<<cgrid, 256, 0, st>>>(xp, ldp, ms->n, k, ms->npad, ms->x16);
   else
-    convert_xp_kernel<false><<<cgrid, 256, 0, st>>>(xp, ldp, ms->n, k, ms->npad, ms->x16,
-                                                    ms->x8a);
+    convert_xp_kernel<false><<<cgrid, 256, 0, st>>>(xp, ldp, ms->n, k, ms->npad, ms->x16);
   return cudaGetLastError();
 }
 
