@@ -84,8 +84,9 @@ typedef enum {
    *     bits) under a per-row power of two plus an FP32 low part, together at
    *     least 36 bits of the row's diagonal-block scale, applied in FP32 with
    *     one rounding;
-   *   - S_BR = x~^T x~: compensated (error-free) FP32 sums per 128-row block,
-   *     added across blocks in binary64;
+   *   - S_BR = x~^T x~: FP32 squares (each row rounded once) in a
+   *     compensated FP32 sum per 128-row block, added across blocks in
+   *     binary64;
    *   - S_BL and b_B: the same tensor-core products against the rows of
    *     W^T = (M^{-1} [X_L | y])^T (equal to X~_L^T x~ and y~^T x~ by
    *     associativity), scaled to binary64;

@@ -280,23 +280,26 @@ __device__ __forceinline__ float two_sum(float a, float b, float& err) {
   return s;
 }
 
-// Adds (u (aH + aR) + dh)^2 to the compensated sum (sum, comp).  The tensor
-// terms scale exactly by the power of two u; their sum and the diagonal-block
-// term dh join by error-free two-sums into hi + lo; hi^2 is split exactly and
-// 2 hi lo goes to the compensation.
-__device__ __forceinline__ void add_square(uint32_t aH, uint32_t aR, float u, float dh,
-                                           float& sum, float& comp) {
-  const float th = __fmul_rn(__uint_as_float(aH), u);
-  const float tr = __fmul_rn(__uint_as_float(aR), u);
-  float e1, e2, e3;
-  const float s1 = two_sum(th, tr, e1);
-  const float hi = two_sum(s1, dh, e2);
-  const float lo = __fadd_rn(e1, e2);
-  const float pr = __fmul_rn(hi, hi);
-  const float pe = fmaf(hi, hi, -pr);
-  const float cr = __fmul_rn(__fmul_rn(2.f, hi), lo);
-  sum = two_sum(sum, pr, e3);
-  comp = __fadd_rn(comp, __fadd_rn(e3, __fadd_rn(pe, cr)));
+// Adds the squares of four rows' values v = u (aH + aR) + d to the
+// compensated sum (sum, comp): u is a power of two, d the diagonal-block term.
+// Each value and its square are rounded once and the four squares summed in
+// FP32; only that partial sum joins the running total through an error-free
+// two-sum.  The per-row roundings are a few units in the last place of values
+// whose FP32 tensor-core accumulation already carries a larger error, and
+// being independent and unbiased they shrink against the total over n rows;
+// the long sum across the rows is the part whose error would grow with n, and
+// it is the part that is compensated.
+__device__ __forceinline__ void add_squares4(const uint32_t* aH, const uint32_t* aR,
+                                             const float* u, float d0, float d1, float d2,
+                                             float d3, float& sum, float& comp) {
+  const float h0 = fmaf(u[0], __fadd_rn(__uint_as_float(aH[0]), __uint_as_float(aR[0])), d0);
+  const float h1 = fmaf(u[1], __fadd_rn(__uint_as_float(aH[1]), __uint_as_float(aR[1])), d1);
+  const float h2 = fmaf(u[2], __fadd_rn(__uint_as_float(aH[2]), __uint_as_float(aR[2])), d2);
+  const float h3 = fmaf(u[3], __fadd_rn(__uint_as_float(aH[3]), __uint_as_float(aR[3])), d3);
+  const float q = __fadd_rn(fmaf(h0, h0, __fmul_rn(h1, h1)), fmaf(h2, h2, __fmul_rn(h3, h3)));
+  float e;
+  sum = two_sum(sum, q, e);
+  comp = __fadd_rn(comp, e);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -567,10 +570,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const float d3 =
               fmaf(fmaf(z[27], x3, fmaf(z[26], x2, fmaf(z[25], x1, z[24] * x0))), s4.w,
                    fmaf(z[31], x3, fmaf(z[30], x2, fmaf(z[29], x1, z[28] * x0))));
-          add_square(aH[g4 * 4 + 0], aR[g4 * 4 + 0], su[rl + 0], d0, sum, comp);
-          add_square(aH[g4 * 4 + 1], aR[g4 * 4 + 1], su[rl + 1], d1, sum, comp);
-          add_square(aH[g4 * 4 + 2], aR[g4 * 4 + 2], su[rl + 2], d2, sum, comp);
-          add_square(aH[g4 * 4 + 3], aR[g4 * 4 + 3], su[rl + 3], d3, sum, comp);
+          add_squares4(aH + g4 * 4, aR + g4 * 4, su + rl, d0, d1, d2, d3, sum, comp);
         }
       }
       if (jv) pd->Pbr[(int64_t)blk * ldp + j] = (double)sum + (double)comp;
