@@ -149,7 +149,7 @@ struct ProblemDesc {
   int64_t npad, ldp;
   int nI, p;
   uint32_t idesc, idesc_half;  // MMA N = 256 (two row blocks) and N = 128 (one), BF16 or FP16
-  uint32_t idesc_w;            // MMA N = 32: the W^T block (p <= 32 rows)
+  uint32_t idesc_w;            // MMA N = 32 S: the W^T block's rows of all S slices
 };
 
 // The TMA map of every problem's genotype operand in a launch, passed by value
@@ -358,7 +358,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         // group I of the tiled slices (I = nP is the W^T group); an N = 128
         // product reads the first 128 rows of the tile only (its first 8 KB),
-        // the W^T product (N = 32) its first 32 rows (2 KB)
+        // the W^T product its first 32 rows (2 KB) of every slice, landed
+        // side by side so that one N = 32 S product covers all slices
         const uint16_t* tiles = pd->tiles;
         const int nG = pd->nG;
         const int64_t nKB = pd->nKB;
@@ -375,8 +376,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           mbar_arrive_expect_tx(&full[st], (uint32_t)S * slice_bytes + kXBytes);
           uint8_t* sb = base + (size_t)st * kc.stage_bytes;
+          const uint32_t dst_stride = w.lin() ? slice_bytes : (uint32_t)kSliceBytes;
           for (int s = 0; s < S; ++s)
-            bulk_load(sb + s * kSliceBytes, tiles + tile_index(s, w.I, kb, nG, nKB) * kTileElems,
+            bulk_load(sb + s * dst_stride, tiles + tile_index(s, w.I, kb, nG, nKB) * kTileElems,
                       slice_bytes, &full[st]);
           tma_load_2d(sb + S * kSliceBytes, tB, &full[st], kb * BK, w.J * BN);
         }
@@ -399,6 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
         const Item w = item_at(probs, run, t);
         const int kblocks = w.kblocks();
+        const bool lin = w.lin();
         // the operand type is per problem: a batch may mix BF16 and FP16 plans
         const uint32_t idesc = w.wide()  ? probs[w.pi].idesc
                                : w.lin() ? probs[w.pi].idesc_w
@@ -425,12 +428,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             // matrices, the second K = 16 half two core matrices further on
             const uint64_t adesc = umma_desc_sw64(sx + kk * 32);
             const uint32_t first = (kb | kk) != 0;
+            // W^T: the S slices' 32 rows each side by side, one product; slice s
+            // lands in accumulator columns 32 s .. 32 s + 31, so no slice's
+            // products share a sum with another's
             umma_f16(dH, adesc, umma_desc_noswz(sz + kk * 2 * kCoreLbo, kCoreLbo, kCoreSbo), idesc,
                      first);
-            for (int s = 1; s < S; ++s)
-              umma_f16(dR, adesc,
-                       umma_desc_noswz(sz + s * kSliceBytes + kk * 2 * kCoreLbo, kCoreLbo, kCoreSbo),
-                       idesc, first | (s > 1));
+            if (!lin)
+              for (int s = 1; s < S; ++s)
+                umma_f16(dR, adesc,
+                         umma_desc_noswz(sz + s * kSliceBytes + kk * 2 * kCoreLbo, kCoreLbo,
+                                         kCoreSbo),
+                         idesc, first | (s > 1));
           }
           umma_commit(&empty[st]);
         }
@@ -501,11 +509,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lin) {
         // W^T block: column q < p holds (M^{-1}[X_L | y])_q^T x_j
         if (half == 0) {
+          // slice 0 in columns 0 .. 31, slice s > 0 in 32 s .. 32 s + 31
           uint32_t aH[32], aR[32];
+          float lo[32];
+#pragma unroll
+          for (int q = 0; q < 32; ++q) lo[q] = 0.f;
+          for (int s = 1; s < S; ++s) {
+            tmem_ld32(lane_base + 32u * (uint32_t)s, aR);
+            tmem_ld_wait(aR);
+#pragma unroll
+            for (int q = 0; q < 32; ++q) lo[q] += __uint_as_float(aR[q]);
+          }
           tmem_ld32(lane_base, aH);
-          tmem_ld32(lane_base + kAccR, aR);
           tmem_ld_wait(aH);
-          tmem_ld_fence(aR);
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(tempty);
@@ -515,7 +531,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (q < p)
                 pd->Glin[(int64_t)q * ldp + j] =
                     (double)su[q] *
-                    ((double)__uint_as_float(aH[q]) + (double)__uint_as_float(aR[q]));
+                    ((double)__uint_as_float(aH[q]) + (double)lo[q]);
           }
         } else {
           tc_fence_before();
@@ -1205,7 +1221,7 @@ gls_status_t mixed_create(MixedState** out, int64_t n, int64_t npad, int p, int6
   d.p = p;
   d.idesc = umma_idesc_f16(BN, kPair, ms->bf16);
   d.idesc_half = umma_idesc_f16(BN, BM, ms->bf16);
-  d.idesc_w = umma_idesc_f16(BN, 32, ms->bf16);
+  d.idesc_w = umma_idesc_f16(BN, 32 * ms->S, ms->bf16);
   *out = ms;
   return GLS_OK;
 }
