@@ -60,7 +60,7 @@ DEFAULT_WORKLOAD = "n10000_p20_m1000000_bf16"
 # DRAM bytes (read + write) of one launch of the mixed blocked-solve kernel, from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the current
 # kernel at that launch size: (precision, n, SNPs per launch) -> bytes.
-TRSM_TRAFFIC = {("bf16", 10000, 65536): 13.238e9 + 0.0527e9}
+TRSM_TRAFFIC = {("bf16", 10000, 65536): 13.476e9 + 0.0501e9}
 
 # Batched uneven scans: each scan its own kinship, h ~ U(0.1, 0.9); one persistent
 # launch per round serves one block of every scan.
