@@ -36,7 +36,10 @@
 // (= M^{-1} [X_L | y], binary64, once per factor) split the same way as Z: one
 // extra 128-row block of the A operand holds the p rows of W^T, its K range
 // is all n, and its accumulators give the p products per SNP directly, with
-// no cross-row reduction.  (In FP32 those cross products lose accuracy to
+// no cross-row reduction.  All S slices of those rows go through one product
+// of N = 32 S, each slice into its own 32 accumulator columns, added once in
+// the epilogue: sharing one FP32 sum inside the tensor core with the larger
+// slice cost the low slices most of their bits.  (In FP32 those cross products lose accuracy to
 // cancellation; through the exact split they keep about 2^-25 relative to
 // each row's scale.)
 //
@@ -56,8 +59,8 @@
 //               tcgen05.ld of 32 rows at a time, the 4 x 4 diagonal blocks (FP32 split)
 //               from the SNP's own genotypes, and the S_BR sum in registers
 // Work items (row-block pair I = blocks 2I and 2I+1, SNP tile J), I = 0..nP
-// (nP = ceil(nI / 2); I = nP is the W^T block, and an odd last pair holds one
-// block, both issued with N = 128), run heaviest first in groups of `group`
+// (nP = ceil(nI / 2); I = nP is the W^T block, issued with N = 32 S, and an
+// odd last pair holds one block, issued with N = 128), run heaviest first in groups of `group`
 // pairs x all SNP tiles, so the concurrently running CTAs share both the Z
 // slices of a few row blocks and the genotype panels of a few dozen SNP tiles
 // in L2.  The accumulators are single-buffered: the epilogue of an item is
