@@ -18,15 +18,15 @@
 // is negligible.  Slice H accumulates in one TMEM accumulator, R1 + R2 in a
 // second one.  The epilogue forms
 //     x~_r = u_r (acc_H + acc_R) + d_r,   d_r = sum_{c in diag block} Z_rc x_c
-// (the tensor part exactly, as an unevaluated pair of floats) and reduces
-// S_BR = x~^T x~ over the tile's 128 rows with error-free transforms in FP32,
-// written as FP64 partials.  d_r is formed in FP32 as well, from the split
+// rounded once to FP32, and reduces S_BR = x~^T x~ over the tile's 128 rows in
+// a compensated FP32 sum (see add_squares4), written as FP64 partials.  d_r
+// is formed in FP32 as well, from the split
 //     Z_rc = s_r k_rc + l_rc,   s_r = 2^(E_r - 12),   k_rc = rint(Z_rc / s_r),
 // where 2^E_r bounds the row's diagonal-block entries: the integers k (|k| <=
 // 2^12) times genotype codes sum exactly in FP32, the FP32 low parts l
 // (|l| <= s_r / 2) carry the rest, and d_r = fma(sum k x, s_r, sum l x) is
-// rounded once, to about the accuracy of rounding the exact d_r to FP32 (which
-// is all the two-sums below keep of it).  Binary64 arithmetic runs at a small
+// rounded once, to about the accuracy of rounding the exact d_r to FP32 (x~_r
+// is rounded to FP32 right after anyway).  Binary64 arithmetic runs at a small
 // fraction of the FP32 rate on this part, and the epilogue is not overlapped
 // with the products.
 //
